@@ -1,0 +1,326 @@
+#!/usr/bin/env python
+"""Ray-fan throughput benchmark of the GB300 RTM-GD tracer.
+
+One step = one fan of the anisotropic workload (E + F2 + TID ionosphere on a
+91x181x151 FP32 grid, centred dipole, 8/12/16 MHz x 115 elevations x 36
+azimuths x O/X = 24,840 rays, RKF45 at rtol 1e-8) traced through the C ABI.
+The grid is resident on the device (created once, as in serving); inputs of a
+step are the fan arrays.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
+                  [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on the machine's host cores (a
+bounded sample of the same fan per step); it is the baseline arm.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "rays/s and ray-steps/s at ≤0.05 km P'/D error; p50/p99 fan latency"
+
+# Algorithmic floating-point operations of one right-hand-side evaluation
+# (one RK stage) with the dipole field, counted from the kernel source (an FMA
+# counts 2): GD weights 3 x 37 FMA, contraction 192 FMA, grid-coordinate and
+# chain factors ~20 flop, dipole + Jacobian ~70, Appleton-Hartree + partials
+# ~60, Hamiltonian partials + ray equations ~70, stage offsets and RK
+# accumulation ~90 (mixed path; the FP64 path accumulates inside rk*_step64).
+FLOP_PER_EVAL = {"mixed": 1000.0, "fp64": 910.0}
+SMS = 152
+FP32_LANES_PER_SM = 128
+FP64_FMA_PER_SM_CLK = 2  # GB300: FP64 issue rate is 1/64 of FP32
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=30)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    p.add_argument("--no-tune", action="store_true")
+    p.add_argument("--cpu-sample", type=int, default=512)
+    return p.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id):
+        self.rows, self.proc, self.th, self.device_id = [], None, None, device_id
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.device_id)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.th:
+            self.th.join(timeout=5)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        sm, mx, reasons = [], None, set()
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_rate(workload, n_sample, seed=1234):
+    """The FP64 oracle as it stands, on all host cores, over a seeded sample."""
+    from oracle import oracle
+    oracle.build()
+    g = oracle.Grid(workload.grid, workload.ne)
+    idx = np.sort(np.random.default_rng(seed).choice(workload.fan.n_rays, n_sample, replace=False))
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    res = oracle.trace_fan(g, workload.fan, indices=idx, n_threads=cores)
+    dt = time.perf_counter() - t0
+    return dict(value=n_sample / dt, unit="rays/s", cores=cores, kind="oracle",
+                sample="%d seeded rays of the %d-ray fan (FP64 CPU oracle, %d threads)"
+                       % (n_sample, workload.fan.n_rays, cores),
+                ray_steps_per_s=float(res["n_steps"].sum()) / dt, seconds=dt)
+
+
+def near_boundary(res, fan):
+    n_az, n_el = len(fan.az_deg), len(fan.el_deg)
+    r = res.reshape(-1, n_el, n_az)
+    flag = np.zeros(r.shape, bool)
+    jump = ((r["status"][:, 1:] != r["status"][:, :-1]) |
+            (np.abs(np.diff(r["ground_range_km"], axis=1)) > 30.0) |
+            (np.abs(np.diff(r["group_path_km"], axis=1)) > 30.0))
+    flag[:, 1:] |= jump
+    flag[:, :-1] |= jump
+    return flag.reshape(-1)
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    from paper_2506_18579_gb300 import workloads as wl
+    from oracle import oracle
+    oracle.build()
+    w = wl.config2()
+    g = oracle.Grid(w.grid, w.ne)
+    cores = os.cpu_count() or 1
+    per_step = max(cores * 4, 32)
+    rng = np.random.default_rng(99)
+    for _ in range(args.warmup):
+        oracle.trace_fan(g, w.fan, indices=np.sort(rng.choice(w.fan.n_rays, cores, replace=False)),
+                         n_threads=cores)
+    times, steps = [], 0
+    for _ in range(args.steps):
+        idx = np.sort(rng.choice(w.fan.n_rays, per_step, replace=False))
+        t0 = time.perf_counter()
+        res = oracle.trace_fan(g, w.fan, indices=idx, n_threads=cores)
+        times.append(time.perf_counter() - t0)
+        steps += int(res["n_steps"].sum())
+    total = sum(times)
+    value = per_step * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": w.name, "rays_per_step": per_step, "sample_of": w.fan.n_rays},
+        "ray_steps_per_s": steps / total,
+        "cpu_baseline": {"value": value, "unit": "rays/s", "cores": cores, "kind": "oracle",
+                         "sample": "%d seeded rays per step of the %d-ray fan" % (per_step, w.fan.n_rays)},
+        "e2e": {"value": value, "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2506_18579_gb300 import build as rtbuild
+    from paper_2506_18579_gb300 import rtgd as rt
+    from paper_2506_18579_gb300 import workloads as wl
+
+    rtbuild.build()
+    w = wl.config2()
+    prec = rt.RT_MIXED if args.precision == "mixed" else rt.RT_FP64
+    grid = rt.Grid(w.grid, w.ne, table=(prec == rt.RT_MIXED))
+    fan = rt.Fan(w.fan, prec)
+    n = fan.n_rays
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    out = torch.empty(n * 64, dtype=torch.uint8, device="cuda")
+    cfg, tune_ms = None, None
+    if prec == rt.RT_MIXED and not args.no_tune:
+        cfg, tune_ms = rt.rt_tune(grid, fan, max_rays=8192, stream=sptr)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")  # > 129 MB L2
+
+    def step():
+        rt.rt_trace_device(grid, fan, out.data_ptr(), n, cfg=cfg, stream=sptr)
+
+    args.warmup = max(args.warmup, 3)  # at least 3 untimed warm-up steps
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    try:
+        dev_id = torch.cuda.get_device_properties(local_rank).uuid
+        dev_id = "GPU-" + str(dev_id) if not str(dev_id).startswith("GPU-") else str(dev_id)
+    except Exception:
+        dev_id = local_rank
+    clocks = ClockSampler(dev_id)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()  # evict the grid and tables from L2 between timed steps
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    mean_ms = float(np.mean(ms))
+    if world > 1:
+        t = torch.tensor([mean_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        mean_ms = float(t.item())
+    res = rt.results_view(out.cpu().numpy(), n)
+    ray_steps = int(res["n_steps"].sum())
+    attempts = int(res["n_attempts"].sum())
+    evals = int(res["n_evals"].sum())
+
+    # end to end through the public call: fan arrays from the host, results
+    # into pinned host memory, synchronised, every step
+    pinned = torch.empty(n * 64, dtype=torch.uint8, pin_memory=True)
+    host_out = pinned.numpy().view(rt.RESULT_DTYPE)
+    e2e_t = []
+    for i in range(max(3, min(args.steps, 10))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rt.rt_trace(grid, fan, out=host_out, cfg=cfg, stream=sptr)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_s = float(np.mean(e2e_t[1:]))
+
+    line = None
+    if rank == 0:
+        # accuracy of this precision against the all-FP64 GPU path, and its speed
+        fan64 = rt.Fan(w.fan, rt.RT_FP64)
+        grid64 = grid
+        t0 = time.perf_counter()
+        ref64 = rt.rt_trace(grid64, fan64, stream=sptr)
+        fp64_s = time.perf_counter() - t0
+        ok = ~near_boundary(ref64, w.fan) & (ref64["status"] == res["status"])
+        acc = {f: float(np.abs(res[f] - ref64[f])[ok].max()) for f in
+               ("group_path_km", "ground_range_km", "az_dev_deg")}
+        acc["rays_compared"] = int(ok.sum())
+        acc["status_mismatch"] = int((ref64["status"] != res["status"]).sum())
+        sec = mean_ms / 1e3
+        flop = evals * FLOP_PER_EVAL[args.precision]
+        if prec == rt.RT_MIXED:
+            peak = SMS * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
+            bound_note = "FP32 issue: 152 SMs x 128 lanes x 2 flop x 2070 MHz"
+        else:
+            peak = SMS * FP64_FMA_PER_SM_CLK * 2 * 2070e6 / 1e12
+            bound_note = "FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz"
+        achieved = flop / sec / 1e12
+        cpu = cpu_oracle_rate(w, args.cpu_sample) if world == 1 else None
+        line = {
+            "metric": METRIC, "value": n * world / sec, "unit": "rays/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if prec == rt.RT_MIXED else "f64", "data": "synthetic",
+            "config": {"workload": w.name, "rays": n, "precision": args.precision,
+                       "launch": None if cfg is None else {"kernel": cfg.kernel, "stencil": cfg.stencil,
+                                                           "block_threads": cfg.block_threads,
+                                                           "order": cfg.order},
+                       "l2": "flushed (512 MiB write) before every timed step",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "ray_steps_per_s": ray_steps * world / sec,
+            "attempts_per_s": attempts * world / sec,
+            "stage_evals_per_s": evals * world / sec,
+            "fan_latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
+            "accuracy_vs_fp64_gpu": acc,
+            "fp64_gpu_path": {"rays_per_s": n / fp64_s, "seconds": fp64_s},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None, "peak_basis": bound_note,
+                         "flop_per_stage_eval": FLOP_PER_EVAL[args.precision]},
+            "cpu_baseline": cpu,
+            "e2e": {"value": n * world / e2e_s, "unit": "rays/s", "h2d_bytes_per_step": fan.host_bytes,
+                    "d2h_bytes_per_step": n * 64},
+            "gpu_launches": args.steps,
+            "clocks": clk,
+            "wall_s_timed": t_wall,
+            "tune_ms": tune_ms,
+        }
+    grid.close()
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,236 @@
+/*
+ * rtgd.h -- C ABI of the GB300 (sm_103a) RTM-GD ray-fan tracer.
+ *
+ * RTM-GD (arXiv 2506.18579) traces HF rays through a gridded ionosphere: the
+ * Haselgrove ray equations in spherical coordinates (Sec. II-A, Eq. 1a-1f)
+ * with the cold-plasma Hamiltonian (Eq. 2) and the Appleton-Hartree
+ * refractive index without collisions (Eq. 3), where electron density and its
+ * gradient come from the C1 Galerkin-Difference p=3 interpolant of the grid
+ * samples (Sec. II-B, Eq. 13, Appendix A), integrated by Runge-Kutta until the
+ * ray returns to the ground or leaves the ionosphere (Sec. II-C).  Inputs of
+ * the paper's problem statement (Sec. II-C): a gridded Ne field plus a
+ * geomagnetic field model (preprocessing module), and transmitter position,
+ * azimuth, elevation and frequency per ray (main module); outputs: group path,
+ * ground distance, azimuth deviation and reflection height.
+ *
+ * Conventions for every call:
+ *   - The return value carries the call status (rt_err).  On any error the
+ *     message is available from rt_last_error() on the calling thread.
+ *   - Per-ray failures are not call errors; they are reported in
+ *     rt_ray_result.status.
+ *   - Units: degrees, km, MHz, electrons per m^3, tesla.
+ *   - A CUDA GPU is required.  There is no CPU fallback: without a usable
+ *     device every call returns RT_EUNSUPPORTED or RT_ECUDA.
+ *   - "stream" arguments are cudaStream_t values passed as void*; NULL means
+ *     the legacy default stream.
+ *   - Grid handles are immutable after creation and may be used from several
+ *     threads and streams at once; rt_grid_destroy must not race with them.
+ */
+#ifndef RTGD_H
+#define RTGD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RTGD_API_VERSION 1
+
+typedef enum rt_err {
+    RT_OK = 0,
+    RT_EINVAL = 1,       /* bad argument: null pointer, bad size, bad descriptor field */
+    RT_ENOMEM = 2,       /* device or host allocation failed */
+    RT_ECUDA = 3,        /* a CUDA runtime call failed */
+    RT_ETIMEOUT = 4,     /* a bounded wait expired */
+    RT_EUNSUPPORTED = 5  /* no usable CUDA device, or a feature this build lacks */
+} rt_err;
+
+/* Sample type of the Ne array handed to rt_grid_create. */
+enum { RT_F32 = 0, RT_F64 = 1 };
+
+/* rt_grid_desc.flags */
+enum {
+    RT_GRID_TABLE = 1u  /* also build the per-cell stencil table (64 FP32 values per
+                           cell, Sec. II-C "weights computed once per grid cell") */
+};
+
+/* Centred tilted dipole standing in for the geomagnetic model (Sec. II-C):
+ * B = -B0 (R_E/r)^3 [3 (m.p) p - m], m = unit vector to the geomagnetic north
+ * pole at (pole_lat_deg, pole_lon_deg).  b0_tesla = 0 gives an isotropic
+ * medium (no field; O and X modes coincide). */
+typedef struct rt_dipole {
+    double b0_tesla;
+    double pole_lat_deg;
+    double pole_lon_deg;
+} rt_dipole;
+
+/* Uniform geographic grid (Sec. II-B, Eq. 12-13).  Sample (i, j, k) sits at
+ * lat0 + i*dlat, lon0 + j*dlon, alt0 + k*dalt; the host array is laid out
+ * [lat][lon][alt] with alt fastest.  Each dimension needs >= 4 nodes. */
+typedef struct rt_grid_desc {
+    int32_t n_lat, n_lon, n_alt;
+    int32_t dtype;              /* RT_F32 or RT_F64 */
+    double lat0_deg, lon0_deg, alt0_km;
+    double dlat_deg, dlon_deg, dalt_km;
+    double earth_radius_km;     /* e.g. 6371 */
+    rt_dipole field;
+    uint32_t flags;             /* RT_GRID_* */
+    uint32_t reserved;          /* must be 0 */
+} rt_grid_desc;
+
+typedef struct rt_grid rt_grid;  /* opaque; owned by the library until rt_grid_destroy */
+
+/* Create a device-resident grid (Sec. II-C preprocessing module).  ne_host
+ * points to n_lat*n_lon*n_alt samples of the given dtype in host memory; they
+ * are copied (the caller keeps ownership).  The library pads the grid with one
+ * ghost layer per face (quadratic extrapolation, so quadratics stay exact up
+ * to the faces), converts it to the layouts the kernels read and, with
+ * RT_GRID_TABLE, builds the per-cell stencil table.  Blocks until done.
+ * Errors: RT_EINVAL (null pointer, dims < 4, non-positive spacing or radius,
+ * unknown dtype/flags), RT_ENOMEM, RT_ECUDA, RT_EUNSUPPORTED (no device). */
+rt_err rt_grid_create(const rt_grid_desc *desc, const void *ne_host, rt_grid **out);
+
+/* Release a grid and its device memory.  NULL is accepted.  Must not be called
+ * while work that uses the grid is still queued on any stream. */
+rt_err rt_grid_destroy(rt_grid *grid);
+
+/* Bytes of device memory the grid holds. */
+size_t rt_grid_device_bytes(const rt_grid *grid);
+
+/* Ray modes (bit mask), integrators, precisions. */
+enum { RT_MODE_O = 1u, RT_MODE_X = 2u };
+enum { RT_RK4 = 0, RT_RKF45 = 1 };
+enum {
+    RT_FP64 = 0,  /* every step of the path in double precision */
+    RT_MIXED = 1  /* interpolation, Appleton-Hartree and derivatives in FP32; ray state,
+                     its RK accumulation, path sums and the landing solve in FP64 */
+};
+
+/* A fan of rays (Sec. II-C main module): every combination of frequency,
+ * mode, elevation and azimuth from one transmitter.  Ray results are ordered
+ * canonically as [freq][mode][el][az] (ordinary before extraordinary when
+ * both modes are set).  The three arrays are host memory, read during the
+ * call only.
+ *   integrator RT_RK4: fixed step h_km in group path P' (Sec. II-C).
+ *   integrator RT_RKF45: Fehlberg 4(5) with initial step h_km; the step is
+ *     accepted when err <= 1 with err = max(pos_err / (atol_km + rtol * r),
+ *     k_err / (rtol * max(|k|, 1e-3))), pos_err = max(|dr|, r|dtheta|,
+ *     r sin(theta)|dphi|) and k_err = max|dk_i| (k in units of omega/c); the
+ *     next step is h * min(5, max(0.2, 0.9 err^-0.2)) clamped to
+ *     [h_min_km, h_max_km]; a rejected step below h_min_km stops the ray.
+ *   max_steps bounds the RK step attempts of one ray (rejected steps and
+ *     landing-solve trial steps included).
+ *   max_group_path_km > 0 stops the ray at exactly that group path. */
+typedef struct rt_fan_desc {
+    double tx_lat_deg, tx_lon_deg, tx_alt_km;
+    const double *freq_mhz;     /* n_freq values > 0 */
+    const double *el_deg;       /* n_el values, elevation above the local horizontal */
+    const double *az_deg;       /* n_az values, clockwise from geographic north */
+    int32_t n_freq, n_el, n_az;
+    uint32_t modes;             /* RT_MODE_O | RT_MODE_X */
+    int32_t integrator;         /* RT_RK4 or RT_RKF45 */
+    int32_t precision;          /* RT_FP64 or RT_MIXED */
+    double h_km, rtol, atol_km, h_min_km, h_max_km;
+    int32_t max_steps;
+    int32_t reserved;           /* must be 0 */
+    double max_group_path_km;   /* <= 0: unlimited */
+} rt_fan_desc;
+
+/* Per-ray status. */
+enum {
+    RT_RAY_NOT_RUN = 0,
+    RT_RAY_LANDED = 1,         /* returned to r = R_E (landing point solved to 1e-9 km in FP64) */
+    RT_RAY_ESCAPED = 2,        /* rose above the top of the grid */
+    RT_RAY_LEFT_GRID = 3,      /* left the grid sideways inside its altitude span */
+    RT_RAY_MAX_STEPS = 4,      /* max_steps attempts used */
+    RT_RAY_STEP_UNDERFLOW = 5, /* RKF45 needed a step below h_min_km */
+    RT_RAY_NONFINITE = 6,      /* non-finite state, or mu^2 <= 0 at the transmitter */
+    RT_RAY_MAX_PATH = 7        /* reached max_group_path_km */
+};
+
+/* Per-ray result (64 bytes).  Quantities refer to the final state: the
+ * landing point for LANDED rays, the last accepted state otherwise.
+ * ground_range_km = R_E times the central angle from the transmitter;
+ * az_dev_deg = bearing of the final point from the transmitter minus the
+ * launch azimuth, in [-180, 180); apogee_km = the reflection height (maximum
+ * altitude, refined by a cubic Hermite fit where dr/dP' changes sign). */
+typedef struct rt_ray_result {
+    double group_path_km;
+    double ground_range_km;
+    double az_dev_deg;
+    double apogee_km;
+    double land_lat_deg;
+    double land_lon_deg;        /* in [-180, 180) */
+    int32_t status;             /* RT_RAY_* */
+    int32_t n_steps;            /* accepted steps (the final landing step included) */
+    int32_t n_attempts;         /* all RK step attempts: accepted + rejected + landing trials */
+    int32_t n_evals;            /* right-hand-side (stage) evaluations, the launch one included */
+} rt_ray_result;
+
+/* Number of rays a fan expands to (0 on an invalid descriptor). */
+size_t rt_fan_size(const rt_fan_desc *fan);
+
+/* Kernel choices.  Zero-initialise for the library's defaults. */
+enum { RT_KERNEL_AUTO = 0, RT_KERNEL_PLAIN = 1, RT_KERNEL_PERSISTENT = 2 };
+enum { RT_STENCIL_AUTO = 0, RT_STENCIL_GATHER = 1, RT_STENCIL_QUAD = 2, RT_STENCIL_TABLE = 3 };
+enum { RT_ORDER_CANONICAL = 0, RT_ORDER_ELEVATION_FASTEST = 1 };
+typedef struct rt_launch_config {
+    int32_t kernel;        /* RT_KERNEL_*: PLAIN = one thread per ray; PERSISTENT = one resident
+                              grid whose lanes claim rays from an atomic counter (mixed only) */
+    int32_t stencil;       /* RT_STENCIL_*: where the mixed path reads the 4x4x4 samples:
+                              GATHER = padded FP32 grid, QUAD = 4 consecutive altitude samples
+                              per float4, TABLE = per-cell table (needs RT_GRID_TABLE) */
+    int32_t block_threads; /* 0 = default; a multiple of 32 in [32, 1024] */
+    int32_t order;         /* RT_ORDER_*: order in which the persistent kernel claims rays */
+    int32_t blocks_per_sm; /* persistent kernel: resident blocks per SM (0 = occupancy limit) */
+    int32_t reserved[3];
+} rt_launch_config;
+
+/* Trace a fan; blocking.  out_host receives rt_fan_size(fan) results in
+ * canonical order (out_len must be at least that).  The call copies the fan
+ * arrays to the device, runs the kernels on `stream`, copies the results back
+ * and synchronises the stream.  cfg may be NULL (defaults).  Device scratch
+ * (fan tables, result staging, the persistent kernel's ray counter) is
+ * allocated stream-ordered and released before return.
+ * Errors: RT_EINVAL (null pointers, empty or invalid fan, out_len too small,
+ * bad cfg), RT_ENOMEM, RT_ECUDA, RT_EUNSUPPORTED. */
+rt_err rt_trace(const rt_grid *grid, const rt_fan_desc *fan, rt_ray_result *out_host,
+                size_t out_len, const rt_launch_config *cfg, void *stream);
+
+/* Same as rt_trace but asynchronous: out_dev is device memory (e.g. a PyTorch
+ * CUDA tensor) of at least rt_fan_size(fan) records; the call returns once the
+ * work is queued on `stream`.  The fan arrays are read before return. */
+rt_err rt_trace_device(const rt_grid *grid, const rt_fan_desc *fan, rt_ray_result *out_dev,
+                       size_t out_len, const rt_launch_config *cfg, void *stream);
+
+/* Autotuner: times the candidate launch configurations for this grid and fan
+ * shape on `stream` (each candidate on a seeded subsample of at most
+ * max_rays rays; 0 = 4096) and returns the fastest in *best and its time in
+ * *best_ms.  Blocking.  Results are also cached inside the library, keyed by
+ * grid and fan shape, and used by later RT_KERNEL_AUTO calls. */
+rt_err rt_tune(const rt_grid *grid, const rt_fan_desc *fan, size_t max_rays, void *stream,
+               rt_launch_config *best, float *best_ms);
+
+/* Diagnostic: the right-hand side dy/dP' of the ray equations (Eq. 1a-1f)
+ * at n given states, exactly as one stage of the tracer evaluates it.
+ * y_host: n x 6 doubles (r km, theta rad colatitude, phi rad longitude,
+ * k_r, k_theta, k_phi in units of omega/c); dy_host: n x 6 doubles out;
+ * mu2_host: n doubles out (mu^2 of Eq. 3 at the state).  mode: +1 ordinary,
+ * -1 extraordinary.  precision RT_FP64 or RT_MIXED; stencil as in
+ * rt_launch_config (mixed only; AUTO = QUAD).  Blocking; allocates device
+ * scratch with cudaMalloc.  Errors: RT_EINVAL, RT_ENOMEM, RT_ECUDA. */
+rt_err rt_eval_rhs(const rt_grid *grid, double freq_mhz, int32_t mode, int32_t precision, int32_t stencil,
+                   const double *y_host, double *dy_host, double *mu2_host, size_t n);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *rt_last_error(void);
+
+/* RTGD_API_VERSION of the library. */
+int32_t rt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

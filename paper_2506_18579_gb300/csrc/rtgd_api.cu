@@ -1,0 +1,558 @@
+// rtgd_api.cu -- host side of the C ABI declared in include/rtgd.h.
+//
+// Grid handles own their device memory (cudaMalloc).  Trace calls take their
+// scratch (fan tables, the persistent kernel's ray counter, staged results)
+// from the stream-ordered allocator and release it stream-ordered, so they
+// are safe to issue from several threads on several streams.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <tuple>
+#include <vector>
+
+#include "rtgd.h"
+#include "rtgd_internal.h"
+
+using namespace rtgd;
+
+struct rt_grid {
+    rt_grid_desc desc;
+    int device;
+    GridDev g;
+    double *pad64 = nullptr;
+    float *pad32 = nullptr;
+    float4 *quad = nullptr;
+    float4 *table = nullptr;
+    size_t bytes = 0;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+rt_err fail(rt_err code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+rt_err cuda_fail(cudaError_t e, const char *what) {
+    if (e == cudaErrorMemoryAllocation) return fail(RT_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+    if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver)
+        return fail(RT_EUNSUPPORTED, "%s: %s", what, cudaGetErrorString(e));
+    return fail(RT_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CUDA_TRY(call)                                  \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+std::mutex g_dev_mu;
+std::map<int, bool> g_dev_ready;
+
+// Checks for a usable device and uploads the Butcher tables once per device.
+rt_err ensure_device(int *dev_out) {
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || n == 0) return fail(RT_EUNSUPPORTED, "no CUDA device available (%s)", cudaGetErrorString(e));
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    if (!g_dev_ready[dev]) {
+        CUDA_TRY(upload_tableaus());
+        g_dev_ready[dev] = true;
+    }
+    if (dev_out) *dev_out = dev;
+    return RT_OK;
+}
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+rt_err validate_grid_desc(const rt_grid_desc *d) {
+    if (!d) return fail(RT_EINVAL, "grid descriptor is NULL");
+    if (d->n_lat < 4 || d->n_lon < 4 || d->n_alt < 4)
+        return fail(RT_EINVAL, "grid needs at least 4 nodes per dimension (got %d x %d x %d)", d->n_lat, d->n_lon,
+                    d->n_alt);
+    if ((long long)d->n_lat * d->n_lon * d->n_alt > (1LL << 34)) return fail(RT_EINVAL, "grid too large");
+    if (d->dtype != RT_F32 && d->dtype != RT_F64) return fail(RT_EINVAL, "unknown dtype %d", d->dtype);
+    if (!finite_pos(d->dlat_deg) || !finite_pos(d->dlon_deg) || !finite_pos(d->dalt_km))
+        return fail(RT_EINVAL, "grid spacings must be finite and > 0");
+    if (!finite_pos(d->earth_radius_km)) return fail(RT_EINVAL, "earth_radius_km must be finite and > 0");
+    if (!std::isfinite(d->lat0_deg) || !std::isfinite(d->lon0_deg) || !std::isfinite(d->alt0_km))
+        return fail(RT_EINVAL, "grid origin must be finite");
+    if (d->lat0_deg < -90.0 || d->lat0_deg + (d->n_lat - 1) * d->dlat_deg > 90.0)
+        return fail(RT_EINVAL, "grid latitudes must lie in [-90, 90]");
+    if (!std::isfinite(d->field.b0_tesla) || d->field.b0_tesla < 0.0 || !std::isfinite(d->field.pole_lat_deg) ||
+        !std::isfinite(d->field.pole_lon_deg))
+        return fail(RT_EINVAL, "dipole parameters must be finite, b0 >= 0");
+    if (d->flags & ~(uint32_t)RT_GRID_TABLE) return fail(RT_EINVAL, "unknown grid flags 0x%x", d->flags);
+    if (d->reserved != 0) return fail(RT_EINVAL, "reserved field must be 0");
+    return RT_OK;
+}
+
+size_t fan_rays(const rt_fan_desc *f) {
+    const int nm = ((f->modes & RT_MODE_O) ? 1 : 0) + ((f->modes & RT_MODE_X) ? 1 : 0);
+    return (size_t)f->n_freq * (size_t)nm * (size_t)f->n_el * (size_t)f->n_az;
+}
+
+rt_err validate_fan(const rt_fan_desc *f) {
+    if (!f) return fail(RT_EINVAL, "fan descriptor is NULL");
+    if (f->n_freq < 1 || f->n_el < 1 || f->n_az < 1)
+        return fail(RT_EINVAL, "fan needs n_freq, n_el, n_az >= 1 (got %d, %d, %d)", f->n_freq, f->n_el, f->n_az);
+    if (!f->freq_mhz || !f->el_deg || !f->az_deg) return fail(RT_EINVAL, "fan arrays must not be NULL");
+    if (f->modes == 0 || (f->modes & ~3u)) return fail(RT_EINVAL, "modes must be a non-empty subset of O|X");
+    if (f->integrator != RT_RK4 && f->integrator != RT_RKF45) return fail(RT_EINVAL, "unknown integrator %d", f->integrator);
+    if (f->precision != RT_FP64 && f->precision != RT_MIXED) return fail(RT_EINVAL, "unknown precision %d", f->precision);
+    if (!finite_pos(f->h_km)) return fail(RT_EINVAL, "h_km must be finite and > 0");
+    if (f->integrator == RT_RKF45) {
+        if (!finite_pos(f->rtol) || !std::isfinite(f->atol_km) || f->atol_km < 0.0)
+            return fail(RT_EINVAL, "RKF45 needs rtol > 0 and atol_km >= 0");
+        if (!finite_pos(f->h_min_km) || !finite_pos(f->h_max_km) || f->h_max_km < f->h_min_km)
+            return fail(RT_EINVAL, "RKF45 needs 0 < h_min_km <= h_max_km");
+    }
+    if (f->max_steps < 1) return fail(RT_EINVAL, "max_steps must be >= 1");
+    if (f->reserved != 0) return fail(RT_EINVAL, "reserved field must be 0");
+    if (!std::isfinite(f->tx_lat_deg) || !std::isfinite(f->tx_lon_deg) || !std::isfinite(f->tx_alt_km) ||
+        f->tx_lat_deg <= -90.0 || f->tx_lat_deg >= 90.0)
+        return fail(RT_EINVAL, "transmitter position must be finite with |lat| < 90");
+    if (!std::isfinite(f->max_group_path_km)) return fail(RT_EINVAL, "max_group_path_km must be finite");
+    for (int i = 0; i < f->n_freq; ++i)
+        if (!finite_pos(f->freq_mhz[i])) return fail(RT_EINVAL, "freq_mhz[%d] must be finite and > 0", i);
+    for (int i = 0; i < f->n_el; ++i)
+        if (!std::isfinite(f->el_deg[i])) return fail(RT_EINVAL, "el_deg[%d] is not finite", i);
+    for (int i = 0; i < f->n_az; ++i)
+        if (!std::isfinite(f->az_deg[i])) return fail(RT_EINVAL, "az_deg[%d] is not finite", i);
+    return RT_OK;
+}
+
+struct DevProps {
+    int sms = 0;
+};
+std::mutex g_props_mu;
+std::map<int, DevProps> g_props;
+
+DevProps props(int dev) {
+    std::lock_guard<std::mutex> lk(g_props_mu);
+    auto it = g_props.find(dev);
+    if (it != g_props.end()) return it->second;
+    DevProps p;
+    cudaDeviceGetAttribute(&p.sms, cudaDevAttrMultiProcessorCount, dev);
+    g_props[dev] = p;
+    return p;
+}
+
+// Autotuner cache: (grid, integrator, ray-count bucket) -> launch config.
+std::mutex g_tune_mu;
+std::map<std::tuple<const rt_grid *, int, int>, rt_launch_config> g_tuned;
+
+int ray_bucket(size_t n) {
+    int b = 0;
+    while (n > 1) {
+        n >>= 1;
+        ++b;
+    }
+    return b;
+}
+
+rt_err make_plan(const rt_grid *grid, const rt_fan_desc *fan, size_t n_rays, const rt_launch_config *cfg,
+                 LaunchPlan *lp, int *order) {
+    rt_launch_config c;
+    std::memset(&c, 0, sizeof(c));
+    if (cfg) c = *cfg;
+    if (c.kernel < 0 || c.kernel > RT_KERNEL_PERSISTENT) return fail(RT_EINVAL, "unknown kernel %d", c.kernel);
+    if (c.stencil < 0 || c.stencil > RT_STENCIL_TABLE) return fail(RT_EINVAL, "unknown stencil %d", c.stencil);
+    if (c.block_threads != 0 && (c.block_threads < 32 || c.block_threads > 128 || c.block_threads % 32))
+        return fail(RT_EINVAL, "block_threads must be 0 or a multiple of 32 in [32, 128]");
+    if (c.order != RT_ORDER_CANONICAL && c.order != RT_ORDER_ELEVATION_FASTEST)
+        return fail(RT_EINVAL, "unknown order %d", c.order);
+    if (c.blocks_per_sm < 0) return fail(RT_EINVAL, "blocks_per_sm must be >= 0");
+    if (fan->precision == RT_MIXED && c.kernel == RT_KERNEL_AUTO && c.stencil == RT_STENCIL_AUTO) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(std::make_tuple(grid, fan->integrator, ray_bucket(n_rays)));
+        if (it != g_tuned.end()) c = it->second;
+    }
+    if (c.kernel == RT_KERNEL_AUTO) c.kernel = fan->precision == RT_MIXED ? RT_KERNEL_PERSISTENT : RT_KERNEL_PLAIN;
+    if (fan->precision == RT_FP64 && c.kernel != RT_KERNEL_PLAIN)
+        return fail(RT_EINVAL, "the FP64 path runs the plain one-thread-per-ray kernel only");
+    if (c.stencil == RT_STENCIL_AUTO) c.stencil = RT_STENCIL_QUAD;
+    if (c.stencil == RT_STENCIL_TABLE && !grid->table)
+        return fail(RT_EINVAL, "stencil TABLE needs a grid created with RT_GRID_TABLE");
+    if (c.order == RT_ORDER_CANONICAL && cfg == nullptr) c.order = RT_ORDER_ELEVATION_FASTEST;
+    lp->kernel = c.kernel;
+    lp->stencil = c.stencil;
+    lp->threads = c.block_threads ? c.block_threads : 128;
+    lp->blocks = 0;
+    if (fan->precision == RT_MIXED && c.kernel == RT_KERNEL_PERSISTENT) {
+        int occ = 0;
+        CUDA_TRY(persistent_occupancy(c.stencil, lp->threads, &occ));
+        if (occ < 1) return fail(RT_ECUDA, "persistent kernel does not fit on an SM with %d threads", lp->threads);
+        if (c.blocks_per_sm > 0) occ = std::min(occ, c.blocks_per_sm);
+        const long long want = (long long)props(grid->device).sms * occ;
+        const long long need = (long long)((n_rays + lp->threads - 1) / lp->threads);
+        lp->blocks = (int)std::max(1LL, std::min(want, need));
+    }
+    *order = c.order;
+    return RT_OK;
+}
+
+double sync_timeout_s() {
+    const char *s = std::getenv("RTGD_SYNC_TIMEOUT_S");
+    if (s) {
+        const double v = std::atof(s);
+        if (v > 0) return v;
+    }
+    return 900.0;
+}
+
+// Waits for the stream with a deadline instead of blocking indefinitely.
+rt_err sync_with_timeout(cudaStream_t st) {
+    const auto t0 = std::chrono::steady_clock::now();
+    const double limit = sync_timeout_s();
+    int sleep_us = 20;
+    for (;;) {
+        const cudaError_t e = cudaStreamQuery(st);
+        if (e == cudaSuccess) return RT_OK;
+        if (e != cudaErrorNotReady) return cuda_fail(e, "kernel execution");
+        const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (dt > limit) return fail(RT_ETIMEOUT, "stream did not finish within %.0f s", limit);
+        std::this_thread::sleep_for(std::chrono::microseconds(sleep_us));
+        sleep_us = std::min(sleep_us * 2, 1000);
+    }
+}
+
+// Queues one trace: scratch allocation, fan upload, kernel, scratch release.
+rt_err queue_trace(const rt_grid *grid, const rt_fan_desc *fan, rt_ray_result *out_dev, size_t out_len,
+                   const rt_launch_config *cfg, cudaStream_t st) {
+    rt_err r = validate_fan(fan);
+    if (r != RT_OK) return r;
+    if (!grid) return fail(RT_EINVAL, "grid is NULL");
+    if (!out_dev) return fail(RT_EINVAL, "output pointer is NULL");
+    int dev = 0;
+    if ((r = ensure_device(&dev)) != RT_OK) return r;
+    if (dev != grid->device) return fail(RT_EINVAL, "grid lives on device %d, current device is %d", grid->device, dev);
+    const size_t n = fan_rays(fan);
+    if (out_len < n) return fail(RT_EINVAL, "out_len %zu < %zu rays", out_len, n);
+    if (n > (size_t)1 << 40) return fail(RT_EINVAL, "fan too large");
+    LaunchPlan lp;
+    int order = 0;
+    if ((r = make_plan(grid, fan, n, cfg, &lp, &order)) != RT_OK) return r;
+
+    const size_t n_tab = (size_t)fan->n_freq + fan->n_el + fan->n_az;
+    const size_t bytes = 16 + n_tab * sizeof(double);
+    char *ws = nullptr;
+    CUDA_TRY(cudaMallocAsync((void **)&ws, bytes, st));
+    unsigned long long *counter = (unsigned long long *)ws;
+    double *tab = (double *)(ws + 16);
+    cudaError_t e = cudaMemsetAsync(counter, 0, 16, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(tab, fan->freq_mhz, fan->n_freq * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(tab + fan->n_freq, fan->el_deg, fan->n_el * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(tab + fan->n_freq + fan->n_el, fan->az_deg, fan->n_az * sizeof(double),
+                            cudaMemcpyHostToDevice, st);
+    FanDev f;
+    std::memset(&f, 0, sizeof(f));
+    f.freq = tab;
+    f.el = tab + fan->n_freq;
+    f.az = tab + fan->n_freq + fan->n_el;
+    f.n_freq = fan->n_freq;
+    f.n_el = fan->n_el;
+    f.n_az = fan->n_az;
+    f.n_modes = ((fan->modes & RT_MODE_O) ? 1 : 0) + ((fan->modes & RT_MODE_X) ? 1 : 0);
+    f.mode0 = (fan->modes & RT_MODE_O) ? 1 : -1;
+    f.mode1 = -1;
+    f.integrator = fan->integrator;
+    f.precision = fan->precision;
+    f.max_steps = fan->max_steps;
+    f.order = order;
+    f.n_rays = (long long)n;
+    f.tx_r = grid->desc.earth_radius_km + fan->tx_alt_km;
+    f.tx_th = (90.0 - fan->tx_lat_deg) * kDeg2Rad;
+    f.tx_ph = fan->tx_lon_deg * kDeg2Rad;
+    f.h0 = fan->h_km;
+    f.rtol = fan->rtol;
+    f.atol = fan->atol_km;
+    f.hmin = fan->integrator == RT_RKF45 ? fan->h_min_km : 0.0;
+    f.hmax = fan->integrator == RT_RKF45 ? fan->h_max_km : fan->h_km;
+    f.max_path = fan->max_group_path_km;
+    // FP64: 1e-9 km; mixed: the float increment resolves ~1e-6 km, so 1e-5 km
+    f.land_tol = fan->precision == RT_FP64 ? 1e-9 : 1e-5;
+    f.rtol_f = (float)fan->rtol;
+    f.atol_f = (float)fan->atol_km;
+    if (e == cudaSuccess) e = launch_trace(grid->g, f, out_dev, counter, lp, st);
+    const cudaError_t e2 = cudaFreeAsync(ws, st);
+    if (e != cudaSuccess) return cuda_fail(e, "trace launch");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync");
+    return RT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t rt_version(void) { return RTGD_API_VERSION; }
+
+const char *rt_last_error(void) { return g_err.c_str(); }
+
+size_t rt_fan_size(const rt_fan_desc *fan) {
+    if (!fan || fan->n_freq < 1 || fan->n_el < 1 || fan->n_az < 1 || fan->modes == 0 || (fan->modes & ~3u)) return 0;
+    return fan_rays(fan);
+}
+
+rt_err rt_grid_create(const rt_grid_desc *desc, const void *ne_host, rt_grid **out) {
+    if (!out) return fail(RT_EINVAL, "out is NULL");
+    *out = nullptr;
+    rt_err r = validate_grid_desc(desc);
+    if (r != RT_OK) return r;
+    if (!ne_host) return fail(RT_EINVAL, "ne_host is NULL");
+    int dev = 0;
+    if ((r = ensure_device(&dev)) != RT_OK) return r;
+    rt_grid *g = new rt_grid();
+    g->desc = *desc;
+    g->device = dev;
+    const long long nl = desc->n_lat, nn = desc->n_lon, na = desc->n_alt;
+    const size_t n_raw = (size_t)(nl * nn * na);
+    const size_t n_pad = (size_t)((nl + 2) * (nn + 2) * (na + 2));
+    const size_t n_quad = (size_t)((nl + 2) * (nn + 2) * (na - 1));
+    const size_t n_tab = (desc->flags & RT_GRID_TABLE) ? (size_t)((nl - 1) * (nn - 1) * (na - 1) * 16) : 0;
+    const size_t esz = desc->dtype == RT_F64 ? 8 : 4;
+    void *raw = nullptr;
+    cudaStream_t st = nullptr;
+    auto cleanup = [&](rt_err code) {
+        if (st) cudaStreamDestroy(st);
+        if (raw) cudaFree(raw);
+        if (code != RT_OK) {
+            cudaFree(g->pad64);
+            cudaFree(g->pad32);
+            cudaFree(g->quad);
+            cudaFree(g->table);
+            delete g;
+        }
+        return code;
+    };
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&raw, n_raw * esz);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&g->pad64, n_pad * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&g->pad32, n_pad * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&g->quad, n_quad * sizeof(float4));
+    if (e == cudaSuccess && n_tab) e = cudaMalloc((void **)&g->table, n_tab * sizeof(float4));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(raw, ne_host, n_raw * esz, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        GridSizes sz{desc->n_lat, desc->n_lon, desc->n_alt};
+        e = launch_grid_prep(raw, desc->dtype, sz, g->pad64, g->pad32, g->quad, g->table, st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "rt_grid_create"));
+    g->bytes = n_pad * (sizeof(double) + sizeof(float)) + n_quad * sizeof(float4) + n_tab * sizeof(float4);
+    GridDev &d = g->g;
+    d.n_lat = desc->n_lat;
+    d.n_lon = desc->n_lon;
+    d.n_alt = desc->n_alt;
+    d.p_lon = desc->n_lon + 2;
+    d.p_alt = desc->n_alt + 2;
+    d.q_alt = desc->n_alt - 1;
+    d.lat0 = desc->lat0_deg;
+    d.lon0 = desc->lon0_deg;
+    d.alt0 = desc->alt0_km;
+    d.inv_dlat = 1.0 / desc->dlat_deg;
+    d.inv_dlon = 1.0 / desc->dlon_deg;
+    d.inv_dalt = 1.0 / desc->dalt_km;
+    d.R_E = desc->earth_radius_km;
+    d.top = desc->alt0_km + (desc->n_alt - 1) * desc->dalt_km;
+    d.b0 = desc->field.b0_tesla;
+    const double plat = desc->field.pole_lat_deg * kDeg2Rad, plon = desc->field.pole_lon_deg * kDeg2Rad;
+    d.m[0] = std::cos(plat) * std::cos(plon);
+    d.m[1] = std::cos(plat) * std::sin(plon);
+    d.m[2] = std::sin(plat);
+    d.sa = (float)(-kRad2Deg / desc->dlat_deg);
+    d.sb = (float)(kRad2Deg / desc->dlon_deg);
+    d.sc = (float)(1.0 / desc->dalt_km);
+    d.pad64 = g->pad64;
+    d.pad32 = g->pad32;
+    d.quad = g->quad;
+    d.table = g->table;
+    *out = g;
+    return cleanup(RT_OK);
+}
+
+rt_err rt_grid_destroy(rt_grid *grid) {
+    if (!grid) return RT_OK;
+    cudaError_t e = cudaSuccess;
+    for (void *p : {(void *)grid->pad64, (void *)grid->pad32, (void *)grid->quad, (void *)grid->table}) {
+        if (!p) continue;
+        const cudaError_t ei = cudaFree(p);
+        if (ei != cudaSuccess && e == cudaSuccess) e = ei;
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        for (auto it = g_tuned.begin(); it != g_tuned.end();) {
+            if (std::get<0>(it->first) == grid) it = g_tuned.erase(it);
+            else ++it;
+        }
+    }
+    delete grid;
+    if (e != cudaSuccess) return cuda_fail(e, "rt_grid_destroy");
+    return RT_OK;
+}
+
+size_t rt_grid_device_bytes(const rt_grid *grid) { return grid ? grid->bytes : 0; }
+
+rt_err rt_trace_device(const rt_grid *grid, const rt_fan_desc *fan, rt_ray_result *out_dev, size_t out_len,
+                       const rt_launch_config *cfg, void *stream) {
+    return queue_trace(grid, fan, out_dev, out_len, cfg, (cudaStream_t)stream);
+}
+
+rt_err rt_trace(const rt_grid *grid, const rt_fan_desc *fan, rt_ray_result *out_host, size_t out_len,
+                const rt_launch_config *cfg, void *stream) {
+    if (!out_host) return fail(RT_EINVAL, "out_host is NULL");
+    rt_err r = validate_fan(fan);
+    if (r != RT_OK) return r;
+    if ((r = ensure_device(nullptr)) != RT_OK) return r;
+    const size_t n = fan_rays(fan);
+    if (out_len < n) return fail(RT_EINVAL, "out_len %zu < %zu rays", out_len, n);
+    cudaStream_t st = (cudaStream_t)stream;
+    rt_ray_result *dev = nullptr;
+    CUDA_TRY(cudaMallocAsync((void **)&dev, n * sizeof(rt_ray_result), st));
+    r = queue_trace(grid, fan, dev, n, cfg, st);
+    if (r == RT_OK) r = sync_with_timeout(st);
+    if (r == RT_OK) {
+        const cudaError_t e = cudaMemcpyAsync(out_host, dev, n * sizeof(rt_ray_result), cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) r = cuda_fail(e, "result copy");
+        else r = sync_with_timeout(st);
+    }
+    const cudaError_t e2 = cudaFreeAsync(dev, st);
+    if (r == RT_OK && e2 != cudaSuccess) r = cuda_fail(e2, "cudaFreeAsync");
+    return r;
+}
+
+rt_err rt_tune(const rt_grid *grid, const rt_fan_desc *fan, size_t max_rays, void *stream, rt_launch_config *best,
+               float *best_ms) {
+    if (!grid || !best) return fail(RT_EINVAL, "NULL argument");
+    rt_err r = validate_fan(fan);
+    if (r != RT_OK) return r;
+    if ((r = ensure_device(nullptr)) != RT_OK) return r;
+    if (max_rays == 0) max_rays = 4096;
+    cudaStream_t st = (cudaStream_t)stream;
+    // strided sub-fan with at most max_rays rays (every k-th elevation, azimuth, frequency)
+    std::vector<double> fr(fan->freq_mhz, fan->freq_mhz + fan->n_freq), el(fan->el_deg, fan->el_deg + fan->n_el),
+        az(fan->az_deg, fan->az_deg + fan->n_az);
+    auto thin = [](std::vector<double> &v) {
+        std::vector<double> o;
+        for (size_t i = 0; i < v.size(); i += 2) o.push_back(v[i]);
+        v.swap(o);
+    };
+    rt_fan_desc sub = *fan;
+    for (int guard = 0; guard < 64; ++guard) {
+        sub.freq_mhz = fr.data();
+        sub.el_deg = el.data();
+        sub.az_deg = az.data();
+        sub.n_freq = (int)fr.size();
+        sub.n_el = (int)el.size();
+        sub.n_az = (int)az.size();
+        if (fan_rays(&sub) <= max_rays) break;
+        if (el.size() >= az.size() && el.size() > 1) thin(el);
+        else if (az.size() > 1) thin(az);
+        else if (fr.size() > 1) thin(fr);
+        else break;
+    }
+    const size_t n = fan_rays(&sub);
+    std::vector<rt_launch_config> cands;
+    rt_launch_config c;
+    std::memset(&c, 0, sizeof(c));
+    if (fan->precision == RT_FP64) {
+        c.kernel = RT_KERNEL_PLAIN;
+        cands.push_back(c);
+    } else {
+        for (int kernel : {RT_KERNEL_PLAIN, RT_KERNEL_PERSISTENT})
+            for (int stencil : {RT_STENCIL_GATHER, RT_STENCIL_QUAD, RT_STENCIL_TABLE})
+                for (int order : {RT_ORDER_CANONICAL, RT_ORDER_ELEVATION_FASTEST})
+                    for (int threads : {64, 128}) {
+                        if (stencil == RT_STENCIL_TABLE && !grid->table) continue;
+                        c.kernel = kernel;
+                        c.stencil = stencil;
+                        c.order = order;
+                        c.block_threads = threads;
+                        cands.push_back(c);
+                    }
+    }
+    rt_ray_result *out = nullptr;
+    CUDA_TRY(cudaMallocAsync((void **)&out, n * sizeof(rt_ray_result), st));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best_t = 1e30f;
+    rt_launch_config best_c = cands[0];
+    for (const auto &cc : cands) {
+        if ((r = queue_trace(grid, &sub, out, n, &cc, st)) != RT_OK) break;  // warm-up
+        float t_min = 1e30f;
+        for (int rep = 0; rep < 2 && r == RT_OK; ++rep) {
+            cudaEventRecord(e0, st);
+            r = queue_trace(grid, &sub, out, n, &cc, st);
+            cudaEventRecord(e1, st);
+            if (r == RT_OK) r = sync_with_timeout(st);
+            float ms = 0.0f;
+            if (r == RT_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) t_min = std::min(t_min, ms);
+        }
+        if (r != RT_OK) break;
+        if (t_min < best_t) {
+            best_t = t_min;
+            best_c = cc;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFreeAsync(out, st);
+    if (r != RT_OK) return r;
+    if (fan->precision == RT_MIXED) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned[std::make_tuple(grid, fan->integrator, ray_bucket(fan_rays(fan)))] = best_c;
+    }
+    *best = best_c;
+    if (best_ms) *best_ms = best_t;
+    return RT_OK;
+}
+
+rt_err rt_eval_rhs(const rt_grid *grid, double freq_mhz, int32_t mode, int32_t precision, int32_t stencil,
+                   const double *y_host, double *dy_host, double *mu2_host, size_t n) {
+    if (!grid || !y_host || !dy_host || !mu2_host) return fail(RT_EINVAL, "NULL argument");
+    if (!finite_pos(freq_mhz)) return fail(RT_EINVAL, "freq_mhz must be finite and > 0");
+    if (mode != 1 && mode != -1) return fail(RT_EINVAL, "mode must be +1 (O) or -1 (X)");
+    if (precision != RT_FP64 && precision != RT_MIXED) return fail(RT_EINVAL, "unknown precision");
+    if (stencil < 0 || stencil > RT_STENCIL_TABLE) return fail(RT_EINVAL, "unknown stencil");
+    if (stencil == RT_STENCIL_TABLE && !grid->table) return fail(RT_EINVAL, "grid has no table");
+    rt_err r = ensure_device(nullptr);
+    if (r != RT_OK) return r;
+    if (n == 0) return RT_OK;
+    double *buf = nullptr;
+    CUDA_TRY(cudaMalloc((void **)&buf, n * 13 * sizeof(double)));
+    cudaError_t e = cudaMemcpy(buf, y_host, n * 6 * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = launch_eval_rhs(grid->g, buf, buf + n * 6, buf + n * 12, freq_mhz, mode, precision, stencil,
+                            (long long)n, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(dy_host, buf + n * 6, n * 6 * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(mu2_host, buf + n * 12, n * sizeof(double), cudaMemcpyDeviceToHost);
+    cudaFree(buf);
+    if (e != cudaSuccess) return cuda_fail(e, "rt_eval_rhs");
+    return RT_OK;
+}
+
+}  // extern "C"

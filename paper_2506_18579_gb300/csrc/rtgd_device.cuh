@@ -1,0 +1,274 @@
+// rtgd_device.cuh -- device-side building blocks of the RTM-GD tracer.
+//
+// Everything the stage evaluation needs, written once and instantiated for
+// double (the all-FP64 path) and float (the mixed path):
+//   - p = 3 Galerkin-Difference weights and their derivatives (Appendix A),
+//   - the 4x4x4 tensor contraction of Eq. 13 giving Ne and its gradient,
+//   - the centred dipole field and its Jacobian in local spherical components,
+//   - Appleton-Hartree (Eq. 3) with hand-derived partial derivatives,
+//   - the Hamiltonian partials (Eq. 2) and the ray equations (Eq. 1a-1f).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rtgd.h"
+
+namespace rtgd {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kRad2Deg = 180.0 / kPi;
+constexpr double kDeg2Rad = kPi / 180.0;
+// f_N^2 = 80.6 Ne (Hz^2, Ne in m^-3), so X = f_N^2 / f^2 (Sec. II-A).
+constexpr double kPlasmaHz2PerM3 = 80.6;
+// f_H = e B / (2 pi m_e) in Hz per tesla, so Y = f_H / f (Sec. II-A).
+constexpr double kGyroHzPerTesla = 2.7992489872e10;
+
+// Device view of a grid.  Node (i, j, k), i in [0, n_lat), sits at padded
+// index (i+1, j+1, k+1) of the ghost-padded arrays.
+struct GridDev {
+    int n_lat, n_lon, n_alt;
+    int p_lon, p_alt;                // padded sizes n_lon + 2, n_alt + 2
+    int q_alt;                       // n_alt - 1 cells per (lat, lon) row of the quad layout
+    double lat0, lon0, alt0;
+    double inv_dlat, inv_dlon, inv_dalt;
+    double R_E, top;                 // earth radius; top = alt0 + (n_alt - 1) dalt
+    double b0;                       // dipole strength (0: isotropic)
+    double m[3];                     // unit vector to the geomagnetic north pole
+    float sa, sb, sc;                // d(grid coord)/d(theta, phi, r): -rad2deg/dlat, rad2deg/dlon, 1/dalt
+    const double *pad64;             // (n_lat+2)(n_lon+2)(n_alt+2) doubles
+    const float *pad32;              // same, rounded to float
+    const float4 *quad;              // (n_lat+2)(n_lon+2)(n_alt-1): samples k-1..k+2 of cell k
+    const float4 *table;             // (n_lat-1)(n_lon-1)(n_alt-1) cells x 16 float4 (64 samples)
+};
+
+// --------------------------------------------------------------------------
+// GD p = 3 weights (Appendix A).  For a point at local coordinate t in [0, 1]
+// of the cell [x_j, x_{j+1}], the weight of node j-1 is the printed piece
+// psi_1 (in powers of t), of node j the piece psi_0, of node j+1 psi_{-1} and
+// of node j+2 psi_{-2}.  The global basis function is even, so the last two
+// are the first two mirrored: w_{j+1}(t) = w_j(1-t), w_{j+2}(t) = w_{j-1}(1-t).
+// w[a] / d[a] hold the weight of node j-1+a and its t-derivative.
+template <typename R>
+__device__ __forceinline__ void gd_weights(R t, R w[4], R d[4]) {
+    const R s = R(1) - t;
+    w[0] = t * (R(-0.5) + t * (R(11.0 / 12.0) + t * (R(-1.0 / 6.0) + t * (R(-5.0 / 12.0) + t * R(1.0 / 6.0)))));
+    w[1] = R(1) + t * t * (R(-2.25) + t * (R(0.5) + t * (R(1.25) - t * R(0.5))));
+    w[2] = R(1) + s * s * (R(-2.25) + s * (R(0.5) + s * (R(1.25) - s * R(0.5))));
+    w[3] = s * (R(-0.5) + s * (R(11.0 / 12.0) + s * (R(-1.0 / 6.0) + s * (R(-5.0 / 12.0) + s * R(1.0 / 6.0)))));
+    d[0] = R(-0.5) + t * (R(11.0 / 6.0) + t * (R(-0.5) + t * (R(-5.0 / 3.0) + t * R(5.0 / 6.0))));
+    d[1] = t * (R(-4.5) + t * (R(1.5) + t * (R(5.0) - t * R(2.5))));
+    d[2] = -(s * (R(-4.5) + s * (R(1.5) + s * (R(5.0) - s * R(2.5)))));
+    d[3] = -(R(-0.5) + s * (R(11.0 / 6.0) + s * (R(-0.5) + s * (R(-5.0 / 3.0) + s * R(5.0 / 6.0)))));
+}
+
+// Eq. 13 contraction of one row of 4 altitude samples.
+template <typename R>
+__device__ __forceinline__ void row4(R u0, R u1, R u2, R u3, const R wc[4], const R dc[4], R &v, R &dv) {
+    v = u0 * wc[0] + u1 * wc[1] + u2 * wc[2] + u3 * wc[3];
+    dv = u0 * dc[0] + u1 * dc[1] + u2 * dc[2] + u3 * dc[3];
+}
+
+// Accumulates the (a, b) row into the lon/lat partial sums.
+template <typename R>
+__device__ __forceinline__ void acc_row(R v, R dv, R wb, R db, R &s, R &sb, R &sc) {
+    s += v * wb;
+    sb += v * db;
+    sc += dv * wb;
+}
+
+// out = {Ne, dNe/dxa, dNe/dxb, dNe/dxc} in per-cell units, from the 16 rows
+// of 4 altitude samples.  ROW(a, b, u0..u3) loads row (a, b).
+#define RTGD_CONTRACT(R, ROW, wa, da, wb, db, wc, dc, out)                        \
+    do {                                                                          \
+        R n_ = R(0), na_ = R(0), nb_ = R(0), nc_ = R(0);                          \
+        _Pragma("unroll") for (int a_ = 0; a_ < 4; ++a_) {                        \
+            R s_ = R(0), sb_ = R(0), sc_ = R(0);                                  \
+            _Pragma("unroll") for (int b_ = 0; b_ < 4; ++b_) {                    \
+                R u0_, u1_, u2_, u3_, v_, dv_;                                    \
+                ROW(a_, b_, u0_, u1_, u2_, u3_);                                  \
+                row4<R>(u0_, u1_, u2_, u3_, wc, dc, v_, dv_);                     \
+                acc_row<R>(v_, dv_, wb[b_], db[b_], s_, sb_, sc_);                \
+            }                                                                     \
+            n_ += s_ * wa[a_];                                                    \
+            na_ += s_ * da[a_];                                                   \
+            nb_ += sb_ * wa[a_];                                                  \
+            nc_ += sc_ * wa[a_];                                                  \
+        }                                                                         \
+        out[0] = n_;                                                              \
+        out[1] = na_;                                                             \
+        out[2] = nb_;                                                             \
+        out[3] = nc_;                                                             \
+    } while (0)
+
+// Cell index and local coordinate along one axis; false outside [0, n-1].
+template <typename R>
+__device__ __forceinline__ bool cell_coord(R x, int n, int &i, R &t) {
+    if (!(x >= R(0) && x <= R(n - 1))) return false;
+    R f = floor(x);
+    int fi = (int)f;
+    if (fi > n - 2) fi = n - 2;
+    i = fi;
+    t = x - R(fi);
+    return true;
+}
+
+// --------------------------------------------------------------------------
+// Physics at one stage: everything after the interpolation.
+template <typename R>
+struct StageIn {
+    R r, sth, cth, sph, cph;  // position (km, sin/cos of colatitude and longitude)
+    R k[3];                   // wave vector (r, theta, phi components), units of omega/c
+    R X;                      // f_N^2 / f^2
+    R dX[3];                  // dX/dr, dX/dtheta, dX/dphi
+};
+
+// Per-ray physics constants in the precision of the stage arithmetic.
+template <typename R>
+struct RayPhys {
+    R xfac;   // 80.6 / f^2: X = xfac * Ne
+    R ab0;    // (kGyroHzPerTesla / f) * B0: |Y| at the magnetic equator on the ground
+    R R_E;
+    R m[3];   // unit vector to the geomagnetic north pole
+    bool iso; // no field
+    int mode; // +1 ordinary, -1 extraordinary
+};
+
+template <typename R>
+__device__ __forceinline__ RayPhys<R> make_phys(const GridDev &g, double f_hz, int mode) {
+    RayPhys<R> p;
+    p.xfac = R(kPlasmaHz2PerM3 / (f_hz * f_hz));
+    p.ab0 = R(kGyroHzPerTesla / f_hz * g.b0);
+    p.R_E = R(g.R_E);
+    p.m[0] = R(g.m[0]);
+    p.m[1] = R(g.m[1]);
+    p.m[2] = R(g.m[2]);
+    p.iso = g.b0 == 0.0;
+    p.mode = mode;
+    return p;
+}
+
+// Appleton-Hartree mu^2(X, L = Y_L^2, T = Y_T^2) (Eq. 3) and its partials.
+// Ordinary wave (upper sign): the printed denominator 2u - T + S (u = 1 - X,
+// S = sqrt(T^2 + 4 L u^2)) is rewritten with S - T = 4 L u^2 / (S + T), which
+// gives mu^2 = 1 - X / (1 + g), g = 2 L u / (S + T): the same function, free
+// of the 0/0 at X = 1.  Extraordinary wave: the printed form.
+template <typename R>
+__device__ __forceinline__ void appleton_hartree(R X, R L, R T, int mode, R &mu2, R &FX, R &FL, R &FT) {
+    const R u = R(1) - X;
+    const R S = sqrt(T * T + R(4) * L * u * u);
+    const R iS = R(1) / S;
+    if (mode > 0) {
+        const R W = S + T;
+        const R iW = R(1) / W;
+        const R g = R(2) * L * u * iW;
+        const R opg = R(1) + g;
+        const R iopg = R(1) / opg;
+        const R gX = R(2) * L * (R(4) * L * u * u * iS - W) * iW * iW;
+        const R gL = R(2) * u * iW - R(4) * L * u * u * u * iS * iW * iW;
+        const R gT = -g * iS;
+        mu2 = R(1) - X * iopg;
+        const R i2 = iopg * iopg;
+        FX = (X * gX - opg) * i2;
+        FL = X * gL * i2;
+        FT = X * gT * i2;
+    } else {
+        const R D = R(2) * u - T - S;
+        const R N = R(2) * X * u;
+        const R SX = R(-4) * L * u * iS;
+        const R SL = R(2) * u * u * iS;
+        const R ST = T * iS;
+        const R iD = R(1) / D;
+        const R iD2 = iD * iD;
+        mu2 = R(1) - N * iD;
+        FX = (N * (R(-2) - SX) - (R(2) - R(4) * X) * D) * iD2;
+        FL = N * (-SL) * iD2;
+        FT = N * (R(-1) - ST) * iD2;
+    }
+}
+
+// Hamiltonian H = (|k|^2 - mu^2)/2 (Eq. 2, k in units of omega/c) and the ray
+// equations (Eq. 1a-1f, with k_phi sin(theta) dphi/dP' in the k_r equation as
+// the canonical momentum p_phi = r sin(theta) k_phi requires).  With G =
+// omega dH/domega at fixed k:
+//   dr/dP' = -H_kr/G, dtheta/dP' = -H_kth/(r G), dphi/dP' = -H_kph/(r sin G),
+//   dk_r/dP'   = H_r/G + k_th dtheta + k_ph sin dphi,
+//   dk_th/dP'  = (H_th/G - k_th dr + k_ph r cos dphi) / r,
+//   dk_ph/dP'  = (H_ph/G - k_ph sin dr - k_ph r cos dtheta) / (r sin).
+// mu2_out receives mu^2 at the stage.
+template <typename R>
+__device__ __forceinline__ void ray_rhs(const RayPhys<R> &rp, const StageIn<R> &s, R dy[6], R *mu2_out) {
+    const R kr = s.k[0], kt = s.k[1], kp = s.k[2];
+    const R kk = kr * kr + kt * kt + kp * kp;
+    R Hr, Ht, Hp, Hk0, Hk1, Hk2, G, mu2;
+    if (rp.iso) {
+        // no field: mu^2 = 1 - X, so H_x = grad(X)/2, H_k = k, G = -|k|^2 - X
+        mu2 = R(1) - s.X;
+        Hr = R(0.5) * s.dX[0];
+        Ht = R(0.5) * s.dX[1];
+        Hp = R(0.5) * s.dX[2];
+        Hk0 = kr;
+        Hk1 = kt;
+        Hk2 = kp;
+        G = -kk - s.X;
+    } else {
+        // dipole: components of m in the local basis (r, theta, phi)
+        const R mx = rp.m[0], my = rp.m[1], mz = rp.m[2];
+        const R mr = mx * s.sth * s.cph + my * s.sth * s.sph + mz * s.cth;
+        const R mt = mx * s.cth * s.cph + my * s.cth * s.sph - mz * s.sth;
+        const R mp = -mx * s.sph + my * s.cph;
+        const R ir = R(1) / s.r;
+        const R q = rp.R_E * ir;
+        const R A = rp.ab0 * q * q * q;  // Y = A (-2 m_r, m_th, m_ph)
+        const R Y0 = R(-2) * A * mr, Y1 = A * mt, Y2 = A * mp;
+        // Jacobian dY_i/d(r, theta, phi) from dm_r/dth = m_th, dm_r/dph = sin m_ph,
+        // dm_th/dth = -m_r, dm_th/dph = cos m_ph, dm_ph/dph = -(sin m_r + cos m_th)
+        const R J00 = R(6) * A * mr * ir, J01 = R(-2) * A * mt, J02 = R(-2) * A * s.sth * mp;
+        const R J10 = R(-3) * A * mt * ir, J11 = -A * mr, J12 = A * s.cth * mp;
+        const R J20 = R(-3) * A * mp * ir, J21 = R(0), J22 = -A * (s.sth * mr + s.cth * mt);
+        const R YY = Y0 * Y0 + Y1 * Y1 + Y2 * Y2;
+        const R kY = kr * Y0 + kt * Y1 + kp * Y2;
+        const R ikk = R(1) / kk;
+        const R L = kY * kY * ikk;
+        R T = YY - L;
+        if (T < R(0)) T = R(0);
+        R F, FX, FL, FT;
+        appleton_hartree<R>(s.X, L, T, rp.mode, F, FX, FL, FT);
+        mu2 = F;
+        // mu^2 = F(X, L, T) with T = Y^2 - L: d/dY^2 = F_T, d/dL|_{Y^2} = F_L - F_T
+        const R FYL = FL - FT;
+        const R c2 = R(2) * kY * ikk;
+        const R gY2_0 = R(2) * (Y0 * J00 + Y1 * J10 + Y2 * J20);
+        const R gY2_1 = R(2) * (Y0 * J01 + Y1 * J11 + Y2 * J21);
+        const R gY2_2 = R(2) * (Y0 * J02 + Y1 * J12 + Y2 * J22);
+        const R gL_0 = c2 * (kr * J00 + kt * J10 + kp * J20);
+        const R gL_1 = c2 * (kr * J01 + kt * J11 + kp * J21);
+        const R gL_2 = c2 * (kr * J02 + kt * J12 + kp * J22);
+        Hr = R(-0.5) * (FX * s.dX[0] + FT * gY2_0 + FYL * gL_0);
+        Ht = R(-0.5) * (FX * s.dX[1] + FT * gY2_1 + FYL * gL_1);
+        Hp = R(-0.5) * (FX * s.dX[2] + FT * gY2_2 + FYL * gL_2);
+        // dL/dk_i = (2 kY / |k|^2) (Y_i - (kY / |k|^2) k_i)
+        const R kYn = kY * ikk;
+        const R hf = R(0.5) * FYL * c2;
+        Hk0 = kr - hf * (Y0 - kYn * kr);
+        Hk1 = kt - hf * (Y1 - kYn * kt);
+        Hk2 = kp - hf * (Y2 - kYn * kp);
+        // omega dH/domega: X, L and T all scale as omega^-2, |k|^2 as omega^-2
+        G = -kk + s.X * FX + L * FL + T * FT;
+    }
+    const R iG = R(1) / G;
+    const R ir = R(1) / s.r;
+    const R irs = ir / s.sth;
+    const R dr = -Hk0 * iG;
+    const R dt = -Hk1 * iG * ir;
+    const R dp = -Hk2 * iG * irs;
+    dy[0] = dr;
+    dy[1] = dt;
+    dy[2] = dp;
+    dy[3] = Hr * iG + kt * dt + kp * s.sth * dp;
+    dy[4] = (Ht * iG - kt * dr + kp * s.r * s.cth * dp) * ir;
+    dy[5] = (Hp * iG - kp * s.sth * dr - kp * s.r * s.cth * dt) * irs;
+    if (mu2_out) *mu2_out = mu2;
+}
+
+}  // namespace rtgd

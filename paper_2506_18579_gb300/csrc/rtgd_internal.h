@@ -1,0 +1,46 @@
+// rtgd_internal.h -- structures shared by the host API and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "rtgd.h"
+#include "rtgd_device.cuh"
+
+namespace rtgd {
+
+struct GridSizes {
+    int n_lat, n_lon, n_alt;
+};
+
+// Device view of a fan (arrays in device memory) plus the integrator settings.
+struct FanDev {
+    const double *freq;  // MHz
+    const double *el;    // degrees
+    const double *az;    // degrees
+    int n_freq, n_el, n_az, n_modes;
+    int mode0, mode1;    // mode sign of mode index 0 / 1 (+1 ordinary, -1 extraordinary)
+    int integrator, precision, max_steps, order;
+    long long n_rays;
+    double tx_r, tx_th, tx_ph;  // launch position (km, rad, rad)
+    double h0, rtol, atol, hmin, hmax, max_path;
+    double land_tol;            // |r - R_E| accepted by the landing solve (km)
+    float rtol_f, atol_f;
+};
+
+struct LaunchPlan {
+    int kernel;   // RT_KERNEL_PLAIN / RT_KERNEL_PERSISTENT
+    int stencil;  // RT_STENCIL_GATHER / QUAD / TABLE
+    int threads;
+    int blocks;   // persistent grid size
+};
+
+cudaError_t launch_grid_prep(const void *raw, int dtype, const GridSizes &sz, double *pad64, float *pad32,
+                             float4 *quad, float4 *table, cudaStream_t st);
+cudaError_t upload_tableaus();
+cudaError_t launch_trace(const GridDev &g, const FanDev &f, rt_ray_result *out, unsigned long long *counter,
+                         const LaunchPlan &lp, cudaStream_t st);
+cudaError_t persistent_occupancy(int stencil, int threads, int *blocks_per_sm);
+cudaError_t launch_eval_rhs(const GridDev &g, const double *ys, double *dys, double *mu2s, double freq_mhz, int mode,
+                            int precision, int stencil, long long n, cudaStream_t st);
+
+}  // namespace rtgd

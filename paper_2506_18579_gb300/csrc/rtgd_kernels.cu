@@ -1,0 +1,1030 @@
+// rtgd_kernels.cu -- CUDA kernels of the RTM-GD tracer (sm_103a).
+//
+//   grid preparation  : ghost padding (FP64 + FP32 copies), the "quad" layout
+//                       (4 consecutive altitude samples per float4) and the
+//                       optional per-cell 64-sample table (Sec. II-C: the
+//                       interpolation data are prepared once per grid cell).
+//   trace_fp64        : all-FP64 tracer, one thread per ray.
+//   trace_mixed_*     : mixed-precision tracer.  A lane advances its ray one
+//                       stage (one right-hand-side evaluation) per loop
+//                       iteration, so lanes at different stages, steps or
+//                       rays never diverge in the heavy part.  The plain
+//                       kernel gives each lane one ray; the persistent kernel
+//                       keeps a resident grid whose idle lanes claim new rays
+//                       from an atomic counter (warp-aggregated).
+//   eval_rhs          : diagnostic evaluation of dy/dP' at given states.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "rtgd.h"
+#include "rtgd_device.cuh"
+#include "rtgd_internal.h"
+
+namespace rtgd {
+
+// ===================================================================== grid
+// Padded value at padded index (pi, pj, pk): interior nodes are copied; a
+// ghost index maps to quadratic extrapolation u_{-1} = 3u_0 - 3u_1 + u_2
+// (and its mirror at the far face), applied along every ghost axis (tensor
+// product, so corners combine up to 27 nodes).
+__device__ __forceinline__ int ghost_taps(int p, int n, int idx[3], double w[3]) {
+    if (p == 0) {
+        idx[0] = 0; idx[1] = 1; idx[2] = 2;
+        w[0] = 3.0; w[1] = -3.0; w[2] = 1.0;
+        return 3;
+    }
+    if (p == n + 1) {
+        idx[0] = n - 1; idx[1] = n - 2; idx[2] = n - 3;
+        w[0] = 3.0; w[1] = -3.0; w[2] = 1.0;
+        return 3;
+    }
+    idx[0] = p - 1;
+    w[0] = 1.0;
+    return 1;
+}
+
+template <typename T>
+__global__ void pad_kernel(const T *__restrict__ raw, double *__restrict__ pad64, float *__restrict__ pad32,
+                           int n_lat, int n_lon, int n_alt) {
+    const long long P_lon = n_lon + 2, P_alt = n_alt + 2;
+    const long long total = (long long)(n_lat + 2) * P_lon * P_alt;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int pk = (int)(e % P_alt);
+        const int pj = (int)((e / P_alt) % P_lon);
+        const int pi = (int)(e / (P_alt * P_lon));
+        int ia[3], ja[3], ka[3];
+        double wa[3], wb[3], wc[3];
+        const int na = ghost_taps(pi, n_lat, ia, wa);
+        const int nb = ghost_taps(pj, n_lon, ja, wb);
+        const int nc = ghost_taps(pk, n_alt, ka, wc);
+        double v = 0.0;
+        for (int a = 0; a < na; ++a)
+            for (int b = 0; b < nb; ++b)
+                for (int c = 0; c < nc; ++c)
+                    v += wa[a] * wb[b] * wc[c] *
+                         (double)raw[((long long)ia[a] * n_lon + ja[b]) * n_alt + ka[c]];
+        pad64[e] = v;
+        pad32[e] = (float)v;
+    }
+}
+
+// quad[(pi, pj, k)] = padded samples k..k+3 (nodes k-1..k+2) of cell k.
+__global__ void quad_kernel(const float *__restrict__ pad32, float4 *__restrict__ quad, int n_lat, int n_lon,
+                            int n_alt) {
+    const long long P_lon = n_lon + 2, P_alt = n_alt + 2, Q = n_alt - 1;
+    const long long total = (long long)(n_lat + 2) * P_lon * Q;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long k = e % Q;
+        const long long row = e / Q;  // pi * P_lon + pj
+        const float *p = pad32 + row * P_alt + k;
+        quad[e] = make_float4(p[0], p[1], p[2], p[3]);
+    }
+}
+
+// table[cell * 16 + a * 4 + b] = the 4 altitude samples of row (a, b) of the
+// 4x4x4 stencil of cell (i, j, k); cells are ordered [i][j][k].
+__global__ void table_kernel(const float4 *__restrict__ quad, float4 *__restrict__ table, int n_lat, int n_lon,
+                             int n_alt) {
+    const long long C_lon = n_lon - 1, C_alt = n_alt - 1, P_lon = n_lon + 2;
+    const long long total = (long long)(n_lat - 1) * C_lon * C_alt * 16;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int ab = (int)(e & 15);
+        const long long cell = e >> 4;
+        const long long k = cell % C_alt;
+        const long long j = (cell / C_alt) % C_lon;
+        const long long i = cell / (C_alt * C_lon);
+        const int a = ab >> 2, b = ab & 3;
+        table[e] = quad[((i + a) * P_lon + (j + b)) * C_alt + k];
+    }
+}
+
+static int blocks_for(long long n, int threads) {
+    long long b = (n + threads - 1) / threads;
+    if (b > 152 * 64) b = 152 * 64;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+cudaError_t launch_grid_prep(const void *raw, int dtype, const GridSizes &sz, double *pad64, float *pad32,
+                             float4 *quad, float4 *table, cudaStream_t st) {
+    const long long n_pad = (long long)(sz.n_lat + 2) * (sz.n_lon + 2) * (sz.n_alt + 2);
+    if (dtype == RT_F64)
+        pad_kernel<double><<<blocks_for(n_pad, 256), 256, 0, st>>>((const double *)raw, pad64, pad32, sz.n_lat,
+                                                                    sz.n_lon, sz.n_alt);
+    else
+        pad_kernel<float><<<blocks_for(n_pad, 256), 256, 0, st>>>((const float *)raw, pad64, pad32, sz.n_lat,
+                                                                   sz.n_lon, sz.n_alt);
+    const long long n_quad = (long long)(sz.n_lat + 2) * (sz.n_lon + 2) * (sz.n_alt - 1);
+    quad_kernel<<<blocks_for(n_quad, 256), 256, 0, st>>>(pad32, quad, sz.n_lat, sz.n_lon, sz.n_alt);
+    if (table) {
+        const long long n_tab = (long long)(sz.n_lat - 1) * (sz.n_lon - 1) * (sz.n_alt - 1) * 16;
+        table_kernel<<<blocks_for(n_tab, 256), 256, 0, st>>>(quad, table, sz.n_lat, sz.n_lon, sz.n_alt);
+    }
+    return cudaGetLastError();
+}
+
+// ====================================================================== fan
+// Canonical ray index -> (frequency, mode, elevation, azimuth) of the fan,
+// order [freq][mode][el][az].
+struct RayParams {
+    double f_hz, el, az;  // el, az in radians
+    int mode;
+};
+
+__device__ __forceinline__ RayParams ray_params(const FanDev &f, long long id) {
+    const long long a = id % f.n_az;
+    const long long e = (id / f.n_az) % f.n_el;
+    const long long m = (id / ((long long)f.n_az * f.n_el)) % f.n_modes;
+    const long long q = id / ((long long)f.n_az * f.n_el * f.n_modes);
+    RayParams p;
+    p.f_hz = f.freq[q] * 1e6;
+    p.el = f.el[e] * kDeg2Rad;
+    p.az = f.az[a] * kDeg2Rad;
+    p.mode = (m == 0) ? f.mode0 : f.mode1;
+    return p;
+}
+
+// Claim index -> canonical index.  ORDER_ELEVATION_FASTEST hands out
+// neighbouring elevations of one azimuth together (similar paths, so the
+// lanes of a warp gather from nearby cells).
+__device__ __forceinline__ long long claim_to_ray(const FanDev &f, long long c) {
+    if (f.order != RT_ORDER_ELEVATION_FASTEST) return c;
+    const long long e = c % f.n_el;
+    const long long a = (c / f.n_el) % f.n_az;
+    const long long fm = c / ((long long)f.n_el * f.n_az);  // freq * n_modes + mode
+    return (fm * f.n_el + e) * f.n_az + a;
+}
+
+// ================================================================ utilities
+__device__ __forceinline__ double wrap180(double x) { return x - 360.0 * floor((x + 180.0) / 360.0); }
+
+// Peak of the cubic Hermite fit of r(s), s in [0,1], through (r0, h d0) and
+// (r1, h d1) with d0 > 0 >= d1 (zero of p'(s) by bisection).
+__device__ double hermite_peak(double r0, double r1, double d0, double d1, double h) {
+    const double m0 = h * d0, m1 = h * d1;
+    const double A = 2.0 * (r0 - r1) + m0 + m1;
+    const double B = 3.0 * (r1 - r0) - 2.0 * m0 - m1;
+    double lo = 0.0, hi = 1.0;
+    for (int it = 0; it < 60; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        const double dp = m0 + 2.0 * B * mid + 3.0 * A * mid * mid;
+        if (dp > 0.0) lo = mid;
+        else hi = mid;
+    }
+    const double s = 0.5 * (lo + hi);
+    return r0 + m0 * s + B * s * s + A * s * s * s;
+}
+
+// Output quantities of a final state (Sec. II-C: group path, ground distance,
+// azimuth deviation, reflection height): central angle and initial bearing
+// on the sphere from the transmitter (th0, ph0) to (th, ph).
+__device__ void finish_result(const FanDev &f, double az_launch, const double y[6], double P, double apo,
+                              int status, int n_steps, int n_att, int n_evals, double R_E, rt_ray_result *out) {
+    double s0, c0, s1, c1, sd, cd;
+    sincos(f.tx_th, &s0, &c0);
+    sincos(y[1], &s1, &c1);
+    sincos(y[2] - f.tx_ph, &sd, &cd);
+    const double east = s1 * sd;                 // components of the final point in the
+    const double north = s0 * c1 - c0 * s1 * cd;  // tangent plane at the transmitter
+    const double dot = s0 * s1 * cd + c0 * c1;
+    const double ang = atan2(sqrt(east * east + north * north), dot);
+    rt_ray_result r;
+    r.group_path_km = P;
+    r.ground_range_km = R_E * ang;
+    r.az_dev_deg = ang > 1e-15 ? wrap180(atan2(east, north) * kRad2Deg - az_launch * kRad2Deg) : 0.0;
+    r.apogee_km = apo;
+    r.land_lat_deg = 90.0 - y[1] * kRad2Deg;
+    r.land_lon_deg = wrap180(y[2] * kRad2Deg);
+    r.status = status;
+    r.n_steps = n_steps;
+    r.n_attempts = n_att;
+    r.n_evals = n_evals;
+    *out = r;
+}
+
+__device__ __forceinline__ bool finite6(const double y[6]) {
+    bool ok = true;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) ok = ok && isfinite(y[i]);
+    return ok;
+}
+
+// Lateral position inside the grid's lat/lon span?
+__device__ __forceinline__ bool inside_latlon(const GridDev &g, double th, double ph) {
+    const double lat = 90.0 - th * kRad2Deg;
+    double lonrel = ph * kRad2Deg - g.lon0;
+    lonrel -= 360.0 * floor(lonrel / 360.0);
+    const double xa = (lat - g.lat0) * g.inv_dlat;
+    const double xb = lonrel * g.inv_dlon;
+    return xa >= 0.0 && xa <= (double)(g.n_lat - 1) && xb >= 0.0 && xb <= (double)(g.n_lon - 1);
+}
+
+// ================================================================ FP64 path
+// dy/dP' at state y, all in double: Ne and its gradient from the FP64 padded
+// grid (Eq. 13), then the dipole, Appleton-Hartree and Eq. 1.
+__device__ void rhs64(const GridDev &g, const RayPhys<double> &rp, const double y[6], double dy[6],
+                      double *mu2) {
+    StageIn<double> s;
+    s.r = y[0];
+    sincos(y[1], &s.sth, &s.cth);
+    sincos(y[2], &s.sph, &s.cph);
+    s.k[0] = y[3];
+    s.k[1] = y[4];
+    s.k[2] = y[5];
+    const double alt = y[0] - g.R_E;
+    const double lat = 90.0 - y[1] * kRad2Deg;
+    double lonrel = y[2] * kRad2Deg - g.lon0;
+    lonrel -= 360.0 * floor(lonrel / 360.0);
+    const double xa = (lat - g.lat0) * g.inv_dlat;
+    const double xb = lonrel * g.inv_dlon;
+    const double xc = (alt - g.alt0) * g.inv_dalt;
+    int ia, ib, ic;
+    double ta, tb, tc;
+    s.X = 0.0;
+    s.dX[0] = s.dX[1] = s.dX[2] = 0.0;
+    if (cell_coord<double>(xa, g.n_lat, ia, ta) && cell_coord<double>(xb, g.n_lon, ib, tb) &&
+        cell_coord<double>(xc, g.n_alt, ic, tc)) {
+        double wa[4], da[4], wb[4], db[4], wc[4], dc[4], out[4];
+        gd_weights<double>(ta, wa, da);
+        gd_weights<double>(tb, wb, db);
+        gd_weights<double>(tc, wc, dc);
+        const long long sj = g.p_alt, si = (long long)g.p_lon * g.p_alt;
+        // padded index of node (ia-1, ib-1, ic-1) is (ia, ib, ic)
+        const double *base = g.pad64 + (long long)ia * si + (long long)ib * sj + ic;
+#define RTGD_ROW64(a, b, u0, u1, u2, u3)              \
+    {                                                 \
+        const double *p_ = base + (a) * si + (b) * sj; \
+        u0 = __ldg(p_);                               \
+        u1 = __ldg(p_ + 1);                           \
+        u2 = __ldg(p_ + 2);                           \
+        u3 = __ldg(p_ + 3);                           \
+    }
+        RTGD_CONTRACT(double, RTGD_ROW64, wa, da, wb, db, wc, dc, out);
+#undef RTGD_ROW64
+        s.X = rp.xfac * out[0];
+        s.dX[0] = rp.xfac * out[3] * g.inv_dalt;
+        s.dX[1] = -rp.xfac * out[1] * g.inv_dlat * kRad2Deg;
+        s.dX[2] = rp.xfac * out[2] * g.inv_dlon * kRad2Deg;
+    }
+    ray_rhs<double>(rp, s, dy, mu2);
+}
+
+__device__ void rk4_step64(const GridDev &g, const RayPhys<double> &rp, const double y[6], const double k1[6],
+                           double h, double yn[6]) {
+    double k2[6], k3[6], k4[6], t[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) t[i] = y[i] + 0.5 * h * k1[i];
+    rhs64(g, rp, t, k2, nullptr);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) t[i] = y[i] + 0.5 * h * k2[i];
+    rhs64(g, rp, t, k3, nullptr);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) t[i] = y[i] + h * k3[i];
+    rhs64(g, rp, t, k4, nullptr);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) yn[i] = y[i] + h / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+}
+
+// Runge-Kutta-Fehlberg 4(5): fourth-order solution in yn, (5th - 4th) in e.
+__device__ void rkf45_step64(const GridDev &g, const RayPhys<double> &rp, const double y[6], const double k1[6],
+                             double h, double yn[6], double e[6]) {
+    double k2[6], k3[6], k4[6], k5[6], k6[6], t[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) t[i] = y[i] + h * (k1[i] / 4.0);
+    rhs64(g, rp, t, k2, nullptr);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) t[i] = y[i] + h * (3.0 / 32.0 * k1[i] + 9.0 / 32.0 * k2[i]);
+    rhs64(g, rp, t, k3, nullptr);
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+        t[i] = y[i] + h * (1932.0 / 2197.0 * k1[i] - 7200.0 / 2197.0 * k2[i] + 7296.0 / 2197.0 * k3[i]);
+    rhs64(g, rp, t, k4, nullptr);
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+        t[i] = y[i] + h * (439.0 / 216.0 * k1[i] - 8.0 * k2[i] + 3680.0 / 513.0 * k3[i] - 845.0 / 4104.0 * k4[i]);
+    rhs64(g, rp, t, k5, nullptr);
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+        t[i] = y[i] + h * (-8.0 / 27.0 * k1[i] + 2.0 * k2[i] - 3544.0 / 2565.0 * k3[i] + 1859.0 / 4104.0 * k4[i] -
+                           11.0 / 40.0 * k5[i]);
+    rhs64(g, rp, t, k6, nullptr);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const double y4 =
+            y[i] + h * (25.0 / 216.0 * k1[i] + 1408.0 / 2565.0 * k3[i] + 2197.0 / 4104.0 * k4[i] - k5[i] / 5.0);
+        const double y5 = y[i] + h * (16.0 / 135.0 * k1[i] + 6656.0 / 12825.0 * k3[i] + 28561.0 / 56430.0 * k4[i] -
+                                      9.0 / 50.0 * k5[i] + 2.0 / 55.0 * k6[i]);
+        yn[i] = y4;
+        e[i] = y5 - y4;
+    }
+}
+
+// RKF45 error norm (<= 1 accepts) and step factor, as documented in rtgd.h.
+template <typename R>
+__device__ __forceinline__ R rkf45_err(R r, R sth, R kmag, const R e[6], R rtol, R atol) {
+    const R pos = fmax(fabs(e[0]), fmax(r * fabs(e[1]), r * sth * fabs(e[2])));
+    const R kerr = fmax(fabs(e[3]), fmax(fabs(e[4]), fabs(e[5])));
+    return fmax(pos / (atol + rtol * r), kerr / (rtol * fmax(kmag, R(1e-3))));
+}
+
+template <typename R>
+__device__ __forceinline__ R step_factor(R err) {
+    if (err == R(0)) return R(5);
+    return fmin(R(5), fmax(R(0.2), R(0.9) * pow(err, R(-0.2))));
+}
+
+// Launch direction (elevation above the horizontal, azimuth clockwise from
+// north; the theta unit vector points south) and position of a ray.
+__device__ __forceinline__ void launch_dir(const FanDev &f, const RayParams &p, double y[6]) {
+    double se, ce, sa, ca;
+    sincos(p.el, &se, &ce);
+    sincos(p.az, &sa, &ca);
+    y[0] = f.tx_r;
+    y[1] = f.tx_th;
+    y[2] = f.tx_ph;
+    y[3] = se;
+    y[4] = -ce * ca;
+    y[5] = ce * sa;
+}
+
+__device__ void trace_ray_fp64(const GridDev &g, const FanDev &f, long long id, rt_ray_result *out) {
+    const RayParams p = ray_params(f, id);
+    const RayPhys<double> rp = make_phys<double>(g, p.f_hz, p.mode);
+    const double RE = g.R_E;
+    double y[6], dummy[6], mu2 = 0.0;
+    launch_dir(f, p, y);
+    rhs64(g, rp, y, dummy, &mu2);  // mu^2 at the transmitter for this direction
+    if (!(mu2 > 0.0)) {
+        finish_result(f, p.az, y, 0.0, f.tx_r - RE, RT_RAY_NONFINITE, 0, 0, 1, RE, out);
+        return;
+    }
+    const double mu = sqrt(mu2);
+    y[3] *= mu;
+    y[4] *= mu;
+    y[5] *= mu;
+    const bool adaptive = f.integrator == RT_RKF45;
+    double P = 0.0, h = f.h0, apo = y[0] - RE;
+    int n_steps = 0, n_att = 0, n_ev = 1, status = RT_RAY_NOT_RUN;
+    const int ev_per_step = adaptive ? 5 : 3;  // stage evaluations besides k1
+    bool have_prev = false, k1_valid = false;
+    double r_prev = 0.0, dr_prev = 0.0, h_prev = 0.0;
+    double k1[6];
+    while (status == RT_RAY_NOT_RUN) {
+        if (n_att >= f.max_steps) {
+            status = RT_RAY_MAX_STEPS;
+            break;
+        }
+        double hs = h;
+        if (f.max_path > 0.0 && P + hs > f.max_path) hs = f.max_path - P;
+        if (!k1_valid) {
+            rhs64(g, rp, y, k1, nullptr);
+            k1_valid = true;
+            ++n_ev;
+        }
+        if (have_prev && dr_prev > 0.0 && k1[0] <= 0.0)
+            apo = fmax(apo, hermite_peak(r_prev, y[0], dr_prev, k1[0], h_prev) - RE);
+        have_prev = false;
+        double yn[6], e[6];
+        if (adaptive) rkf45_step64(g, rp, y, k1, hs, yn, e);
+        else rk4_step64(g, rp, y, k1, hs, yn);
+        ++n_att;
+        n_ev += ev_per_step;
+        double h_next = h;
+        if (adaptive) {
+            const double err = rkf45_err<double>(y[0], sin(y[1]), sqrt(y[3] * y[3] + y[4] * y[4] + y[5] * y[5]), e,
+                                                 f.rtol, f.atol);
+            const double fac = step_factor<double>(err);
+            if (!(err <= 1.0)) {
+                h = hs * fac;
+                if (h < f.hmin) status = RT_RAY_STEP_UNDERFLOW;
+                continue;
+            }
+            h_next = fmin(fmax(hs * fac, f.hmin), f.hmax);
+        }
+        if (!finite6(yn)) {
+            status = RT_RAY_NONFINITE;
+            break;
+        }
+        if (yn[0] < RE) {
+            // ground return: r(step(h*)) = R_E for h* in (0, hs], Illinois regula falsi
+            double a = 0.0, fa = y[0] - RE, b = hs, fb = yn[0] - RE, c = b;
+            double yc[6], ec[6];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) yc[i] = yn[i];
+            int side = 0;
+            for (int it = 0; it < 60; ++it) {
+                c = b - fb * (b - a) / (fb - fa);
+                if (adaptive) rkf45_step64(g, rp, y, k1, c, yc, ec);
+                else rk4_step64(g, rp, y, k1, c, yc);
+                ++n_att;
+                n_ev += ev_per_step;
+                const double fc = yc[0] - RE;
+                if (fabs(fc) < 1e-9) break;
+                if (fc < 0.0) {
+                    b = c;
+                    fb = fc;
+                    if (side == -1) fa *= 0.5;
+                    side = -1;
+                } else {
+                    a = c;
+                    fa = fc;
+                    if (side == 1) fb *= 0.5;
+                    side = 1;
+                }
+            }
+            P += c;
+            ++n_steps;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) y[i] = yc[i];
+            status = RT_RAY_LANDED;
+            break;
+        }
+        P += hs;
+        ++n_steps;
+        apo = fmax(apo, yn[0] - RE);
+        have_prev = true;
+        r_prev = y[0];
+        dr_prev = k1[0];
+        h_prev = hs;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) y[i] = yn[i];
+        k1_valid = false;
+        const double alt = y[0] - RE;
+        if (alt > g.top) {
+            status = RT_RAY_ESCAPED;
+            break;
+        }
+        if (alt >= g.alt0 && !inside_latlon(g, y[1], y[2])) {
+            status = RT_RAY_LEFT_GRID;
+            break;
+        }
+        if (f.max_path > 0.0 && P >= f.max_path - 1e-12) {
+            status = RT_RAY_MAX_PATH;
+            break;
+        }
+        h = h_next;
+    }
+    finish_result(f, p.az, y, P, apo, status, n_steps, n_att, n_ev, RE, out);
+}
+
+__global__ void __launch_bounds__(128) trace_fp64_kernel(GridDev g, FanDev f, rt_ray_result *__restrict__ out) {
+    const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (id >= f.n_rays) return;
+    rt_ray_result r;
+    trace_ray_fp64(g, f, id, &r);
+    out[id] = r;
+}
+
+// =============================================================== mixed path
+// The ray state (r, theta, phi, k) and group path stay in double.  A step
+// attempt starts from a "base": the grid cell and in-cell coordinates of the
+// state, computed once in double, plus float copies of the state.  Each stage
+// then works on float offsets delta from the base: its grid coordinates are
+// base + delta * (d coord / d state), so they keep the full resolution of the
+// base; everything after (weights, contraction, dipole, Appleton-Hartree,
+// Eq. 1) runs in float.  The accepted step adds the float increment to the
+// double state.
+struct Base32 {
+    int ia, ib, ic;
+    float ta, tb, tc;
+    float r, th, ph;
+    float k[3];
+};
+
+__device__ __forceinline__ void make_base(const GridDev &g, const double y[6], Base32 &b) {
+    const double lat = 90.0 - y[1] * kRad2Deg;
+    double lonrel = y[2] * kRad2Deg - g.lon0;
+    lonrel -= 360.0 * floor(lonrel / 360.0);
+    const double xa = (lat - g.lat0) * g.inv_dlat;
+    const double xb = lonrel * g.inv_dlon;
+    const double xc = (y[0] - g.R_E - g.alt0) * g.inv_dalt;
+    const double fa = floor(xa), fb = floor(xb), fc = floor(xc);
+    // positions far outside the grid are clamped so the integer stays small; they
+    // remain outside (and non-finite positions give NaN fractions, also outside)
+    b.ia = (int)fmin(fmax(fa, -1e6), 1e6);
+    b.ib = (int)fmin(fmax(fb, -1e6), 1e6);
+    b.ic = (int)fmin(fmax(fc, -1e6), 1e6);
+    b.ta = (float)(xa - fa);
+    b.tb = (float)(xb - fb);
+    b.tc = (float)(xc - fc);
+    b.r = (float)y[0];
+    b.th = (float)y[1];
+    b.ph = (float)y[2];
+    b.k[0] = (float)y[3];
+    b.k[1] = (float)y[4];
+    b.k[2] = (float)y[5];
+}
+
+// Stage cell along one axis from base cell i0 and offset coordinate t = t0 +
+// delta * scale; false outside [0, n-1].
+__device__ __forceinline__ bool stage_cell(int i0, float t, int n, int &i, float &tt) {
+    const float fl = fminf(fmaxf(floorf(t), -1e6f), 1e6f);  // keeps the int sum far from overflow
+    int ii = i0 + (int)fl;
+    float tr = t - fl;
+    if (!(tr >= 0.0f && tr <= 1.0f)) return false;  // NaN, or an offset beyond the clamp
+    if (ii < 0 || ii > n - 1) return false;
+    if (ii == n - 1) {
+        if (tr != 0.0f) return false;
+        ii = n - 2;
+        tr = 1.0f;
+    }
+    i = ii;
+    tt = tr;
+    return true;
+}
+
+// dy/dP' (float) at base + delta.  STENCIL selects where the 64 samples come
+// from; kdir overrides the wave vector (used for the launch direction).
+template <int STENCIL>
+__device__ __forceinline__ void rhs_mixed(const GridDev &g, const RayPhys<float> &rp, const Base32 &b,
+                                          const float d[6], float dy[6], float *mu2) {
+    StageIn<float> s;
+    s.r = b.r + d[0];
+    const float th = b.th + d[1], ph = b.ph + d[2];
+    sincosf(th, &s.sth, &s.cth);
+    sincosf(ph, &s.sph, &s.cph);
+    s.k[0] = b.k[0] + d[3];
+    s.k[1] = b.k[1] + d[4];
+    s.k[2] = b.k[2] + d[5];
+    s.X = 0.0f;
+    s.dX[0] = s.dX[1] = s.dX[2] = 0.0f;
+    int ia, ib, ic;
+    float ta, tb, tc;
+    if (stage_cell(b.ia, b.ta + g.sa * d[1], g.n_lat, ia, ta) && stage_cell(b.ib, b.tb + g.sb * d[2], g.n_lon, ib, tb) &&
+        stage_cell(b.ic, b.tc + g.sc * d[0], g.n_alt, ic, tc)) {
+        float wa[4], da[4], wb[4], db[4], wc[4], dc[4], out[4];
+        gd_weights<float>(ta, wa, da);
+        gd_weights<float>(tb, wb, db);
+        gd_weights<float>(tc, wc, dc);
+        if (STENCIL == RT_STENCIL_QUAD) {
+            // quad (pi, pj, k): 4 samples of cell k in padded row (pi, pj); node i-1 -> padded i
+            const long long sj = g.q_alt, si = (long long)(g.n_lon + 2) * g.q_alt;
+            const float4 *q = g.quad + (long long)ia * si + (long long)ib * sj + ic;
+#define RTGD_ROWQ(a, b, u0, u1, u2, u3)               \
+    {                                                 \
+        const float4 v_ = __ldg(q + (a) * si + (b) * sj); \
+        u0 = v_.x;                                    \
+        u1 = v_.y;                                    \
+        u2 = v_.z;                                    \
+        u3 = v_.w;                                    \
+    }
+            RTGD_CONTRACT(float, RTGD_ROWQ, wa, da, wb, db, wc, dc, out);
+#undef RTGD_ROWQ
+        } else if (STENCIL == RT_STENCIL_TABLE) {
+            const long long cell = ((long long)ia * (g.n_lon - 1) + ib) * (g.n_alt - 1) + ic;
+            const float4 *q = g.table + cell * 16;
+#define RTGD_ROWT(a, b, u0, u1, u2, u3)         \
+    {                                           \
+        const float4 v_ = __ldg(q + (a) * 4 + (b)); \
+        u0 = v_.x;                              \
+        u1 = v_.y;                              \
+        u2 = v_.z;                              \
+        u3 = v_.w;                              \
+    }
+            RTGD_CONTRACT(float, RTGD_ROWT, wa, da, wb, db, wc, dc, out);
+#undef RTGD_ROWT
+        } else {
+            const long long sj = g.p_alt, si = (long long)g.p_lon * g.p_alt;
+            const float *p = g.pad32 + (long long)ia * si + (long long)ib * sj + ic;
+#define RTGD_ROWG(a, b, u0, u1, u2, u3)              \
+    {                                                \
+        const float *p_ = p + (a) * si + (b) * sj;   \
+        u0 = __ldg(p_);                              \
+        u1 = __ldg(p_ + 1);                          \
+        u2 = __ldg(p_ + 2);                          \
+        u3 = __ldg(p_ + 3);                          \
+    }
+            RTGD_CONTRACT(float, RTGD_ROWG, wa, da, wb, db, wc, dc, out);
+#undef RTGD_ROWG
+        }
+        s.X = rp.xfac * out[0];
+        s.dX[0] = rp.xfac * out[3] * g.sc;
+        s.dX[1] = rp.xfac * out[1] * g.sa;
+        s.dX[2] = rp.xfac * out[2] * g.sb;
+    }
+    ray_rhs<float>(rp, s, dy, mu2);
+}
+
+// Butcher tables in "shifted accumulator" form.  After stage s produced k_s,
+// acc[t] <- acc[t+1] + A[s][t] k_s (t = 0..4, acc[5] = 0), so acc[0] always
+// holds sum_j a[s+1][j] k_j, the offset (over h) of the next stage; y4 and the
+// error estimate accumulate B4[s] k_s and E[s] k_s.
+struct Tableau {
+    float A[6][5];
+    float B4[6];
+    float E[6];
+    int ns;
+};
+
+__constant__ Tableau c_tab[2];  // [RT_RK4], [RT_RKF45]
+
+// Per-lane state of the mixed tracer.
+struct Lane {
+    long long out_id;
+    double y[6];
+    double P, h, hs, apo;
+    double r_prev, h_prev;
+    double la, lfa, lb, lfb;  // landing bracket
+    float dr_prev;
+    float acc[5][6];
+    float y4[6], e[6];
+    float k1[6];
+    RayPhys<float> rp;
+    Base32 b;
+    double az;
+    int stage, n_steps, n_att, n_ev, status, side, land_it;
+    bool active, launch, landing, have_prev, k1_valid;
+};
+
+// Fills acc/y4/e from stage s output ks.
+__device__ __forceinline__ void accumulate(Lane &L, const Tableau &T, int s, const float ks[6]) {
+    const bool first = s == 0;  // stage 0 starts a fresh attempt
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) L.acc[t][c] = (first ? 0.0f : L.acc[t + 1][c]) + T.A[s][t] * ks[c];
+        L.acc[4][c] = T.A[s][4] * ks[c];
+        L.y4[c] = (first ? 0.0f : L.y4[c]) + T.B4[s] * ks[c];
+        L.e[c] = (first ? 0.0f : L.e[c]) + T.E[s] * ks[c];
+    }
+}
+
+__device__ void lane_begin_ray(Lane &L, const GridDev &g, const FanDev &f, long long id) {
+    const RayParams p = ray_params(f, id);
+    L.out_id = id;
+    L.rp = make_phys<float>(g, p.f_hz, p.mode);
+    L.az = p.az;
+    launch_dir(f, p, L.y);
+    L.P = 0.0;
+    L.h = f.h0;
+    L.apo = f.tx_r - g.R_E;
+    L.n_steps = L.n_att = L.n_ev = 0;
+    L.status = RT_RAY_NOT_RUN;
+    L.have_prev = L.k1_valid = L.landing = false;
+    L.launch = true;
+    L.stage = 0;
+    make_base(g, L.y, L.b);
+}
+
+__device__ __forceinline__ void lane_finish(Lane &L, const GridDev &g, const FanDev &f, rt_ray_result *out) {
+    rt_ray_result r;
+    finish_result(f, L.az, L.y, L.P, L.apo, L.status, L.n_steps, L.n_att, L.n_ev, g.R_E, &r);
+    out[L.out_id] = r;
+    L.active = false;
+}
+
+// Starts the next step attempt from the current state; returns false when the
+// ray stops (step budget).
+__device__ __forceinline__ bool lane_begin_attempt(Lane &L, const FanDev &f, const Tableau &T) {
+    if (L.n_att >= f.max_steps) {
+        L.status = RT_RAY_MAX_STEPS;
+        return false;
+    }
+    if (!L.landing) {
+        L.hs = L.h;
+        if (f.max_path > 0.0 && L.P + L.hs > f.max_path) L.hs = f.max_path - L.P;
+    }
+    if (L.k1_valid) {  // k1 at this state is known: start at stage 1
+        accumulate(L, T, 0, L.k1);
+        L.stage = 1;
+    } else {
+        L.stage = 0;
+    }
+    return true;
+}
+
+// One stage evaluation of one lane plus its bookkeeping.  Returns true when
+// the ray has finished (status set).
+template <int STENCIL>
+__device__ bool lane_advance(Lane &L, const GridDev &g, const FanDev &f, const Tableau &T) {
+    const double RE = g.R_E;
+    float d[6], ks[6], mu2;
+    ++L.n_ev;
+    if (L.launch) {
+        // mu^2 at the transmitter for the launch direction (|k| = 1 in the base)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) d[c] = 0.0f;
+        rhs_mixed<STENCIL>(g, L.rp, L.b, d, ks, &mu2);
+        L.launch = false;
+        if (!(mu2 > 0.0f)) {
+            L.status = RT_RAY_NONFINITE;
+            return true;
+        }
+        const double mu = sqrt((double)mu2);
+        L.y[3] *= mu;
+        L.y[4] *= mu;
+        L.y[5] *= mu;
+        make_base(g, L.y, L.b);
+        return !lane_begin_attempt(L, f, T);
+    }
+    const float hf = (float)L.hs;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) d[c] = (L.stage == 0) ? 0.0f : hf * L.acc[0][c];
+    rhs_mixed<STENCIL>(g, L.rp, L.b, d, ks, nullptr);
+    if (L.stage == 0) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) L.k1[c] = ks[c];
+        L.k1_valid = true;
+        if (L.have_prev && L.dr_prev > 0.0f && ks[0] <= 0.0f)
+            L.apo = fmax(L.apo, hermite_peak(L.r_prev, L.y[0], (double)L.dr_prev, (double)ks[0], L.h_prev) - RE);
+        L.have_prev = false;
+    }
+    accumulate(L, T, L.stage, ks);
+    if (++L.stage < T.ns) return false;
+
+    // ---- attempt complete: increments in float, state update in double
+    ++L.n_att;
+    float dy4[6], ef[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        dy4[c] = hf * L.y4[c];
+        ef[c] = hf * L.e[c];
+    }
+    if (L.landing) {
+        // Illinois regula falsi on the step size: f(h*) = r(step(h*)) - R_E
+        const double fc = (L.y[0] - RE) + (double)dy4[0];
+        ++L.land_it;
+        const bool done = fabs(fc) < f.land_tol || L.land_it >= 60 || fabs(L.lb - L.la) < 1e-12;
+        if (!done) {
+            if (fc < 0.0) {
+                L.lb = L.hs;
+                L.lfb = fc;
+                if (L.side == -1) L.lfa *= 0.5;
+                L.side = -1;
+            } else {
+                L.la = L.hs;
+                L.lfa = fc;
+                if (L.side == 1) L.lfb *= 0.5;
+                L.side = 1;
+            }
+            L.hs = L.lb - L.lfb * (L.lb - L.la) / (L.lfb - L.lfa);
+            return !lane_begin_attempt(L, f, T);
+        }
+        L.P += L.hs;
+        ++L.n_steps;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) L.y[c] += (double)dy4[c];
+        L.status = RT_RAY_LANDED;
+        return true;
+    }
+    double h_next = L.h;
+    if (f.integrator == RT_RKF45) {
+        const float kmag = sqrtf(L.b.k[0] * L.b.k[0] + L.b.k[1] * L.b.k[1] + L.b.k[2] * L.b.k[2]);
+        const float err = rkf45_err<float>(L.b.r, sinf(L.b.th), kmag, ef, f.rtol_f, f.atol_f);
+        const double fac = (double)step_factor<float>(err);
+        if (!(err <= 1.0f)) {
+            L.h = L.hs * fac;
+            if (L.h < f.hmin) {
+                L.status = RT_RAY_STEP_UNDERFLOW;
+                return true;
+            }
+            return !lane_begin_attempt(L, f, T);
+        }
+        h_next = fmin(fmax(L.hs * fac, f.hmin), f.hmax);
+    }
+    double yn[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) yn[c] = L.y[c] + (double)dy4[c];
+    if (!finite6(yn)) {
+        L.status = RT_RAY_NONFINITE;
+        return true;
+    }
+    if (yn[0] < RE) {
+        L.landing = true;
+        L.la = 0.0;
+        L.lfa = L.y[0] - RE;
+        L.lb = L.hs;
+        L.lfb = yn[0] - RE;
+        L.side = 0;
+        L.land_it = 0;
+        L.hs = L.lb - L.lfb * (L.lb - L.la) / (L.lfb - L.lfa);
+        return !lane_begin_attempt(L, f, T);
+    }
+    L.P += L.hs;
+    ++L.n_steps;
+    L.apo = fmax(L.apo, yn[0] - RE);
+    L.have_prev = true;
+    L.r_prev = L.y[0];
+    L.dr_prev = L.k1[0];
+    L.h_prev = L.hs;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) L.y[c] = yn[c];
+    L.k1_valid = false;
+    const double alt = yn[0] - RE;
+    if (alt > g.top) {
+        L.status = RT_RAY_ESCAPED;
+        return true;
+    }
+    if (alt >= g.alt0 && !inside_latlon(g, yn[1], yn[2])) {
+        L.status = RT_RAY_LEFT_GRID;
+        return true;
+    }
+    if (f.max_path > 0.0 && L.P >= f.max_path - 1e-12) {
+        L.status = RT_RAY_MAX_PATH;
+        return true;
+    }
+    L.h = h_next;
+    make_base(g, L.y, L.b);
+    return !lane_begin_attempt(L, f, T);
+}
+
+// One ray per thread; each thread loops stage by stage until its ray ends.
+template <int STENCIL>
+__global__ void __launch_bounds__(128) trace_mixed_plain_kernel(GridDev g, FanDev f, rt_ray_result *__restrict__ out) {
+    const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (id >= f.n_rays) return;
+    const Tableau &T = c_tab[f.integrator == RT_RKF45 ? 1 : 0];
+    Lane L;
+    L.active = true;
+    lane_begin_ray(L, g, f, claim_to_ray(f, id));
+    // bounded: at most (max_steps + 1) attempts of T.ns stages plus the launch
+    const long long max_iter = ((long long)f.max_steps + 2) * 6 + 8;
+    bool done = false;
+    for (long long it = 0; it < max_iter && !done; ++it) done = lane_advance<STENCIL>(L, g, f, T);
+    if (!done) L.status = RT_RAY_MAX_STEPS;
+    lane_finish(L, g, f, out);
+}
+
+// Persistent kernel: resident blocks; every warp keeps its 32 lanes busy by
+// claiming new rays (one atomicAdd per warp for all idle lanes) as rays end.
+template <int STENCIL>
+__global__ void __launch_bounds__(128) trace_mixed_persistent_kernel(GridDev g, FanDev f,
+                                                                     rt_ray_result *__restrict__ out,
+                                                                     unsigned long long *__restrict__ counter) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const Tableau &T = c_tab[f.integrator == RT_RKF45 ? 1 : 0];
+    Lane L;
+    L.active = false;
+    bool exhausted = false;  // warp-uniform
+    long long iters = 0;
+    const long long n = f.n_rays;
+    // bound on the warp's total iterations: every ray needs at most
+    // (max_steps + 2) * 6 + 8 stage iterations, and a warp runs at most all n rays
+    const long long max_iter = (((long long)f.max_steps + 2) * 6 + 8) * (n + 32) + 64;
+    for (;;) {
+        const unsigned idle = __ballot_sync(FULL, !L.active);
+        if (idle != 0u && !exhausted) {
+            const int n_idle = __popc(idle);
+            const int leader = __ffs(idle) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(counter, (unsigned long long)n_idle);
+            base = __shfl_sync(FULL, base, leader);
+            if (base + (unsigned long long)n_idle >= (unsigned long long)n) exhausted = true;
+            if (!L.active) {
+                const unsigned long long c = base + __popc(idle & ((1u << lane) - 1u));
+                if (c < (unsigned long long)n) {
+                    L.active = true;
+                    lane_begin_ray(L, g, f, claim_to_ray(f, (long long)c));
+                }
+            }
+        }
+        if (!__any_sync(FULL, L.active)) break;
+        if (++iters > max_iter) {  // defensive bound; never reached for valid inputs
+            if (L.active) {
+                L.status = RT_RAY_MAX_STEPS;
+                lane_finish(L, g, f, out);
+            }
+            break;
+        }
+        if (L.active && lane_advance<STENCIL>(L, g, f, T)) lane_finish(L, g, f, out);
+    }
+}
+
+// ============================================================== diagnostics
+__global__ void eval_rhs_kernel(GridDev g, const double *__restrict__ ys, double *__restrict__ dys,
+                                double *__restrict__ mu2s, double freq_mhz, int mode, int precision, int stencil,
+                                long long n) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double y[6], dy[6], mu2 = 0.0;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) y[c] = ys[i * 6 + c];
+    if (precision == RT_FP64) {
+        const RayPhys<double> rp = make_phys<double>(g, freq_mhz * 1e6, mode);
+        rhs64(g, rp, y, dy, &mu2);
+    } else {
+        const RayPhys<float> rp = make_phys<float>(g, freq_mhz * 1e6, mode);
+        Base32 b;
+        make_base(g, y, b);
+        float d[6] = {0, 0, 0, 0, 0, 0}, dyf[6], m2;
+        if (stencil == RT_STENCIL_TABLE) rhs_mixed<RT_STENCIL_TABLE>(g, rp, b, d, dyf, &m2);
+        else if (stencil == RT_STENCIL_GATHER) rhs_mixed<RT_STENCIL_GATHER>(g, rp, b, d, dyf, &m2);
+        else rhs_mixed<RT_STENCIL_QUAD>(g, rp, b, d, dyf, &m2);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) dy[c] = dyf[c];
+        mu2 = m2;
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) dys[i * 6 + c] = dy[c];
+    mu2s[i] = mu2;
+}
+
+// ================================================================ launchers
+static void fill_tableaus(Tableau tab[2]) {
+    for (int t = 0; t < 2; ++t) {
+        for (int s = 0; s < 6; ++s) {
+            for (int u = 0; u < 5; ++u) tab[t].A[s][u] = 0.0f;
+            tab[t].B4[s] = tab[t].E[s] = 0.0f;
+        }
+    }
+    // classic RK4: a21 = a32 = 1/2, a43 = 1; b = (1, 2, 2, 1)/6; A[s][t] = a[s+1+t][s]
+    double a4[4][4] = {{0}};
+    a4[1][0] = 0.5;
+    a4[2][1] = 0.5;
+    a4[3][2] = 1.0;
+    const double b4[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+    tab[0].ns = 4;
+    for (int s = 0; s < 4; ++s) {
+        for (int u = 0; u < 5; ++u) tab[0].A[s][u] = (s + 1 + u < 4) ? (float)a4[s + 1 + u][s] : 0.0f;
+        tab[0].B4[s] = (float)b4[s];
+    }
+    // Fehlberg 4(5)
+    double a[6][6] = {{0}};
+    a[1][0] = 1.0 / 4.0;
+    a[2][0] = 3.0 / 32.0;
+    a[2][1] = 9.0 / 32.0;
+    a[3][0] = 1932.0 / 2197.0;
+    a[3][1] = -7200.0 / 2197.0;
+    a[3][2] = 7296.0 / 2197.0;
+    a[4][0] = 439.0 / 216.0;
+    a[4][1] = -8.0;
+    a[4][2] = 3680.0 / 513.0;
+    a[4][3] = -845.0 / 4104.0;
+    a[5][0] = -8.0 / 27.0;
+    a[5][1] = 2.0;
+    a[5][2] = -3544.0 / 2565.0;
+    a[5][3] = 1859.0 / 4104.0;
+    a[5][4] = -11.0 / 40.0;
+    const double b4f[6] = {25.0 / 216.0, 0.0, 1408.0 / 2565.0, 2197.0 / 4104.0, -1.0 / 5.0, 0.0};
+    const double b5f[6] = {16.0 / 135.0, 0.0, 6656.0 / 12825.0, 28561.0 / 56430.0, -9.0 / 50.0, 2.0 / 55.0};
+    tab[1].ns = 6;
+    for (int s = 0; s < 6; ++s) {
+        for (int u = 0; u < 5; ++u) tab[1].A[s][u] = (s + 1 + u < 6) ? (float)a[s + 1 + u][s] : 0.0f;
+        tab[1].B4[s] = (float)b4f[s];
+        tab[1].E[s] = (float)(b5f[s] - b4f[s]);
+    }
+}
+
+cudaError_t upload_tableaus() {
+    Tableau tab[2];
+    fill_tableaus(tab);
+    return cudaMemcpyToSymbol(c_tab, tab, sizeof(tab));
+}
+
+template <int STENCIL>
+static cudaError_t launch_mixed(const GridDev &g, const FanDev &f, rt_ray_result *out,
+                                unsigned long long *counter, const LaunchPlan &lp, cudaStream_t st) {
+    if (lp.kernel == RT_KERNEL_PERSISTENT) {
+        trace_mixed_persistent_kernel<STENCIL><<<lp.blocks, lp.threads, 0, st>>>(g, f, out, counter);
+    } else {
+        const int blocks = (int)((f.n_rays + lp.threads - 1) / lp.threads);
+        trace_mixed_plain_kernel<STENCIL><<<blocks, lp.threads, 0, st>>>(g, f, out);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trace(const GridDev &g, const FanDev &f, rt_ray_result *out, unsigned long long *counter,
+                         const LaunchPlan &lp, cudaStream_t st) {
+    if (f.n_rays == 0) return cudaSuccess;
+    if (f.precision == RT_FP64) {
+        const int threads = 128;
+        const long long blocks = (f.n_rays + threads - 1) / threads;
+        trace_fp64_kernel<<<(unsigned)blocks, threads, 0, st>>>(g, f, out);
+        return cudaGetLastError();
+    }
+    switch (lp.stencil) {
+        case RT_STENCIL_GATHER: return launch_mixed<RT_STENCIL_GATHER>(g, f, out, counter, lp, st);
+        case RT_STENCIL_TABLE: return launch_mixed<RT_STENCIL_TABLE>(g, f, out, counter, lp, st);
+        default: return launch_mixed<RT_STENCIL_QUAD>(g, f, out, counter, lp, st);
+    }
+}
+
+cudaError_t persistent_occupancy(int stencil, int threads, int *blocks_per_sm) {
+    switch (stencil) {
+        case RT_STENCIL_GATHER:
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                blocks_per_sm, trace_mixed_persistent_kernel<RT_STENCIL_GATHER>, threads, 0);
+        case RT_STENCIL_TABLE:
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                blocks_per_sm, trace_mixed_persistent_kernel<RT_STENCIL_TABLE>, threads, 0);
+        default:
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                blocks_per_sm, trace_mixed_persistent_kernel<RT_STENCIL_QUAD>, threads, 0);
+    }
+}
+
+cudaError_t launch_eval_rhs(const GridDev &g, const double *ys, double *dys, double *mu2s, double freq_mhz, int mode,
+                            int precision, int stencil, long long n, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    const int threads = 128;
+    eval_rhs_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, st>>>(g, ys, dys, mu2s, freq_mhz, mode,
+                                                                               precision, stencil, n);
+    return cudaGetLastError();
+}
+
+}  // namespace rtgd

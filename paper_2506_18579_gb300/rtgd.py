@@ -1,0 +1,259 @@
+"""Thin ctypes binding of librtgd.so (the C ABI in include/rtgd.h).
+
+Argument marshalling only: every step of the ray tracing runs in the CUDA
+library.  Functions keep the C names; a few helpers convert the dataclasses
+of ``workloads`` into the C descriptors and wrap results as numpy records.
+There is no CPU fallback: if the library cannot be loaded, or no GPU is
+present, calls raise ``RtError``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librtgd.so")
+
+RT_OK, RT_EINVAL, RT_ENOMEM, RT_ECUDA, RT_ETIMEOUT, RT_EUNSUPPORTED = range(6)
+RT_F32, RT_F64 = 0, 1
+RT_GRID_TABLE = 1
+RT_MODE_O, RT_MODE_X = 1, 2
+RT_RK4, RT_RKF45 = 0, 1
+RT_FP64, RT_MIXED = 0, 1
+(RT_RAY_NOT_RUN, RT_RAY_LANDED, RT_RAY_ESCAPED, RT_RAY_LEFT_GRID, RT_RAY_MAX_STEPS,
+ RT_RAY_STEP_UNDERFLOW, RT_RAY_NONFINITE, RT_RAY_MAX_PATH) = range(8)
+RT_KERNEL_AUTO, RT_KERNEL_PLAIN, RT_KERNEL_PERSISTENT = 0, 1, 2
+RT_STENCIL_AUTO, RT_STENCIL_GATHER, RT_STENCIL_QUAD, RT_STENCIL_TABLE = 0, 1, 2, 3
+RT_ORDER_CANONICAL, RT_ORDER_ELEVATION_FASTEST = 0, 1
+
+EXPORTED = ["rt_grid_create", "rt_grid_destroy", "rt_grid_device_bytes", "rt_fan_size",
+            "rt_trace", "rt_trace_device", "rt_tune", "rt_eval_rhs", "rt_last_error",
+            "rt_version"]
+
+
+class RtError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("rtgd error %d: %s" % (code, msg))
+        self.code = code
+
+
+class rt_dipole(ctypes.Structure):
+    _fields_ = [("b0_tesla", ctypes.c_double), ("pole_lat_deg", ctypes.c_double),
+                ("pole_lon_deg", ctypes.c_double)]
+
+
+class rt_grid_desc(ctypes.Structure):
+    _fields_ = [("n_lat", ctypes.c_int32), ("n_lon", ctypes.c_int32), ("n_alt", ctypes.c_int32),
+                ("dtype", ctypes.c_int32), ("lat0_deg", ctypes.c_double),
+                ("lon0_deg", ctypes.c_double), ("alt0_km", ctypes.c_double),
+                ("dlat_deg", ctypes.c_double), ("dlon_deg", ctypes.c_double),
+                ("dalt_km", ctypes.c_double), ("earth_radius_km", ctypes.c_double),
+                ("field", rt_dipole), ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+_DP = ctypes.POINTER(ctypes.c_double)
+
+
+class rt_fan_desc(ctypes.Structure):
+    _fields_ = [("tx_lat_deg", ctypes.c_double), ("tx_lon_deg", ctypes.c_double),
+                ("tx_alt_km", ctypes.c_double), ("freq_mhz", _DP), ("el_deg", _DP),
+                ("az_deg", _DP), ("n_freq", ctypes.c_int32), ("n_el", ctypes.c_int32),
+                ("n_az", ctypes.c_int32), ("modes", ctypes.c_uint32),
+                ("integrator", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("h_km", ctypes.c_double), ("rtol", ctypes.c_double), ("atol_km", ctypes.c_double),
+                ("h_min_km", ctypes.c_double), ("h_max_km", ctypes.c_double),
+                ("max_steps", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("max_group_path_km", ctypes.c_double)]
+
+
+class rt_launch_config(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int32), ("stencil", ctypes.c_int32),
+                ("block_threads", ctypes.c_int32), ("order", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+RESULT_DTYPE = np.dtype([("group_path_km", "f8"), ("ground_range_km", "f8"),
+                         ("az_dev_deg", "f8"), ("apogee_km", "f8"), ("land_lat_deg", "f8"),
+                         ("land_lon_deg", "f8"), ("status", "i4"), ("n_steps", "i4"),
+                         ("n_attempts", "i4"), ("n_evals", "i4")])
+assert RESULT_DTYPE.itemsize == 64
+
+_lib = None
+
+
+def load(path=None):
+    """Load librtgd.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RtError(RT_EUNSUPPORTED, "CUDA library %s is not built (run build.build())" % path)
+    L = ctypes.CDLL(path)
+    vp, sz = ctypes.c_void_p, ctypes.c_size_t
+    L.rt_grid_create.argtypes = [ctypes.POINTER(rt_grid_desc), vp, ctypes.POINTER(vp)]
+    L.rt_grid_create.restype = ctypes.c_int
+    L.rt_grid_destroy.argtypes = [vp]
+    L.rt_grid_destroy.restype = ctypes.c_int
+    L.rt_grid_device_bytes.argtypes = [vp]
+    L.rt_grid_device_bytes.restype = sz
+    L.rt_fan_size.argtypes = [ctypes.POINTER(rt_fan_desc)]
+    L.rt_fan_size.restype = sz
+    L.rt_trace.argtypes = [vp, ctypes.POINTER(rt_fan_desc), vp, sz, ctypes.POINTER(rt_launch_config), vp]
+    L.rt_trace.restype = ctypes.c_int
+    L.rt_trace_device.argtypes = [vp, ctypes.POINTER(rt_fan_desc), vp, sz,
+                                  ctypes.POINTER(rt_launch_config), vp]
+    L.rt_trace_device.restype = ctypes.c_int
+    L.rt_tune.argtypes = [vp, ctypes.POINTER(rt_fan_desc), sz, vp, ctypes.POINTER(rt_launch_config),
+                          ctypes.POINTER(ctypes.c_float)]
+    L.rt_tune.restype = ctypes.c_int
+    L.rt_eval_rhs.argtypes = [vp, ctypes.c_double, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                              _DP, _DP, _DP, sz]
+    L.rt_eval_rhs.restype = ctypes.c_int
+    L.rt_last_error.argtypes = []
+    L.rt_last_error.restype = ctypes.c_char_p
+    L.rt_version.argtypes = []
+    L.rt_version.restype = ctypes.c_int32
+    _lib = L
+    return L
+
+
+def _check(code):
+    if code != RT_OK:
+        raise RtError(code, load().rt_last_error().decode())
+
+
+def rt_last_error():
+    return load().rt_last_error().decode()
+
+
+def rt_version():
+    return load().rt_version()
+
+
+# ------------------------------------------------------------------ grids
+def grid_desc(spec, dtype=RT_F32, table=False):
+    return rt_grid_desc(spec.n_lat, spec.n_lon, spec.n_alt, dtype, spec.lat0_deg, spec.lon0_deg,
+                        spec.alt0_km, spec.dlat_deg, spec.dlon_deg, spec.dalt_km,
+                        spec.earth_radius_km,
+                        rt_dipole(spec.b0_tesla, spec.pole_lat_deg, spec.pole_lon_deg),
+                        RT_GRID_TABLE if table else 0, 0)
+
+
+class Grid:
+    """Device-resident grid handle (rt_grid_create / rt_grid_destroy)."""
+
+    def __init__(self, spec, ne, table=False):
+        ne = np.ascontiguousarray(ne)
+        if ne.dtype not in (np.float32, np.float64):
+            ne = ne.astype(np.float32)
+        assert ne.shape == (spec.n_lat, spec.n_lon, spec.n_alt)
+        self.spec = spec
+        self.desc = grid_desc(spec, RT_F64 if ne.dtype == np.float64 else RT_F32, table)
+        self.handle = rt_grid_create(self.desc, ne)
+
+    @property
+    def device_bytes(self):
+        return load().rt_grid_device_bytes(self.handle)
+
+    def close(self):
+        if self.handle:
+            rt_grid_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rt_grid_create(desc, ne_host):
+    h = ctypes.c_void_p()
+    _check(load().rt_grid_create(ctypes.byref(desc), ne_host.ctypes.data, ctypes.byref(h)))
+    return h
+
+
+def rt_grid_destroy(handle):
+    _check(load().rt_grid_destroy(handle))
+
+
+# ------------------------------------------------------------------- fans
+class Fan:
+    """rt_fan_desc plus the arrays it points to (kept alive)."""
+
+    def __init__(self, spec, precision=None):
+        self.spec = spec
+        self.freq = np.ascontiguousarray(spec.freq_mhz, dtype=np.float64)
+        self.el = np.ascontiguousarray(spec.el_deg, dtype=np.float64)
+        self.az = np.ascontiguousarray(spec.az_deg, dtype=np.float64)
+        prec = spec.precision if precision is None else precision
+        self.desc = rt_fan_desc(
+            spec.tx_lat_deg, spec.tx_lon_deg, spec.tx_alt_km, self.freq.ctypes.data_as(_DP),
+            self.el.ctypes.data_as(_DP), self.az.ctypes.data_as(_DP), len(self.freq), len(self.el),
+            len(self.az), spec.modes, spec.integrator, prec, spec.h_km, spec.rtol, spec.atol_km,
+            spec.h_min_km, spec.h_max_km, spec.max_steps, 0, spec.max_group_path_km)
+
+    @property
+    def n_rays(self):
+        return rt_fan_size(self.desc)
+
+    @property
+    def host_bytes(self):
+        return self.freq.nbytes + self.el.nbytes + self.az.nbytes
+
+
+def rt_fan_size(desc):
+    return load().rt_fan_size(ctypes.byref(desc))
+
+
+def launch_config(kernel=0, stencil=0, block_threads=0, order=0, blocks_per_sm=0):
+    return rt_launch_config(kernel, stencil, block_threads, order, blocks_per_sm)
+
+
+def _cfg_ptr(cfg):
+    return ctypes.byref(cfg) if cfg is not None else None
+
+
+def rt_trace(grid, fan, out=None, cfg=None, stream=None):
+    """Blocking trace into a host numpy record array (allocated if out is None)."""
+    n = fan.n_rays
+    if out is None:
+        out = np.zeros(n, dtype=RESULT_DTYPE)
+    assert out.dtype == RESULT_DTYPE and out.flags.c_contiguous
+    _check(load().rt_trace(grid.handle, ctypes.byref(fan.desc), out.ctypes.data, len(out),
+                           _cfg_ptr(cfg), stream))
+    return out
+
+
+def rt_trace_device(grid, fan, out_ptr, out_len, cfg=None, stream=None):
+    """Asynchronous trace into device memory (e.g. torch tensor .data_ptr())."""
+    _check(load().rt_trace_device(grid.handle, ctypes.byref(fan.desc), ctypes.c_void_p(out_ptr),
+                                  out_len, _cfg_ptr(cfg), stream))
+
+
+def rt_tune(grid, fan, max_rays=0, stream=None):
+    best = rt_launch_config()
+    ms = ctypes.c_float()
+    _check(load().rt_tune(grid.handle, ctypes.byref(fan.desc), max_rays, stream, ctypes.byref(best),
+                          ctypes.byref(ms)))
+    return best, ms.value
+
+
+def rt_eval_rhs(grid, freq_mhz, mode, y, precision=RT_FP64, stencil=RT_STENCIL_AUTO):
+    y = np.ascontiguousarray(np.atleast_2d(y), dtype=np.float64)
+    n = len(y)
+    dy = np.zeros((n, 6))
+    mu2 = np.zeros(n)
+    _check(load().rt_eval_rhs(grid.handle, float(freq_mhz), int(mode), int(precision), int(stencil),
+                              y.ctypes.data_as(_DP), dy.ctypes.data_as(_DP), mu2.ctypes.data_as(_DP),
+                              n))
+    return dy, mu2
+
+
+def results_view(tensor_or_array, n):
+    """Record view of n results held in a uint8/int64 host buffer."""
+    a = np.asarray(tensor_or_array).view(np.uint8)[: n * 64]
+    return a.view(RESULT_DTYPE)

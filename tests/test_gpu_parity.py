@@ -1,0 +1,225 @@
+"""Parity of the CUDA tracer with the FP64 CPU oracle, through the C ABI.
+
+Tolerances: the all-FP64 path agrees within 1e-6 km in group path and ground
+range and 1e-7 deg in azimuth deviation; the mixed path within 0.05 km and
+1e-4 deg, over rays that are not next to a skip or Pedersen boundary (a
+status change or a range jump between neighbouring elevations).  Sizes: full
+fans where the oracle finishes in seconds, seeded samples of the full-size
+fans otherwise, plus ragged and degenerate cases.
+"""
+import numpy as np
+import pytest
+
+from paper_2506_18579_gb300 import build as rtbuild
+from paper_2506_18579_gb300 import rtgd as rt
+from paper_2506_18579_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+FP64_KM, FP64_DEG = 1e-6, 1e-7
+MIX_KM, MIX_DEG = 0.05, 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    rtbuild.build()
+    return rt.load()
+
+
+def _close64(gpu, ref, idx=None, km=FP64_KM, deg=FP64_DEG):
+    ref = ref if idx is None else ref
+    g = gpu if idx is None else gpu[idx]
+    assert np.array_equal(g["status"], ref["status"]), (g["status"], ref["status"])
+    for f, tol in (("group_path_km", km), ("ground_range_km", km), ("apogee_km", km),
+                   ("az_dev_deg", deg), ("land_lat_deg", deg), ("land_lon_deg", deg)):
+        d = np.abs(g[f] - ref[f])
+        assert np.all(d <= tol), (f, d.max(), int(np.argmax(d)))
+
+
+def near_boundary(res, fan):
+    """Rays adjacent (in elevation) to a status change or a jump of ground
+    range or group path larger than 30 km between neighbouring elevations."""
+    n_az, n_el = len(fan.az_deg), len(fan.el_deg)
+    r = res.reshape(-1, n_el, n_az)
+    flag = np.zeros(r.shape, bool)
+    jump = ((r["status"][:, 1:] != r["status"][:, :-1]) |
+            (np.abs(np.diff(r["ground_range_km"], axis=1)) > 30.0) |
+            (np.abs(np.diff(r["group_path_km"], axis=1)) > 30.0))
+    flag[:, 1:] |= jump
+    flag[:, :-1] |= jump
+    return flag.reshape(-1)
+
+
+# ------------------------------------------------------------------ RHS
+def _states(w, n, seed):
+    rng = np.random.default_rng(seed)
+    RE = w.grid.earth_radius_km
+    lat = rng.uniform(w.grid.lat0_deg + 1, w.grid.lat0_deg + (w.grid.n_lat - 2) * w.grid.dlat_deg, n)
+    lon = rng.uniform(w.grid.lon0_deg + 1, w.grid.lon0_deg + (w.grid.n_lon - 2) * w.grid.dlon_deg, n)
+    alt = rng.uniform(w.grid.alt0_km - 20, w.grid.alt0_km + (w.grid.n_alt - 1) * w.grid.dalt_km + 20, n)
+    k = rng.normal(size=(n, 3))
+    k *= (rng.uniform(0.3, 1.0, n) / np.linalg.norm(k, axis=1))[:, None]
+    return np.column_stack([RE + alt, np.radians(90 - lat), np.radians(lon), k])
+
+
+@pytest.mark.parametrize("cfg", ["c1", "c2"])
+def test_rhs_matches_oracle(orc, cfg):
+    w = wl.config1() if cfg == "c1" else wl.config2()
+    g = rt.Grid(w.grid, w.ne, table=True)
+    og = orc.Grid(w.grid, w.ne)
+    ys = _states(w, 400, 5)
+    for f, mode in ((10.0, 1), (12.0, -1), (8.0, 1)):
+        ref = np.array([orc.rhs(og, f, mode, y) for y in ys])
+        scale = np.abs(ref).max(axis=0) + 1e-300
+        dy64, _ = rt.rt_eval_rhs(g, f, mode, ys, rt.RT_FP64)
+        assert np.max(np.abs(dy64 - ref) / scale) < 1e-10
+        prev = None
+        for st in (rt.RT_STENCIL_GATHER, rt.RT_STENCIL_QUAD, rt.RT_STENCIL_TABLE):
+            dym, _ = rt.rt_eval_rhs(g, f, mode, ys, rt.RT_MIXED, st)
+            assert np.max(np.abs(dym - ref) / scale) < 2e-4
+            if prev is not None:  # the three sample layouts hold the same values
+                assert np.array_equal(prev, dym)
+            prev = dym
+
+
+# ------------------------------------------------------------- FP64 path
+def test_fp64_config1_all_rays(orc):
+    w = wl.config1()
+    g = rt.Grid(w.grid, w.ne)
+    gpu = rt.rt_trace(g, rt.Fan(w.fan, rt.RT_FP64))
+    ref = orc.trace_fan(orc.Grid(w.grid, w.ne), w.fan)
+    assert np.all(ref["status"] == orc.LANDED)
+    _close64(gpu, ref)
+    assert np.array_equal(gpu["n_steps"], ref["n_steps"])
+    assert np.array_equal(gpu["n_attempts"], ref["n_attempts"])
+
+
+def _c2_small():
+    return wl.config2(elev_step=6.0, az_step=60.0)  # 3 x 2 x 10 x 6 = 360 rays
+
+
+def test_fp64_rkf45_small_fan(orc):
+    w = _c2_small()
+    g = rt.Grid(w.grid, w.ne)
+    gpu = rt.rt_trace(g, rt.Fan(w.fan, rt.RT_FP64))
+    ref = orc.trace_fan(orc.Grid(w.grid, w.ne), w.fan)
+    _close64(gpu, ref)
+    assert np.mean(gpu["n_attempts"] == ref["n_attempts"]) > 0.98
+
+
+def test_fp64_config2_full_size_sampled(orc):
+    w = wl.config2()
+    assert w.fan.n_rays == 24840
+    g = rt.Grid(w.grid, w.ne)
+    gpu = rt.rt_trace(g, rt.Fan(w.fan, rt.RT_FP64))
+    idx = wl.sample_indices(w.fan.n_rays, 48, seed=21)
+    ref = orc.trace_fan(orc.Grid(w.grid, w.ne), w.fan, indices=idx)
+    _close64(gpu[idx], ref)
+    assert np.all(gpu["status"] != rt.RT_RAY_NOT_RUN)
+
+
+# ------------------------------------------------------------ mixed path
+@pytest.mark.parametrize("kernel", [rt.RT_KERNEL_PLAIN, rt.RT_KERNEL_PERSISTENT])
+def test_mixed_config1_all_rays(orc, kernel):
+    w = wl.config1()
+    g = rt.Grid(w.grid, w.ne)
+    gpu = rt.rt_trace(g, rt.Fan(w.fan, rt.RT_MIXED), cfg=rt.launch_config(kernel=kernel))
+    ref = orc.trace_fan(orc.Grid(w.grid, w.ne), w.fan)
+    _close64(gpu, ref, km=MIX_KM, deg=MIX_DEG)
+
+
+def test_mixed_config2_full_size(orc):
+    w = wl.config2()
+    g = rt.Grid(w.grid, w.ne, table=True)
+    fan = rt.Fan(w.fan, rt.RT_MIXED)
+    outs = {}
+    for st in (rt.RT_STENCIL_GATHER, rt.RT_STENCIL_QUAD, rt.RT_STENCIL_TABLE):
+        for kern in (rt.RT_KERNEL_PLAIN, rt.RT_KERNEL_PERSISTENT):
+            outs[(st, kern)] = rt.rt_trace(g, fan, cfg=rt.launch_config(kernel=kern, stencil=st))
+    base = outs[(rt.RT_STENCIL_QUAD, rt.RT_KERNEL_PERSISTENT)]
+    for k, v in outs.items():  # same arithmetic, same samples: bitwise equal
+        assert v.tobytes() == base.tobytes(), k
+    ref64 = rt.rt_trace(g, rt.Fan(w.fan, rt.RT_FP64))
+    ok = ~near_boundary(ref64, w.fan)
+    assert ok.mean() > 0.9
+    same = base["status"] == ref64["status"]
+    assert same[ok].mean() > 0.999
+    m = ok & same
+    for f, tol in (("group_path_km", MIX_KM), ("ground_range_km", MIX_KM), ("az_dev_deg", MIX_DEG)):
+        d = np.abs(base[f] - ref64[f])[m]
+        assert np.all(d <= tol), (f, d.max())
+    idx = wl.sample_indices(w.fan.n_rays, 48, seed=22)
+    idx = idx[m[idx]]
+    ref = orc.trace_fan(orc.Grid(w.grid, w.ne), w.fan, indices=idx)
+    _close64(base[idx], ref, km=MIX_KM, deg=MIX_DEG)
+
+
+# --------------------------------------------------------- edge cases
+def test_ragged_and_tiny_fans(orc):
+    w = _c2_small()
+    g = rt.Grid(w.grid, w.ne)
+    og = orc.Grid(w.grid, w.ne)
+    for n_el in (1, 3, 33):
+        spec = w.fan.replace(el_deg=np.linspace(5.0, 55.0, n_el), az_deg=[17.0], freq_mhz=[9.0])
+        ref = orc.trace_fan(og, spec)
+        _close64(rt.rt_trace(g, rt.Fan(spec, rt.RT_FP64)), ref)
+        for kern in (rt.RT_KERNEL_PLAIN, rt.RT_KERNEL_PERSISTENT):
+            gm = rt.rt_trace(g, rt.Fan(spec, rt.RT_MIXED), cfg=rt.launch_config(kernel=kern))
+            ok = ~near_boundary(ref, spec)
+            _close64(gm[ok], ref[ok], km=MIX_KM, deg=MIX_DEG)
+
+
+def test_statuses_match_oracle(orc):
+    w = wl.config1()
+    g = rt.Grid(w.grid, w.ne)
+    og = orc.Grid(w.grid, w.ne)
+    cases = [w.fan.replace(freq_mhz=[30.0], el_deg=[70.0]),        # escapes
+             w.fan.replace(max_steps=10),                            # step budget
+             w.fan.replace(tx_alt_km=150.0, max_group_path_km=123.4), # group-path limit
+             w.fan.replace(integrator=wl.RKF45, rtol=1e-14, atol_km=1e-14, h_min_km=0.5)]  # underflow
+    for spec in cases:
+        ref = orc.trace_fan(og, spec)
+        for prec in (rt.RT_FP64, rt.RT_MIXED):
+            gpu = rt.rt_trace(g, rt.Fan(spec, prec))
+            assert np.array_equal(gpu["status"], ref["status"]), (spec, prec)
+    bad = w.ne.copy()
+    bad[:, :, 10:] = np.nan
+    gb = rt.Grid(w.grid, bad)
+    for prec in (rt.RT_FP64, rt.RT_MIXED):
+        assert np.all(rt.rt_trace(gb, rt.Fan(w.fan, prec))["status"] == rt.RT_RAY_NONFINITE)
+
+
+def test_invalid_calls_are_errors():
+    w = wl.config1()
+    g = rt.Grid(w.grid, w.ne)
+    fan = rt.Fan(w.fan)
+    fan.desc.n_el = 0
+    with pytest.raises(rt.RtError) as ei:
+        rt.rt_trace(g, fan, out=np.zeros(16, dtype=rt.RESULT_DTYPE))
+    assert ei.value.code == rt.RT_EINVAL
+    with pytest.raises(rt.RtError):
+        rt.rt_trace(g, rt.Fan(w.fan), out=np.zeros(3, dtype=rt.RESULT_DTYPE))
+    with pytest.raises(rt.RtError):  # table stencil on a grid without a table
+        rt.rt_trace(g, rt.Fan(w.fan, rt.RT_MIXED), cfg=rt.launch_config(stencil=rt.RT_STENCIL_TABLE))
+    spec = w.grid
+    with pytest.raises(rt.RtError):
+        rt.Grid(wl.GridSpec(**{**spec.__dict__, "n_alt": 3}), w.ne[:, :, :3])
+
+
+def test_device_output_and_tuner():
+    torch = pytest.importorskip("torch")
+    w = _c2_small()
+    g = rt.Grid(w.grid, w.ne, table=True)
+    fan = rt.Fan(w.fan, rt.RT_MIXED)
+    n = fan.n_rays
+    out = torch.empty(n * 64, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.current_stream()
+    rt.rt_trace_device(g, fan, out.data_ptr(), n, stream=s.cuda_stream)
+    s.synchronize()
+    dev = rt.results_view(out.cpu().numpy(), n)
+    host = rt.rt_trace(g, fan)
+    assert dev.tobytes() == host.tobytes()
+    best, ms = rt.rt_tune(g, fan, max_rays=512)
+    assert ms > 0 and best.kernel in (rt.RT_KERNEL_PLAIN, rt.RT_KERNEL_PERSISTENT)
+    tuned = rt.rt_trace(g, fan)  # picks the cached configuration
+    assert np.array_equal(tuned["status"], host["status"])
