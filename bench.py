@@ -52,6 +52,13 @@ def parse_args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     p.add_argument("--no-tune", action="store_true")
+    p.add_argument("--kernel", choices=["plain", "persistent"], default=None,
+                   help="fixed launch configuration instead of the autotuner")
+    p.add_argument("--stencil", choices=["gather", "quad", "table"], default="quad")
+    p.add_argument("--order", choices=["canonical", "elevation"], default="elevation")
+    p.add_argument("--threads", type=int, default=128)
+    p.add_argument("--profile", action="store_true",
+                   help="warm-up launches then one launch, nothing else (for ncu captures)")
     p.add_argument("--cpu-sample", type=int, default=512)
     return p.parse_args()
 
@@ -193,15 +200,32 @@ def run_ours(args):
     rtbuild.build()
     w = wl.config2()
     prec = rt.RT_MIXED if args.precision == "mixed" else rt.RT_FP64
-    grid = rt.Grid(w.grid, w.ne, table=(prec == rt.RT_MIXED))
+    grid = rt.Grid(w.grid, w.ne, table=(prec == rt.RT_MIXED and
+                                        (args.kernel is None or args.stencil == "table")))
     fan = rt.Fan(w.fan, prec)
     n = fan.n_rays
     stream = torch.cuda.current_stream()
     sptr = stream.cuda_stream
     out = torch.empty(n * 64, dtype=torch.uint8, device="cuda")
     cfg, tune_ms = None, None
-    if prec == rt.RT_MIXED and not args.no_tune:
+    if args.kernel is not None:
+        cfg = rt.launch_config(
+            kernel=rt.RT_KERNEL_PLAIN if args.kernel == "plain" else rt.RT_KERNEL_PERSISTENT,
+            stencil={"gather": rt.RT_STENCIL_GATHER, "quad": rt.RT_STENCIL_QUAD,
+                     "table": rt.RT_STENCIL_TABLE}[args.stencil],
+            block_threads=args.threads,
+            order=rt.RT_ORDER_CANONICAL if args.order == "canonical" else rt.RT_ORDER_ELEVATION_FASTEST)
+    elif prec == rt.RT_MIXED and not args.no_tune:
         cfg, tune_ms = rt.rt_tune(grid, fan, max_rays=8192, stream=sptr)
+    if args.profile:
+        for _ in range(max(args.warmup, 1) + 1):
+            rt.rt_trace_device(grid, fan, out.data_ptr(), n, cfg=cfg, stream=sptr)
+        torch.cuda.synchronize()
+        res = rt.results_view(out.cpu().numpy(), n)
+        print(json.dumps({"profile_run": True, "rays": n, "evals": int(res["n_evals"].sum()),
+                          "launches": max(args.warmup, 1) + 1}), flush=True)
+        grid.close()
+        return
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")  # > 129 MB L2
 
     def step():

@@ -364,7 +364,9 @@ void rk4_step(const Ctx &c, const double y[6], const double k1[6], double h, dou
 }
 
 /* Runge-Kutta-Fehlberg 4(5) (Fehlberg 1969).  Returns the fourth-order
- * solution in yn and the difference fifth-minus-fourth order in e. */
+ * solution in yn and the local error estimate (fifth minus fourth order) in
+ * e, formed directly as h * sum((b5_i - b4_i) k_i): the difference of the two
+ * solutions would cancel against r ~ 6371 km and keep only a few digits. */
 void rkf45_step(const Ctx &c, const double y[6], const double k1[6], double h, double yn[6],
                 double e[6]) {
     double k2[6], k3[6], k4[6], k5[6], k6[6], t[6];
@@ -384,13 +386,12 @@ void rkf45_step(const Ctx &c, const double y[6], const double k1[6], double h, d
                            1859.0 / 4104.0 * k4[i] - 11.0 / 40.0 * k5[i]);
     rhs(c, t, k6, nullptr);
     for (int i = 0; i < 6; ++i) {
-        const double y4 = y[i] + h * (25.0 / 216.0 * k1[i] + 1408.0 / 2565.0 * k3[i] +
-                                      2197.0 / 4104.0 * k4[i] - k5[i] / 5.0);
-        const double y5 = y[i] + h * (16.0 / 135.0 * k1[i] + 6656.0 / 12825.0 * k3[i] +
-                                      28561.0 / 56430.0 * k4[i] - 9.0 / 50.0 * k5[i] +
-                                      2.0 / 55.0 * k6[i]);
-        yn[i] = y4;
-        e[i] = y5 - y4;
+        yn[i] = y[i] + h * (25.0 / 216.0 * k1[i] + 1408.0 / 2565.0 * k3[i] +
+                            2197.0 / 4104.0 * k4[i] - k5[i] / 5.0);
+        e[i] = h * ((16.0 / 135.0 - 25.0 / 216.0) * k1[i] +
+                    (6656.0 / 12825.0 - 1408.0 / 2565.0) * k3[i] +
+                    (28561.0 / 56430.0 - 2197.0 / 4104.0) * k4[i] +
+                    (-9.0 / 50.0 + 1.0 / 5.0) * k5[i] + 2.0 / 55.0 * k6[i]);
     }
 }
 
@@ -405,10 +406,15 @@ double rkf45_err(const double y[6], const double e[6], double rtol, double atol)
     return std::max(pos / (atol + rtol * r), kerr / (rtol * std::max(kmag, 1e-3)));
 }
 
-/* Step-size factor: 0.9 err^(-1/5), limited to [0.2, 5]. */
+/* Step-size factor: the classical 0.9 err^(-1/5) limited to [0.2, 5], then
+ * rounded down to a power of 2^(1/4).  Step sizes thus change only through
+ * discrete decisions; a continuous factor lets round-off in err feed back
+ * into the step sequence, which then diverges chaotically because the error
+ * estimate of a step that crosses a cell face of the C1 interpolant depends
+ * sharply on where the face falls inside the step. */
 double step_factor(double err) {
-    if (err == 0.0) return 5.0;
-    return std::min(5.0, std::max(0.2, 0.9 * std::pow(err, -0.2)));
+    const double fac = (err == 0.0) ? 5.0 : std::min(5.0, std::max(0.2, 0.9 * std::pow(err, -0.2)));
+    return std::exp2(std::floor(4.0 * std::log2(fac)) * 0.25);
 }
 
 /* Peak of the cubic Hermite fit of r(s), s in [0,1], through (r0, h*d0) and

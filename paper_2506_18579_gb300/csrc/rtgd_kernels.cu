@@ -289,7 +289,9 @@ __device__ void rk4_step64(const GridDev &g, const RayPhys<double> &rp, const do
     for (int i = 0; i < 6; ++i) yn[i] = y[i] + h / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
 }
 
-// Runge-Kutta-Fehlberg 4(5): fourth-order solution in yn, (5th - 4th) in e.
+// Runge-Kutta-Fehlberg 4(5): fourth-order solution in yn, local error
+// estimate (5th - 4th order) in e, formed as h sum((b5_i - b4_i) k_i) so it
+// keeps full relative precision (y5 - y4 would cancel against r ~ 6371 km).
 __device__ void rkf45_step64(const GridDev &g, const RayPhys<double> &rp, const double y[6], const double k1[6],
                              double h, double yn[6], double e[6]) {
     double k2[6], k3[6], k4[6], k5[6], k6[6], t[6];
@@ -314,12 +316,10 @@ __device__ void rkf45_step64(const GridDev &g, const RayPhys<double> &rp, const 
     rhs64(g, rp, t, k6, nullptr);
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-        const double y4 =
-            y[i] + h * (25.0 / 216.0 * k1[i] + 1408.0 / 2565.0 * k3[i] + 2197.0 / 4104.0 * k4[i] - k5[i] / 5.0);
-        const double y5 = y[i] + h * (16.0 / 135.0 * k1[i] + 6656.0 / 12825.0 * k3[i] + 28561.0 / 56430.0 * k4[i] -
-                                      9.0 / 50.0 * k5[i] + 2.0 / 55.0 * k6[i]);
-        yn[i] = y4;
-        e[i] = y5 - y4;
+        yn[i] = y[i] + h * (25.0 / 216.0 * k1[i] + 1408.0 / 2565.0 * k3[i] + 2197.0 / 4104.0 * k4[i] - k5[i] / 5.0);
+        e[i] = h * ((16.0 / 135.0 - 25.0 / 216.0) * k1[i] + (6656.0 / 12825.0 - 1408.0 / 2565.0) * k3[i] +
+                    (28561.0 / 56430.0 - 2197.0 / 4104.0) * k4[i] + (1.0 / 5.0 - 9.0 / 50.0) * k5[i] +
+                    2.0 / 55.0 * k6[i]);
     }
 }
 
@@ -331,10 +331,13 @@ __device__ __forceinline__ R rkf45_err(R r, R sth, R kmag, const R e[6], R rtol,
     return fmax(pos / (atol + rtol * r), kerr / (rtol * fmax(kmag, R(1e-3))));
 }
 
+// Step-size factor: 0.9 err^(-1/5) limited to [0.2, 5], rounded down to a
+// power of 2^(1/4), so step sizes change through discrete decisions only and
+// round-off in err cannot feed back into the step sequence.
 template <typename R>
-__device__ __forceinline__ R step_factor(R err) {
-    if (err == R(0)) return R(5);
-    return fmin(R(5), fmax(R(0.2), R(0.9) * pow(err, R(-0.2))));
+__device__ __forceinline__ double step_factor(R err) {
+    const R fac = (err == R(0)) ? R(5) : fmin(R(5), fmax(R(0.2), R(0.9) * pow(err, R(-0.2))));
+    return exp2(floor(4.0 * log2((double)fac)) * 0.25);
 }
 
 // Launch direction (elevation above the horizontal, azimuth clockwise from
@@ -775,7 +778,7 @@ __device__ bool lane_advance(Lane &L, const GridDev &g, const FanDev &f, const T
     if (f.integrator == RT_RKF45) {
         const float kmag = sqrtf(L.b.k[0] * L.b.k[0] + L.b.k[1] * L.b.k[1] + L.b.k[2] * L.b.k[2]);
         const float err = rkf45_err<float>(L.b.r, sinf(L.b.th), kmag, ef, f.rtol_f, f.atol_f);
-        const double fac = (double)step_factor<float>(err);
+        const double fac = step_factor<float>(err);
         if (!(err <= 1.0f)) {
             L.h = L.hs * fac;
             if (L.h < f.hmin) {

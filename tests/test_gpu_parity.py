@@ -137,8 +137,11 @@ def test_mixed_config2_full_size(orc):
         for kern in (rt.RT_KERNEL_PLAIN, rt.RT_KERNEL_PERSISTENT):
             outs[(st, kern)] = rt.rt_trace(g, fan, cfg=rt.launch_config(kernel=kern, stencil=st))
     base = outs[(rt.RT_STENCIL_QUAD, rt.RT_KERNEL_PERSISTENT)]
-    for k, v in outs.items():  # same arithmetic, same samples: bitwise equal
-        assert v.tobytes() == base.tobytes(), k
+    for k, v in outs.items():  # same samples and arithmetic up to FMA contraction
+        assert np.array_equal(v["status"], base["status"]), k
+        for f in ("group_path_km", "ground_range_km"):
+            assert np.abs(v[f] - base[f]).max() < 1e-7, (k, f)
+        assert np.abs(v["az_dev_deg"] - base["az_dev_deg"]).max() < 1e-9, k
     ref64 = rt.rt_trace(g, rt.Fan(w.fan, rt.RT_FP64))
     ok = ~near_boundary(ref64, w.fan)
     assert ok.mean() > 0.9

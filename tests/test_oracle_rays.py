@@ -195,3 +195,16 @@ def test_statuses(orc):
     # a step-size floor above what the tolerance needs
     r = orc.trace_fan(g, _fan(integrator=wl.RKF45, rtol=1e-14, atol_km=1e-14, h_min_km=0.5))[0]
     assert r["status"] == orc.STEP_UNDERFLOW
+
+
+def test_rkf45_step_sequence_is_well_conditioned(orc):
+    """With the step factor quantised to powers of 2^(1/4), perturbing the
+    launch elevations by 1 part in 1e13 leaves every step sequence unchanged
+    and moves group paths by round-off only (a continuous factor makes the
+    sequence chaotic at C1 cell faces: km-level changes)."""
+    w = wl.config2(elev_step=12.0, az_step=90.0)
+    g = orc.Grid(w.grid, w.ne)
+    a = orc.trace_fan(g, w.fan)
+    b = orc.trace_fan(g, w.fan.replace(el_deg=w.fan.el_deg * (1 + 1e-13)))
+    assert np.array_equal(a["n_attempts"], b["n_attempts"])
+    assert np.abs(a["group_path_km"] - b["group_path_km"]).max() < 1e-7
