@@ -249,7 +249,7 @@ rt_err queue_trace(const rt_grid *grid, const rt_fan_desc *fan, rt_ray_result *o
     if (dev != grid->device) return fail(RT_EINVAL, "grid lives on device %d, current device is %d", grid->device, dev);
     const size_t n = fan_rays(fan);
     if (out_len < n) return fail(RT_EINVAL, "out_len %zu < %zu rays", out_len, n);
-    if (n > (size_t)1 << 40) return fail(RT_EINVAL, "fan too large");
+    if (n >= ((size_t)1 << 31)) return fail(RT_EINVAL, "fan too large (at most 2^31 - 1 rays)");
     LaunchPlan lp;
     int order = 0;
     if ((r = make_plan(grid, fan, n, cfg, &lp, &order)) != RT_OK) return r;
@@ -297,6 +297,9 @@ rt_err queue_trace(const rt_grid *grid, const rt_fan_desc *fan, rt_ray_result *o
     f.land_tol = fan->precision == RT_FP64 ? 1e-9 : 1e-5;
     f.rtol_f = (float)fan->rtol;
     f.atol_f = (float)fan->atol_km;
+    f.h0_f = (float)f.h0;
+    f.hmin_f = (float)f.hmin;
+    f.hmax_f = (float)f.hmax;
     if (e == cudaSuccess) e = launch_trace(grid->g, f, out_dev, counter, lp, st);
     const cudaError_t e2 = cudaFreeAsync(ws, st);
     if (e != cudaSuccess) return cuda_fail(e, "trace launch");
@@ -385,6 +388,10 @@ rt_err rt_grid_create(const rt_grid_desc *desc, const void *ne_host, rt_grid **o
     d.sa = (float)(-kRad2Deg / desc->dlat_deg);
     d.sb = (float)(kRad2Deg / desc->dlon_deg);
     d.sc = (float)(1.0 / desc->dalt_km);
+    d.R_Ef = (float)d.R_E;
+    d.mf[0] = (float)d.m[0];
+    d.mf[1] = (float)d.m[1];
+    d.mf[2] = (float)d.m[2];
     d.pad64 = g->pad64;
     d.pad32 = g->pad32;
     d.quad = g->quad;

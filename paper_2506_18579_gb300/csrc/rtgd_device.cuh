@@ -36,6 +36,7 @@ struct GridDev {
     double b0;                       // dipole strength (0: isotropic)
     double m[3];                     // unit vector to the geomagnetic north pole
     float sa, sb, sc;                // d(grid coord)/d(theta, phi, r): -rad2deg/dlat, rad2deg/dlon, 1/dalt
+    float R_Ef, mf[3];               // float copies of R_E and m
     const double *pad64;             // (n_lat+2)(n_lon+2)(n_alt+2) doubles
     const float *pad32;              // same, rounded to float
     const float4 *quad;              // (n_lat+2)(n_lon+2)(n_alt-1): samples k-1..k+2 of cell k
@@ -101,6 +102,11 @@ __device__ __forceinline__ void acc_row(R v, R dv, R wb, R db, R &s, R &sb, R &s
         out[3] = nc_;                                                             \
     } while (0)
 
+// 1/x: correctly rounded in double; in float the fast reciprocal (MUFU.RCP,
+// within 2 ulp), which is ample for the mixed path's tolerance.
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+__device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
+
 // Cell index and local coordinate along one axis; false outside [0, n-1].
 template <typename R>
 __device__ __forceinline__ bool cell_coord(R x, int n, int &i, R &t) {
@@ -157,13 +163,13 @@ template <typename R>
 __device__ __forceinline__ void appleton_hartree(R X, R L, R T, int mode, R &mu2, R &FX, R &FL, R &FT) {
     const R u = R(1) - X;
     const R S = sqrt(T * T + R(4) * L * u * u);
-    const R iS = R(1) / S;
+    const R iS = recip(S);
     if (mode > 0) {
         const R W = S + T;
-        const R iW = R(1) / W;
+        const R iW = recip(W);
         const R g = R(2) * L * u * iW;
         const R opg = R(1) + g;
-        const R iopg = R(1) / opg;
+        const R iopg = recip(opg);
         const R gX = R(2) * L * (R(4) * L * u * u * iS - W) * iW * iW;
         const R gL = R(2) * u * iW - R(4) * L * u * u * u * iS * iW * iW;
         const R gT = -g * iS;
@@ -178,7 +184,7 @@ __device__ __forceinline__ void appleton_hartree(R X, R L, R T, int mode, R &mu2
         const R SX = R(-4) * L * u * iS;
         const R SL = R(2) * u * u * iS;
         const R ST = T * iS;
-        const R iD = R(1) / D;
+        const R iD = recip(D);
         const R iD2 = iD * iD;
         mu2 = R(1) - N * iD;
         FX = (N * (R(-2) - SX) - (R(2) - R(4) * X) * D) * iD2;
@@ -217,7 +223,7 @@ __device__ __forceinline__ void ray_rhs(const RayPhys<R> &rp, const StageIn<R> &
         const R mr = mx * s.sth * s.cph + my * s.sth * s.sph + mz * s.cth;
         const R mt = mx * s.cth * s.cph + my * s.cth * s.sph - mz * s.sth;
         const R mp = -mx * s.sph + my * s.cph;
-        const R ir = R(1) / s.r;
+        const R ir = recip(s.r);
         const R q = rp.R_E * ir;
         const R A = rp.ab0 * q * q * q;  // Y = A (-2 m_r, m_th, m_ph)
         const R Y0 = R(-2) * A * mr, Y1 = A * mt, Y2 = A * mp;
@@ -228,7 +234,7 @@ __device__ __forceinline__ void ray_rhs(const RayPhys<R> &rp, const StageIn<R> &
         const R J20 = R(-3) * A * mp * ir, J21 = R(0), J22 = -A * (s.sth * mr + s.cth * mt);
         const R YY = Y0 * Y0 + Y1 * Y1 + Y2 * Y2;
         const R kY = kr * Y0 + kt * Y1 + kp * Y2;
-        const R ikk = R(1) / kk;
+        const R ikk = recip(kk);
         const R L = kY * kY * ikk;
         R T = YY - L;
         if (T < R(0)) T = R(0);
@@ -256,9 +262,9 @@ __device__ __forceinline__ void ray_rhs(const RayPhys<R> &rp, const StageIn<R> &
         // omega dH/domega: X, L and T all scale as omega^-2, |k|^2 as omega^-2
         G = -kk + s.X * FX + L * FL + T * FT;
     }
-    const R iG = R(1) / G;
-    const R ir = R(1) / s.r;
-    const R irs = ir / s.sth;
+    const R iG = recip(G);
+    const R ir = recip(s.r);
+    const R irs = ir * recip(s.sth);
     const R dr = -Hk0 * iG;
     const R dt = -Hk1 * iG * ir;
     const R dp = -Hk2 * iG * irs;

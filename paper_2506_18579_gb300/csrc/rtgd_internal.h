@@ -24,7 +24,7 @@ struct FanDev {
     double tx_r, tx_th, tx_ph;  // launch position (km, rad, rad)
     double h0, rtol, atol, hmin, hmax, max_path;
     double land_tol;            // |r - R_E| accepted by the landing solve (km)
-    float rtol_f, atol_f;
+    float rtol_f, atol_f, h0_f, hmin_f, hmax_f;
 };
 
 struct LaunchPlan {

@@ -15,6 +15,8 @@
 //   eval_rhs          : diagnostic evaluation of dy/dP' at given states.
 #include <cuda_runtime.h>
 #include <math.h>
+
+#include <cmath>
 #include <stdint.h>
 
 #include "rtgd.h"
@@ -483,40 +485,74 @@ __global__ void __launch_bounds__(128) trace_fp64_kernel(GridDev g, FanDev f, rt
 }
 
 // =============================================================== mixed path
-// The ray state (r, theta, phi, k) and group path stay in double.  A step
-// attempt starts from a "base": the grid cell and in-cell coordinates of the
-// state, computed once in double, plus float copies of the state.  Each stage
-// then works on float offsets delta from the base: its grid coordinates are
-// base + delta * (d coord / d state), so they keep the full resolution of the
-// base; everything after (weights, contraction, dipole, Appleton-Hartree,
-// Eq. 1) runs in float.  The accepted step adds the float increment to the
-// double state.
+// The ray state (r, theta, phi, k) and the group path stay in double.  Each
+// step attempt starts from a "base": the grid cell and in-cell coordinates of
+// the state plus float copies of r, k and of the sines and cosines of theta
+// and phi.  A stage works on float offsets delta from the base: its grid
+// coordinates are base + delta * (d coord / d state) (the coordinates are
+// linear in r, theta, phi), and sin/cos of theta + delta by angle addition,
+// so everything after (weights, contraction, dipole, Appleton-Hartree, Eq. 1)
+// runs in float without losing the base's resolution.  An accepted step adds
+// the float increment to the double state (the only FP64 arithmetic of a
+// step besides the group-path sum and the ground test); the base follows by
+// the same increment in float and is recomputed from the double state every
+// kResyncSteps accepted steps.  GB300 issues FP64 at 1/64 of the FP32 rate,
+// so the step bookkeeping must stay out of double precision.
+constexpr int kResyncSteps = 16;
+
 struct Base32 {
-    int ia, ib, ic;
-    float ta, tb, tc;
-    float r, th, ph;
+    int ia, ib, ic;            // cell of the base (may lie outside the grid)
+    float ta, tb, tc;          // in-cell coordinates
+    float r;                   // radius (km)
+    float sth, cth, sph, cph;  // sin/cos of colatitude and longitude
     float k[3];
 };
 
-__device__ __forceinline__ void make_base(const GridDev &g, const double y[6], Base32 &b) {
+// 2^(k/4) for k = -10..9: the quantised step factors (see step_factor).
+__constant__ float c_pow2q[20];
+
+__device__ __forceinline__ int clamp_cell(double f) { return (int)fmin(fmax(f, -1e6), 1e6); }
+
+// Base of a double state (double arithmetic; used at launch and to resync).
+__device__ void base_from_state(const GridDev &g, const double y[6], Base32 &b) {
     const double lat = 90.0 - y[1] * kRad2Deg;
     double lonrel = y[2] * kRad2Deg - g.lon0;
-    lonrel -= 360.0 * floor(lonrel / 360.0);
+    lonrel -= 360.0 * floor(lonrel * (1.0 / 360.0));
     const double xa = (lat - g.lat0) * g.inv_dlat;
     const double xb = lonrel * g.inv_dlon;
     const double xc = (y[0] - g.R_E - g.alt0) * g.inv_dalt;
     const double fa = floor(xa), fb = floor(xb), fc = floor(xc);
     // positions far outside the grid are clamped so the integer stays small; they
     // remain outside (and non-finite positions give NaN fractions, also outside)
-    b.ia = (int)fmin(fmax(fa, -1e6), 1e6);
-    b.ib = (int)fmin(fmax(fb, -1e6), 1e6);
-    b.ic = (int)fmin(fmax(fc, -1e6), 1e6);
+    b.ia = clamp_cell(fa);
+    b.ib = clamp_cell(fb);
+    b.ic = clamp_cell(fc);
     b.ta = (float)(xa - fa);
     b.tb = (float)(xb - fb);
     b.tc = (float)(xc - fc);
     b.r = (float)y[0];
-    b.th = (float)y[1];
-    b.ph = (float)y[2];
+    sincosf((float)y[1], &b.sth, &b.cth);
+    sincosf((float)y[2], &b.sph, &b.cph);
+    b.k[0] = (float)y[3];
+    b.k[1] = (float)y[4];
+    b.k[2] = (float)y[5];
+}
+
+__device__ __forceinline__ void shift_axis(int &i, float &t, float dt) {
+    const float u = t + dt;
+    const float fl = fminf(fmaxf(floorf(u), -1e6f), 1e6f);
+    i += (int)fl;
+    t = u - fl;
+}
+
+// Moves the base by the accepted increment d; y is the new double state.
+__device__ __forceinline__ void advance_base(const GridDev &g, Base32 &b, const float d[6], const double y[6]) {
+    shift_axis(b.ia, b.ta, g.sa * d[1]);
+    shift_axis(b.ib, b.tb, g.sb * d[2]);
+    shift_axis(b.ic, b.tc, g.sc * d[0]);
+    b.r = (float)y[0];
+    sincosf((float)y[1], &b.sth, &b.cth);
+    sincosf((float)y[2], &b.sph, &b.cph);
     b.k[0] = (float)y[3];
     b.k[1] = (float)y[4];
     b.k[2] = (float)y[5];
@@ -540,16 +576,24 @@ __device__ __forceinline__ bool stage_cell(int i0, float t, int n, int &i, float
     return true;
 }
 
-// dy/dP' (float) at base + delta.  STENCIL selects where the 64 samples come
-// from; kdir overrides the wave vector (used for the launch direction).
+// sin/cos of (x0 + d) from sin/cos of x0, for |d| well below 0.1 rad (series
+// error < d^7/5040).
+__device__ __forceinline__ void angle_add(float s0, float c0, float d, float &s, float &c) {
+    const float d2 = d * d;
+    const float sd = d * (1.0f - d2 * (1.0f / 6.0f) * (1.0f - d2 * 0.05f));
+    const float cd = 1.0f - 0.5f * d2 * (1.0f - d2 * (1.0f / 12.0f));
+    s = s0 * cd + c0 * sd;
+    c = c0 * cd - s0 * sd;
+}
+
+// dy/dP' (float) at base + delta.  STENCIL selects where the 64 samples come from.
 template <int STENCIL>
 __device__ __forceinline__ void rhs_mixed(const GridDev &g, const RayPhys<float> &rp, const Base32 &b,
                                           const float d[6], float dy[6], float *mu2) {
     StageIn<float> s;
     s.r = b.r + d[0];
-    const float th = b.th + d[1], ph = b.ph + d[2];
-    sincosf(th, &s.sth, &s.cth);
-    sincosf(ph, &s.sph, &s.cph);
+    angle_add(b.sth, b.cth, d[1], s.sth, s.cth);
+    angle_add(b.sph, b.cph, d[2], s.sph, s.cph);
     s.k[0] = b.k[0] + d[3];
     s.k[1] = b.k[1] + d[4];
     s.k[2] = b.k[2] + d[5];
@@ -567,39 +611,39 @@ __device__ __forceinline__ void rhs_mixed(const GridDev &g, const RayPhys<float>
             // quad (pi, pj, k): 4 samples of cell k in padded row (pi, pj); node i-1 -> padded i
             const long long sj = g.q_alt, si = (long long)(g.n_lon + 2) * g.q_alt;
             const float4 *q = g.quad + (long long)ia * si + (long long)ib * sj + ic;
-#define RTGD_ROWQ(a, b, u0, u1, u2, u3)               \
-    {                                                 \
+#define RTGD_ROWQ(a, b, u0, u1, u2, u3)                   \
+    {                                                     \
         const float4 v_ = __ldg(q + (a) * si + (b) * sj); \
-        u0 = v_.x;                                    \
-        u1 = v_.y;                                    \
-        u2 = v_.z;                                    \
-        u3 = v_.w;                                    \
+        u0 = v_.x;                                        \
+        u1 = v_.y;                                        \
+        u2 = v_.z;                                        \
+        u3 = v_.w;                                        \
     }
             RTGD_CONTRACT(float, RTGD_ROWQ, wa, da, wb, db, wc, dc, out);
 #undef RTGD_ROWQ
         } else if (STENCIL == RT_STENCIL_TABLE) {
             const long long cell = ((long long)ia * (g.n_lon - 1) + ib) * (g.n_alt - 1) + ic;
             const float4 *q = g.table + cell * 16;
-#define RTGD_ROWT(a, b, u0, u1, u2, u3)         \
-    {                                           \
+#define RTGD_ROWT(a, b, u0, u1, u2, u3)             \
+    {                                               \
         const float4 v_ = __ldg(q + (a) * 4 + (b)); \
-        u0 = v_.x;                              \
-        u1 = v_.y;                              \
-        u2 = v_.z;                              \
-        u3 = v_.w;                              \
+        u0 = v_.x;                                  \
+        u1 = v_.y;                                  \
+        u2 = v_.z;                                  \
+        u3 = v_.w;                                  \
     }
             RTGD_CONTRACT(float, RTGD_ROWT, wa, da, wb, db, wc, dc, out);
 #undef RTGD_ROWT
         } else {
             const long long sj = g.p_alt, si = (long long)g.p_lon * g.p_alt;
             const float *p = g.pad32 + (long long)ia * si + (long long)ib * sj + ic;
-#define RTGD_ROWG(a, b, u0, u1, u2, u3)              \
-    {                                                \
-        const float *p_ = p + (a) * si + (b) * sj;   \
-        u0 = __ldg(p_);                              \
-        u1 = __ldg(p_ + 1);                          \
-        u2 = __ldg(p_ + 2);                          \
-        u3 = __ldg(p_ + 3);                          \
+#define RTGD_ROWG(a, b, u0, u1, u2, u3)            \
+    {                                              \
+        const float *p_ = p + (a) * si + (b) * sj; \
+        u0 = __ldg(p_);                            \
+        u1 = __ldg(p_ + 1);                        \
+        u2 = __ldg(p_ + 2);                        \
+        u3 = __ldg(p_ + 3);                        \
     }
             RTGD_CONTRACT(float, RTGD_ROWG, wa, da, wb, db, wc, dc, out);
 #undef RTGD_ROWG
@@ -625,57 +669,100 @@ struct Tableau {
 
 __constant__ Tableau c_tab[2];  // [RT_RK4], [RT_RKF45]
 
+// Quantised step factor in float (the mixed path's counterpart of step_factor).
+__device__ __forceinline__ float step_factor_f(float err) {
+    const float fac = (err == 0.0f) ? 5.0f : fminf(5.0f, fmaxf(0.2f, 0.9f * __powf(err, -0.2f)));
+    int k = (int)floorf(4.0f * __log2f(fac));
+    k = k < -10 ? -10 : (k > 9 ? 9 : k);
+    return c_pow2q[k + 10];
+}
+
+// Peak rise of the cubic Hermite fit over one step, relative to its start:
+// p(s) = m0 s + B s^2 + A s^3 with p(1) = dr, p'(0) = m0 > 0 >= p'(1) = m1.
+__device__ __forceinline__ float hermite_rise_f(float dr, float m0, float m1) {
+    const float A = m0 + m1 - 2.0f * dr, B = 3.0f * dr - 2.0f * m0 - m1;
+    float lo = 0.0f, hi = 1.0f;
+    for (int it = 0; it < 24; ++it) {
+        const float mid = 0.5f * (lo + hi);
+        if (m0 + 2.0f * B * mid + 3.0f * A * mid * mid > 0.0f) lo = mid;
+        else hi = mid;
+    }
+    const float s = 0.5f * (lo + hi);
+    return s * (m0 + s * (B + s * A));
+}
+
 // Per-lane state of the mixed tracer.
 struct Lane {
-    long long out_id;
     double y[6];
-    double P, h, hs, apo;
-    double r_prev, h_prev;
-    double la, lfa, lb, lfb;  // landing bracket
-    float dr_prev;
+    double P;
+    double r_prev;            // radius at the start of the last accepted step
+    double la, lfa, lb, lfb;  // landing bracket (step size, r - R_E)
+    float h, hs;              // next step / step of the current attempt (km)
+    float h_prev, dr_prev;    // last accepted step and its dr/dP' at the start
+    float apo;                // reflection height so far (km)
     float acc[5][6];
     float y4[6], e[6];
     float k1[6];
-    RayPhys<float> rp;
+    float xfac, ab0;
     Base32 b;
-    double az;
-    int stage, n_steps, n_att, n_ev, status, side, land_it;
+    int out_id, mode;
+    int stage, n_steps, n_att, n_ev, status, side, land_it, since_sync;
     bool active, launch, landing, have_prev, k1_valid;
 };
+
+__device__ __forceinline__ RayPhys<float> lane_phys(const GridDev &g, const Lane &L) {
+    RayPhys<float> p;
+    p.xfac = L.xfac;
+    p.ab0 = L.ab0;
+    p.R_E = g.R_Ef;
+    p.m[0] = g.mf[0];
+    p.m[1] = g.mf[1];
+    p.m[2] = g.mf[2];
+    p.iso = g.b0 == 0.0;
+    p.mode = L.mode;
+    return p;
+}
 
 // Fills acc/y4/e from stage s output ks.
 __device__ __forceinline__ void accumulate(Lane &L, const Tableau &T, int s, const float ks[6]) {
     const bool first = s == 0;  // stage 0 starts a fresh attempt
+    float A[5];
+#pragma unroll
+    for (int t = 0; t < 5; ++t) A[t] = T.A[s][t];
+    const float b4 = T.B4[s], e = T.E[s];
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
 #pragma unroll
-        for (int t = 0; t < 4; ++t) L.acc[t][c] = (first ? 0.0f : L.acc[t + 1][c]) + T.A[s][t] * ks[c];
-        L.acc[4][c] = T.A[s][4] * ks[c];
-        L.y4[c] = (first ? 0.0f : L.y4[c]) + T.B4[s] * ks[c];
-        L.e[c] = (first ? 0.0f : L.e[c]) + T.E[s] * ks[c];
+        for (int t = 0; t < 4; ++t) L.acc[t][c] = (first ? 0.0f : L.acc[t + 1][c]) + A[t] * ks[c];
+        L.acc[4][c] = A[4] * ks[c];
+        L.y4[c] = (first ? 0.0f : L.y4[c]) + b4 * ks[c];
+        L.e[c] = (first ? 0.0f : L.e[c]) + e * ks[c];
     }
 }
 
 __device__ void lane_begin_ray(Lane &L, const GridDev &g, const FanDev &f, long long id) {
     const RayParams p = ray_params(f, id);
-    L.out_id = id;
-    L.rp = make_phys<float>(g, p.f_hz, p.mode);
-    L.az = p.az;
+    L.out_id = (int)id;
+    L.xfac = (float)(kPlasmaHz2PerM3 / (p.f_hz * p.f_hz));
+    L.ab0 = (float)(kGyroHzPerTesla / p.f_hz * g.b0);
+    L.mode = p.mode;
     launch_dir(f, p, L.y);
     L.P = 0.0;
-    L.h = f.h0;
-    L.apo = f.tx_r - g.R_E;
+    L.h = f.h0_f;
+    L.apo = (float)(f.tx_r - g.R_E);
     L.n_steps = L.n_att = L.n_ev = 0;
+    L.since_sync = 0;
     L.status = RT_RAY_NOT_RUN;
     L.have_prev = L.k1_valid = L.landing = false;
     L.launch = true;
     L.stage = 0;
-    make_base(g, L.y, L.b);
+    base_from_state(g, L.y, L.b);
 }
 
 __device__ __forceinline__ void lane_finish(Lane &L, const GridDev &g, const FanDev &f, rt_ray_result *out) {
     rt_ray_result r;
-    finish_result(f, L.az, L.y, L.P, L.apo, L.status, L.n_steps, L.n_att, L.n_ev, g.R_E, &r);
+    const double az = f.az[L.out_id % f.n_az] * kDeg2Rad;
+    finish_result(f, az, L.y, L.P, (double)L.apo, L.status, L.n_steps, L.n_att, L.n_ev, g.R_E, &r);
     out[L.out_id] = r;
     L.active = false;
 }
@@ -689,7 +776,7 @@ __device__ __forceinline__ bool lane_begin_attempt(Lane &L, const FanDev &f, con
     }
     if (!L.landing) {
         L.hs = L.h;
-        if (f.max_path > 0.0 && L.P + L.hs > f.max_path) L.hs = f.max_path - L.P;
+        if (f.max_path > 0.0 && L.P + (double)L.hs > f.max_path) L.hs = (float)(f.max_path - L.P);
     }
     if (L.k1_valid) {  // k1 at this state is known: start at stage 1
         accumulate(L, T, 0, L.k1);
@@ -705,13 +792,14 @@ __device__ __forceinline__ bool lane_begin_attempt(Lane &L, const FanDev &f, con
 template <int STENCIL>
 __device__ bool lane_advance(Lane &L, const GridDev &g, const FanDev &f, const Tableau &T) {
     const double RE = g.R_E;
+    const RayPhys<float> rp = lane_phys(g, L);
     float d[6], ks[6], mu2;
     ++L.n_ev;
     if (L.launch) {
         // mu^2 at the transmitter for the launch direction (|k| = 1 in the base)
 #pragma unroll
         for (int c = 0; c < 6; ++c) d[c] = 0.0f;
-        rhs_mixed<STENCIL>(g, L.rp, L.b, d, ks, &mu2);
+        rhs_mixed<STENCIL>(g, rp, L.b, d, ks, &mu2);
         L.launch = false;
         if (!(mu2 > 0.0f)) {
             L.status = RT_RAY_NONFINITE;
@@ -721,19 +809,23 @@ __device__ bool lane_advance(Lane &L, const GridDev &g, const FanDev &f, const T
         L.y[3] *= mu;
         L.y[4] *= mu;
         L.y[5] *= mu;
-        make_base(g, L.y, L.b);
+        L.b.k[0] = (float)L.y[3];
+        L.b.k[1] = (float)L.y[4];
+        L.b.k[2] = (float)L.y[5];
         return !lane_begin_attempt(L, f, T);
     }
-    const float hf = (float)L.hs;
+    const float hf = L.hs;
 #pragma unroll
     for (int c = 0; c < 6; ++c) d[c] = (L.stage == 0) ? 0.0f : hf * L.acc[0][c];
-    rhs_mixed<STENCIL>(g, L.rp, L.b, d, ks, nullptr);
+    rhs_mixed<STENCIL>(g, rp, L.b, d, ks, nullptr);
     if (L.stage == 0) {
 #pragma unroll
         for (int c = 0; c < 6; ++c) L.k1[c] = ks[c];
         L.k1_valid = true;
-        if (L.have_prev && L.dr_prev > 0.0f && ks[0] <= 0.0f)
-            L.apo = fmax(L.apo, hermite_peak(L.r_prev, L.y[0], (double)L.dr_prev, (double)ks[0], L.h_prev) - RE);
+        if (L.have_prev && L.dr_prev > 0.0f && ks[0] <= 0.0f) {
+            const float rise = hermite_rise_f((float)(L.y[0] - L.r_prev), L.h_prev * L.dr_prev, L.h_prev * ks[0]);
+            L.apo = fmaxf(L.apo, (float)(L.r_prev - RE) + rise);
+        }
         L.have_prev = false;
     }
     accumulate(L, T, L.stage, ks);
@@ -742,105 +834,130 @@ __device__ bool lane_advance(Lane &L, const GridDev &g, const FanDev &f, const T
     // ---- attempt complete: increments in float, state update in double
     ++L.n_att;
     float dy4[6], ef[6];
+    bool fin = true;
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
         dy4[c] = hf * L.y4[c];
         ef[c] = hf * L.e[c];
+        fin = fin && isfinite(dy4[c]);
     }
     if (L.landing) {
         // Illinois regula falsi on the step size: f(h*) = r(step(h*)) - R_E
         const double fc = (L.y[0] - RE) + (double)dy4[0];
         ++L.land_it;
-        const bool done = fabs(fc) < f.land_tol || L.land_it >= 60 || fabs(L.lb - L.la) < 1e-12;
+        const double c = (double)L.hs;
+        const bool done = fabs(fc) < f.land_tol || L.land_it >= 60 || fabs(L.lb - L.la) < 1e-9 || !fin;
         if (!done) {
             if (fc < 0.0) {
-                L.lb = L.hs;
+                L.lb = c;
                 L.lfb = fc;
                 if (L.side == -1) L.lfa *= 0.5;
                 L.side = -1;
             } else {
-                L.la = L.hs;
+                L.la = c;
                 L.lfa = fc;
                 if (L.side == 1) L.lfb *= 0.5;
                 L.side = 1;
             }
-            L.hs = L.lb - L.lfb * (L.lb - L.la) / (L.lfb - L.lfa);
+            L.hs = (float)(L.lb - L.lfb * (L.lb - L.la) / (L.lfb - L.lfa));
             return !lane_begin_attempt(L, f, T);
         }
-        L.P += L.hs;
+        if (!fin) {
+            L.status = RT_RAY_NONFINITE;
+            return true;
+        }
+        L.P += c;
         ++L.n_steps;
 #pragma unroll
-        for (int c = 0; c < 6; ++c) L.y[c] += (double)dy4[c];
+        for (int i = 0; i < 6; ++i) L.y[i] += (double)dy4[i];
         L.status = RT_RAY_LANDED;
         return true;
     }
-    double h_next = L.h;
+    float h_next = L.h;
     if (f.integrator == RT_RKF45) {
         const float kmag = sqrtf(L.b.k[0] * L.b.k[0] + L.b.k[1] * L.b.k[1] + L.b.k[2] * L.b.k[2]);
-        const float err = rkf45_err<float>(L.b.r, sinf(L.b.th), kmag, ef, f.rtol_f, f.atol_f);
-        const double fac = step_factor<float>(err);
+        const float err = rkf45_err<float>(L.b.r, L.b.sth, kmag, ef, f.rtol_f, f.atol_f);
+        const float fac = step_factor_f(err);
         if (!(err <= 1.0f)) {
             L.h = L.hs * fac;
-            if (L.h < f.hmin) {
+            if (L.h < f.hmin_f) {
                 L.status = RT_RAY_STEP_UNDERFLOW;
                 return true;
             }
             return !lane_begin_attempt(L, f, T);
         }
-        h_next = fmin(fmax(L.hs * fac, f.hmin), f.hmax);
+        h_next = fminf(fmaxf(L.hs * fac, f.hmin_f), f.hmax_f);
     }
-    double yn[6];
-#pragma unroll
-    for (int c = 0; c < 6; ++c) yn[c] = L.y[c] + (double)dy4[c];
-    if (!finite6(yn)) {
+    if (!fin) {
         L.status = RT_RAY_NONFINITE;
         return true;
     }
-    if (yn[0] < RE) {
+    const double r_new = L.y[0] + (double)dy4[0];
+    if (r_new < RE) {
         L.landing = true;
         L.la = 0.0;
         L.lfa = L.y[0] - RE;
-        L.lb = L.hs;
-        L.lfb = yn[0] - RE;
+        L.lb = (double)L.hs;
+        L.lfb = r_new - RE;
         L.side = 0;
         L.land_it = 0;
-        L.hs = L.lb - L.lfb * (L.lb - L.la) / (L.lfb - L.lfa);
+        L.hs = (float)(L.lb - L.lfb * (L.lb - L.la) / (L.lfb - L.lfa));
         return !lane_begin_attempt(L, f, T);
     }
-    L.P += L.hs;
-    ++L.n_steps;
-    L.apo = fmax(L.apo, yn[0] - RE);
-    L.have_prev = true;
     L.r_prev = L.y[0];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) L.y[i] += (double)dy4[i];
+    L.P += (double)L.hs;
+    ++L.n_steps;
+    const double alt = r_new - RE;
+    L.apo = fmaxf(L.apo, (float)alt);
+    L.have_prev = true;
     L.dr_prev = L.k1[0];
     L.h_prev = L.hs;
-#pragma unroll
-    for (int c = 0; c < 6; ++c) L.y[c] = yn[c];
     L.k1_valid = false;
-    const double alt = yn[0] - RE;
     if (alt > g.top) {
         L.status = RT_RAY_ESCAPED;
         return true;
     }
-    if (alt >= g.alt0 && !inside_latlon(g, yn[1], yn[2])) {
-        L.status = RT_RAY_LEFT_GRID;
-        return true;
+    if (++L.since_sync >= kResyncSteps) {
+        L.since_sync = 0;
+        base_from_state(g, L.y, L.b);
+    } else {
+        advance_base(g, L.b, dy4, L.y);
     }
-    if (f.max_path > 0.0 && L.P >= f.max_path - 1e-12) {
+    if (alt >= g.alt0) {
+        const bool in_lat = L.b.ia >= 0 && (L.b.ia < g.n_lat - 1 || (L.b.ia == g.n_lat - 1 && L.b.ta == 0.0f));
+        const bool in_lon = L.b.ib >= 0 && (L.b.ib < g.n_lon - 1 || (L.b.ib == g.n_lon - 1 && L.b.tb == 0.0f));
+        if (!(in_lat && in_lon)) {
+            L.status = RT_RAY_LEFT_GRID;
+            return true;
+        }
+    }
+    if (f.max_path > 0.0 && L.P >= f.max_path - 1e-6) {
         L.status = RT_RAY_MAX_PATH;
         return true;
     }
     L.h = h_next;
-    make_base(g, L.y, L.b);
     return !lane_begin_attempt(L, f, T);
+}
+
+// Loads the Butcher table of the fan's integrator into shared memory (lanes
+// at different stages then read it without constant-cache serialisation).
+__device__ __forceinline__ void load_tableau(Tableau &T, int integrator) {
+    const Tableau &src = c_tab[integrator == RT_RKF45 ? 1 : 0];
+    const float *s = (const float *)&src;
+    float *d = (float *)&T;
+    for (int i = threadIdx.x; i < (int)(sizeof(Tableau) / sizeof(float)); i += blockDim.x) d[i] = s[i];
+    __syncthreads();
 }
 
 // One ray per thread; each thread loops stage by stage until its ray ends.
 template <int STENCIL>
 __global__ void __launch_bounds__(128) trace_mixed_plain_kernel(GridDev g, FanDev f, rt_ray_result *__restrict__ out) {
+    __shared__ Tableau T;
+    load_tableau(T, f.integrator);
     const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (id >= f.n_rays) return;
-    const Tableau &T = c_tab[f.integrator == RT_RKF45 ? 1 : 0];
     Lane L;
     L.active = true;
     lane_begin_ray(L, g, f, claim_to_ray(f, id));
@@ -858,9 +975,10 @@ template <int STENCIL>
 __global__ void __launch_bounds__(128) trace_mixed_persistent_kernel(GridDev g, FanDev f,
                                                                      rt_ray_result *__restrict__ out,
                                                                      unsigned long long *__restrict__ counter) {
+    __shared__ Tableau T;
+    load_tableau(T, f.integrator);
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const Tableau &T = c_tab[f.integrator == RT_RKF45 ? 1 : 0];
     Lane L;
     L.active = false;
     bool exhausted = false;  // warp-uniform
@@ -913,7 +1031,7 @@ __global__ void eval_rhs_kernel(GridDev g, const double *__restrict__ ys, double
     } else {
         const RayPhys<float> rp = make_phys<float>(g, freq_mhz * 1e6, mode);
         Base32 b;
-        make_base(g, y, b);
+        base_from_state(g, y, b);
         float d[6] = {0, 0, 0, 0, 0, 0}, dyf[6], m2;
         if (stencil == RT_STENCIL_TABLE) rhs_mixed<RT_STENCIL_TABLE>(g, rp, b, d, dyf, &m2);
         else if (stencil == RT_STENCIL_GATHER) rhs_mixed<RT_STENCIL_GATHER>(g, rp, b, d, dyf, &m2);
@@ -976,7 +1094,11 @@ static void fill_tableaus(Tableau tab[2]) {
 cudaError_t upload_tableaus() {
     Tableau tab[2];
     fill_tableaus(tab);
-    return cudaMemcpyToSymbol(c_tab, tab, sizeof(tab));
+    cudaError_t e = cudaMemcpyToSymbol(c_tab, tab, sizeof(tab));
+    if (e != cudaSuccess) return e;
+    float q[20];
+    for (int k = -10; k <= 9; ++k) q[k + 10] = (float)std::exp2(k * 0.25);
+    return cudaMemcpyToSymbol(c_pow2q, q, sizeof(q));
 }
 
 template <int STENCIL>
