@@ -118,11 +118,16 @@ enum {
  *     accepted when err <= 1 with err = max(pos_err / (atol_km + rtol * r),
  *     k_err / (rtol * max(|k|, 1e-3))), pos_err = max(|dr|, r|dtheta|,
  *     r sin(theta)|dphi|) and k_err = max|dk_i| (k in units of omega/c),
- *     the error estimate being h * sum((b5_i - b4_i) k_i); the next step is
- *     h * 2^(floor(4 log2(f)) / 4) with f = min(5, max(0.2, 0.9 err^-0.2))
- *     (the factor quantised to powers of 2^(1/4) so that round-off cannot
- *     steer the step sequence), clamped to [h_min_km, h_max_km]; a rejected
- *     step below h_min_km stops the ray.
+ *     the error estimate being h * sum((b5_i - b4_i) k_i).  The nominal
+ *     step h changes only by its quantised factor q = 2^(floor(4 log2(f))/4),
+ *     f = min(5, max(0.2, 0.9 err^-0.2)): h *= q after a rejection or an
+ *     accepted step, clamped to [h_min_km, h_max_km]; a rejected step below
+ *     h_min_km stops the ray.  An attempt whose step would cross a cell face
+ *     of the interpolant (where its second derivatives jump), predicted
+ *     linearly from dy/dP' at the step start, is shortened to end 1e-4 of
+ *     its length past that face; such a step never enlarges h (q <= 1).
+ *     Both rules keep the step sequence a function of discrete decisions,
+ *     so round-off cannot steer it.
  *   max_steps bounds the RK step attempts of one ray (rejected steps and
  *     landing-solve trial steps included).
  *   max_group_path_km > 0 stops the ray at exactly that group path. */

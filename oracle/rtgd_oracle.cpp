@@ -500,6 +500,34 @@ void push_traj(double *traj, int32_t cap, int32_t *len, double P, const double y
     ++*len;
 }
 
+/* Group path to the next cell face of the interpolant that the ray reaches,
+ * predicted linearly from dy/dP' = k1 at y.  Faces are where the C1
+ * interpolant's second derivatives jump (the right-hand side is only C0
+ * there); the grid's outer faces count too.  Lateral faces count only while
+ * the ray is inside the altitude span (below it Ne = 0).  Infinite if none. */
+double face_distance(const or_grid &g, const double y[6], const double k1[6]) {
+    Dual xa, xb, xc;
+    grid_coords(g, cst(y[0]), cst(y[1]), cst(y[2]), &xa, &xb, &xc);
+    const double x[3] = {xa.v, xb.v, xc.v};
+    const double v[3] = {-k1[1] / DEG / g.dlat_deg, k1[2] / DEG / g.dlon_deg, k1[0] / g.dalt_km};
+    const int n[3] = {g.n_lat, g.n_lon, g.n_alt};
+    const bool in_alt = x[2] >= 0.0 && x[2] <= g.n_alt - 1;
+    double best = HUGE_VAL;
+    for (int a = 0; a < 3; ++a) {
+        if (a < 2 && !in_alt) continue;
+        if (v[a] > 0.0) {
+            double F = std::floor(x[a]) + 1.0;
+            if (F < 0.0) F = 0.0;
+            if (F <= n[a] - 1) best = std::min(best, (F - x[a]) / v[a]);
+        } else if (v[a] < 0.0) {
+            double F = std::ceil(x[a]) - 1.0;
+            if (F > n[a] - 1) F = n[a] - 1;
+            if (F >= 0.0) best = std::min(best, (F - x[a]) / v[a]);
+        }
+    }
+    return best;
+}
+
 void trace(const or_grid &g, const or_ray &ray, or_result *res, double *traj, int32_t cap,
            int32_t *tlen) {
     *res = or_result{};
@@ -533,9 +561,18 @@ void trace(const or_grid &g, const or_ray &ray, or_result *res, double *traj, in
             break;
         }
         double hs = h;
-        if (ray.max_group_path_km > 0.0 && P + hs > ray.max_group_path_km) hs = ray.max_group_path_km - P;
         double k1[6];
         rhs(c, y, k1, nullptr);
+        /* adaptive steps end just past the next cell face instead of straddling it */
+        bool at_face = false;
+        if (adaptive) {
+            const double hf = face_distance(g, y, k1);
+            if (hf > 1e-3 * hs && hf < hs) {
+                hs = hf * (1.0 + 1e-4);
+                at_face = true;
+            }
+        }
+        if (ray.max_group_path_km > 0.0 && P + hs > ray.max_group_path_km) hs = ray.max_group_path_km - P;
         if (have_prev && dr_prev > 0.0 && k1[0] <= 0.0)
             apogee = std::max(apogee, hermite_peak(r_prev, y[0], dr_prev, k1[0], h_prev) - RE);
         have_prev = false;
@@ -547,12 +584,15 @@ void trace(const or_grid &g, const or_ray &ray, or_result *res, double *traj, in
         if (adaptive) {
             const double err = rkf45_err(y, e, ray.rtol, ray.atol_km);
             const double fac = step_factor(err);
+            /* the nominal step h changes only by quantised factors of itself, never
+             * through the length of a face-shortened step, so rounding in where a
+             * step ends cannot feed back into later step sizes */
             if (!(err <= 1.0)) {
-                h = hs * fac;
+                h = h * fac;
                 if (h < ray.h_min_km) status = OR_STEP_UNDERFLOW;
                 continue;
             }
-            h_next = std::min(std::max(hs * fac, ray.h_min_km), ray.h_max_km);
+            h_next = std::min(std::max(h * (at_face ? std::min(1.0, fac) : fac), ray.h_min_km), ray.h_max_km);
         }
         if (!finite6(yn)) {
             status = OR_NONFINITE;

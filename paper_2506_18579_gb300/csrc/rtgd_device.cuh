@@ -79,8 +79,11 @@ __device__ __forceinline__ void acc_row(R v, R dv, R wb, R db, R &s, R &sb, R &s
 }
 
 // out = {Ne, dNe/dxa, dNe/dxb, dNe/dxc} in per-cell units, from the 16 rows
-// of 4 altitude samples.  ROW(a, b, u0..u3) loads row (a, b).
-#define RTGD_CONTRACT(R, ROW, wa, da, wb, db, wc, dc, out)                        \
+// of 4 altitude samples.  ROW(a, b, u0..u3) loads row (a, b).  The samples
+// are contracted relative to REF (Ne = REF + sum (u - REF) w, the weights
+// summing to 1 and their derivatives to 0), so that in float the sums do not
+// cancel against the magnitude of Ne; REF = 0 gives the plain sum.
+#define RTGD_CONTRACT(R, ROW, REF, wa, da, wb, db, wc, dc, out)                   \
     do {                                                                          \
         R n_ = R(0), na_ = R(0), nb_ = R(0), nc_ = R(0);                          \
         _Pragma("unroll") for (int a_ = 0; a_ < 4; ++a_) {                        \
@@ -88,6 +91,10 @@ __device__ __forceinline__ void acc_row(R v, R dv, R wb, R db, R &s, R &sb, R &s
             _Pragma("unroll") for (int b_ = 0; b_ < 4; ++b_) {                    \
                 R u0_, u1_, u2_, u3_, v_, dv_;                                    \
                 ROW(a_, b_, u0_, u1_, u2_, u3_);                                  \
+                u0_ -= (REF);                                                     \
+                u1_ -= (REF);                                                     \
+                u2_ -= (REF);                                                     \
+                u3_ -= (REF);                                                     \
                 row4<R>(u0_, u1_, u2_, u3_, wc, dc, v_, dv_);                     \
                 acc_row<R>(v_, dv_, wb[b_], db[b_], s_, sb_, sc_);                \
             }                                                                     \
@@ -96,7 +103,7 @@ __device__ __forceinline__ void acc_row(R v, R dv, R wb, R db, R &s, R &sb, R &s
             nb_ += sb_ * wa[a_];                                                  \
             nc_ += sc_ * wa[a_];                                                  \
         }                                                                         \
-        out[0] = n_;                                                              \
+        out[0] = n_ + (REF);                                                      \
         out[1] = na_;                                                             \
         out[2] = nb_;                                                             \
         out[3] = nc_;                                                             \

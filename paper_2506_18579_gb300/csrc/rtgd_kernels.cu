@@ -265,7 +265,7 @@ __device__ void rhs64(const GridDev &g, const RayPhys<double> &rp, const double 
         u2 = __ldg(p_ + 2);                           \
         u3 = __ldg(p_ + 3);                           \
     }
-        RTGD_CONTRACT(double, RTGD_ROW64, wa, da, wb, db, wc, dc, out);
+        RTGD_CONTRACT(double, RTGD_ROW64, 0.0, wa, da, wb, db, wc, dc, out);
 #undef RTGD_ROW64
         s.X = rp.xfac * out[0];
         s.dX[0] = rp.xfac * out[3] * g.inv_dalt;
@@ -356,6 +356,36 @@ __device__ __forceinline__ void launch_dir(const FanDev &f, const RayParams &p, 
     y[5] = ce * sa;
 }
 
+// Group path to the next cell face the ray reaches, predicted linearly from
+// dy/dP' = k1.  Faces are where the C1 interpolant's second derivatives jump
+// (the right-hand side is only C0 there), the grid's outer faces included;
+// lateral faces count only inside the altitude span.  Adaptive steps end just
+// past such a face instead of straddling it.
+__device__ double face_distance64(const GridDev &g, const double y[6], const double k1[6]) {
+    const double lat = 90.0 - y[1] * kRad2Deg;
+    double lonrel = y[2] * kRad2Deg - g.lon0;
+    lonrel -= 360.0 * floor(lonrel * (1.0 / 360.0));
+    const double x[3] = {(lat - g.lat0) * g.inv_dlat, lonrel * g.inv_dlon, (y[0] - g.R_E - g.alt0) * g.inv_dalt};
+    const double v[3] = {-k1[1] * kRad2Deg * g.inv_dlat, k1[2] * kRad2Deg * g.inv_dlon, k1[0] * g.inv_dalt};
+    const int n[3] = {g.n_lat, g.n_lon, g.n_alt};
+    const bool in_alt = x[2] >= 0.0 && x[2] <= (double)(g.n_alt - 1);
+    double best = HUGE_VAL;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (a < 2 && !in_alt) continue;
+        if (v[a] > 0.0) {
+            double F = floor(x[a]) + 1.0;
+            if (F < 0.0) F = 0.0;
+            if (F <= (double)(n[a] - 1)) best = fmin(best, (F - x[a]) / v[a]);
+        } else if (v[a] < 0.0) {
+            double F = ceil(x[a]) - 1.0;
+            if (F > (double)(n[a] - 1)) F = (double)(n[a] - 1);
+            if (F >= 0.0) best = fmin(best, (F - x[a]) / v[a]);
+        }
+    }
+    return best;
+}
+
 __device__ void trace_ray_fp64(const GridDev &g, const FanDev &f, long long id, rt_ray_result *out) {
     const RayParams p = ray_params(f, id);
     const RayPhys<double> rp = make_phys<double>(g, p.f_hz, p.mode);
@@ -384,12 +414,20 @@ __device__ void trace_ray_fp64(const GridDev &g, const FanDev &f, long long id, 
             break;
         }
         double hs = h;
-        if (f.max_path > 0.0 && P + hs > f.max_path) hs = f.max_path - P;
         if (!k1_valid) {
             rhs64(g, rp, y, k1, nullptr);
             k1_valid = true;
             ++n_ev;
         }
+        bool at_face = false;
+        if (adaptive) {
+            const double hf = face_distance64(g, y, k1);
+            if (hf > 1e-3 * hs && hf < hs) {
+                hs = hf * (1.0 + 1e-4);
+                at_face = true;
+            }
+        }
+        if (f.max_path > 0.0 && P + hs > f.max_path) hs = f.max_path - P;
         if (have_prev && dr_prev > 0.0 && k1[0] <= 0.0)
             apo = fmax(apo, hermite_peak(r_prev, y[0], dr_prev, k1[0], h_prev) - RE);
         have_prev = false;
@@ -403,12 +441,13 @@ __device__ void trace_ray_fp64(const GridDev &g, const FanDev &f, long long id, 
             const double err = rkf45_err<double>(y[0], sin(y[1]), sqrt(y[3] * y[3] + y[4] * y[4] + y[5] * y[5]), e,
                                                  f.rtol, f.atol);
             const double fac = step_factor<double>(err);
+            // the nominal step changes only by quantised factors of itself
             if (!(err <= 1.0)) {
-                h = hs * fac;
+                h = h * fac;
                 if (h < f.hmin) status = RT_RAY_STEP_UNDERFLOW;
                 continue;
             }
-            h_next = fmin(fmax(hs * fac, f.hmin), f.hmax);
+            h_next = fmin(fmax(h * (at_face ? fmin(1.0, fac) : fac), f.hmin), f.hmax);
         }
         if (!finite6(yn)) {
             status = RT_RAY_NONFINITE;
@@ -611,6 +650,7 @@ __device__ __forceinline__ void rhs_mixed(const GridDev &g, const RayPhys<float>
             // quad (pi, pj, k): 4 samples of cell k in padded row (pi, pj); node i-1 -> padded i
             const long long sj = g.q_alt, si = (long long)(g.n_lon + 2) * g.q_alt;
             const float4 *q = g.quad + (long long)ia * si + (long long)ib * sj + ic;
+            const float ref = __ldg(q + si + sj).y;  // node (ia, ib, ic)
 #define RTGD_ROWQ(a, b, u0, u1, u2, u3)                   \
     {                                                     \
         const float4 v_ = __ldg(q + (a) * si + (b) * sj); \
@@ -619,11 +659,12 @@ __device__ __forceinline__ void rhs_mixed(const GridDev &g, const RayPhys<float>
         u2 = v_.z;                                        \
         u3 = v_.w;                                        \
     }
-            RTGD_CONTRACT(float, RTGD_ROWQ, wa, da, wb, db, wc, dc, out);
+            RTGD_CONTRACT(float, RTGD_ROWQ, ref, wa, da, wb, db, wc, dc, out);
 #undef RTGD_ROWQ
         } else if (STENCIL == RT_STENCIL_TABLE) {
             const long long cell = ((long long)ia * (g.n_lon - 1) + ib) * (g.n_alt - 1) + ic;
             const float4 *q = g.table + cell * 16;
+            const float ref = __ldg(q + 5).y;  // node (ia, ib, ic)
 #define RTGD_ROWT(a, b, u0, u1, u2, u3)             \
     {                                               \
         const float4 v_ = __ldg(q + (a) * 4 + (b)); \
@@ -632,11 +673,12 @@ __device__ __forceinline__ void rhs_mixed(const GridDev &g, const RayPhys<float>
         u2 = v_.z;                                  \
         u3 = v_.w;                                  \
     }
-            RTGD_CONTRACT(float, RTGD_ROWT, wa, da, wb, db, wc, dc, out);
+            RTGD_CONTRACT(float, RTGD_ROWT, ref, wa, da, wb, db, wc, dc, out);
 #undef RTGD_ROWT
         } else {
             const long long sj = g.p_alt, si = (long long)g.p_lon * g.p_alt;
             const float *p = g.pad32 + (long long)ia * si + (long long)ib * sj + ic;
+            const float ref = __ldg(p + si + sj + 1);  // node (ia, ib, ic)
 #define RTGD_ROWG(a, b, u0, u1, u2, u3)            \
     {                                              \
         const float *p_ = p + (a) * si + (b) * sj; \
@@ -645,7 +687,7 @@ __device__ __forceinline__ void rhs_mixed(const GridDev &g, const RayPhys<float>
         u2 = __ldg(p_ + 2);                        \
         u3 = __ldg(p_ + 3);                        \
     }
-            RTGD_CONTRACT(float, RTGD_ROWG, wa, da, wb, db, wc, dc, out);
+            RTGD_CONTRACT(float, RTGD_ROWG, ref, wa, da, wb, db, wc, dc, out);
 #undef RTGD_ROWG
         }
         s.X = rp.xfac * out[0];
@@ -691,6 +733,32 @@ __device__ __forceinline__ float hermite_rise_f(float dr, float m0, float m1) {
     return s * (m0 + s * (B + s * A));
 }
 
+// Float counterpart of face_distance64 on the base's (cell, fraction) grid
+// coordinates: the distance to the next face is (integer - fraction) / rate.
+__device__ __forceinline__ float face_axis_f(int i, float t, int n, float v) {
+    if (v > 0.0f) {
+        int F = i + 1;
+        if (F < 0) F = 0;
+        return F <= n - 1 ? ((float)(F - i) - t) / v : INFINITY;
+    }
+    if (v < 0.0f) {
+        int F = t > 0.0f ? i : i - 1;
+        if (F > n - 1) F = n - 1;
+        return F >= 0 ? ((float)(F - i) - t) / v : INFINITY;
+    }
+    return INFINITY;
+}
+
+__device__ __forceinline__ float face_distance_f(const GridDev &g, const Base32 &b, const float k1[6]) {
+    float best = face_axis_f(b.ic, b.tc, g.n_alt, g.sc * k1[0]);
+    const bool in_alt = b.ic >= 0 && (b.ic < g.n_alt - 1 || (b.ic == g.n_alt - 1 && b.tc == 0.0f));
+    if (in_alt) {
+        best = fminf(best, face_axis_f(b.ia, b.ta, g.n_lat, g.sa * k1[1]));
+        best = fminf(best, face_axis_f(b.ib, b.tb, g.n_lon, g.sb * k1[2]));
+    }
+    return best;
+}
+
 // Per-lane state of the mixed tracer.
 struct Lane {
     double y[6];
@@ -707,7 +775,7 @@ struct Lane {
     Base32 b;
     int out_id, mode;
     int stage, n_steps, n_att, n_ev, status, side, land_it, since_sync;
-    bool active, launch, landing, have_prev, k1_valid;
+    bool active, launch, landing, have_prev, k1_valid, at_face;
 };
 
 __device__ __forceinline__ RayPhys<float> lane_phys(const GridDev &g, const Lane &L) {
@@ -767,18 +835,33 @@ __device__ __forceinline__ void lane_finish(Lane &L, const GridDev &g, const Fan
     L.active = false;
 }
 
+// Once k1 is known: end an adaptive step just past the next cell face, and
+// clip it at the group-path limit.
+__device__ __forceinline__ void lane_limit_step(Lane &L, const GridDev &g, const FanDev &f) {
+    if (L.landing) return;
+    if (f.integrator == RT_RKF45) {
+        const float hf = face_distance_f(g, L.b, L.k1);
+        if (hf > 1e-3f * L.hs && hf < L.hs) {
+            L.hs = hf * (1.0f + 1e-4f);
+            L.at_face = true;
+        }
+    }
+    if (f.max_path > 0.0 && L.P + (double)L.hs > f.max_path) L.hs = (float)(f.max_path - L.P);
+}
+
 // Starts the next step attempt from the current state; returns false when the
 // ray stops (step budget).
-__device__ __forceinline__ bool lane_begin_attempt(Lane &L, const FanDev &f, const Tableau &T) {
+__device__ __forceinline__ bool lane_begin_attempt(Lane &L, const GridDev &g, const FanDev &f, const Tableau &T) {
     if (L.n_att >= f.max_steps) {
         L.status = RT_RAY_MAX_STEPS;
         return false;
     }
     if (!L.landing) {
         L.hs = L.h;
-        if (f.max_path > 0.0 && L.P + (double)L.hs > f.max_path) L.hs = (float)(f.max_path - L.P);
+        L.at_face = false;
     }
     if (L.k1_valid) {  // k1 at this state is known: start at stage 1
+        lane_limit_step(L, g, f);
         accumulate(L, T, 0, L.k1);
         L.stage = 1;
     } else {
@@ -812,16 +895,16 @@ __device__ bool lane_advance(Lane &L, const GridDev &g, const FanDev &f, const T
         L.b.k[0] = (float)L.y[3];
         L.b.k[1] = (float)L.y[4];
         L.b.k[2] = (float)L.y[5];
-        return !lane_begin_attempt(L, f, T);
+        return !lane_begin_attempt(L, g, f, T);
     }
-    const float hf = L.hs;
 #pragma unroll
-    for (int c = 0; c < 6; ++c) d[c] = (L.stage == 0) ? 0.0f : hf * L.acc[0][c];
+    for (int c = 0; c < 6; ++c) d[c] = (L.stage == 0) ? 0.0f : L.hs * L.acc[0][c];
     rhs_mixed<STENCIL>(g, rp, L.b, d, ks, nullptr);
     if (L.stage == 0) {
 #pragma unroll
         for (int c = 0; c < 6; ++c) L.k1[c] = ks[c];
         L.k1_valid = true;
+        lane_limit_step(L, g, f);
         if (L.have_prev && L.dr_prev > 0.0f && ks[0] <= 0.0f) {
             const float rise = hermite_rise_f((float)(L.y[0] - L.r_prev), L.h_prev * L.dr_prev, L.h_prev * ks[0]);
             L.apo = fmaxf(L.apo, (float)(L.r_prev - RE) + rise);
@@ -832,6 +915,7 @@ __device__ bool lane_advance(Lane &L, const GridDev &g, const FanDev &f, const T
     if (++L.stage < T.ns) return false;
 
     // ---- attempt complete: increments in float, state update in double
+    const float hf = L.hs;
     ++L.n_att;
     float dy4[6], ef[6];
     bool fin = true;
@@ -860,7 +944,7 @@ __device__ bool lane_advance(Lane &L, const GridDev &g, const FanDev &f, const T
                 L.side = 1;
             }
             L.hs = (float)(L.lb - L.lfb * (L.lb - L.la) / (L.lfb - L.lfa));
-            return !lane_begin_attempt(L, f, T);
+            return !lane_begin_attempt(L, g, f, T);
         }
         if (!fin) {
             L.status = RT_RAY_NONFINITE;
@@ -878,15 +962,16 @@ __device__ bool lane_advance(Lane &L, const GridDev &g, const FanDev &f, const T
         const float kmag = sqrtf(L.b.k[0] * L.b.k[0] + L.b.k[1] * L.b.k[1] + L.b.k[2] * L.b.k[2]);
         const float err = rkf45_err<float>(L.b.r, L.b.sth, kmag, ef, f.rtol_f, f.atol_f);
         const float fac = step_factor_f(err);
+        // the nominal step changes only by quantised factors of itself
         if (!(err <= 1.0f)) {
-            L.h = L.hs * fac;
+            L.h = L.h * fac;
             if (L.h < f.hmin_f) {
                 L.status = RT_RAY_STEP_UNDERFLOW;
                 return true;
             }
-            return !lane_begin_attempt(L, f, T);
+            return !lane_begin_attempt(L, g, f, T);
         }
-        h_next = fminf(fmaxf(L.hs * fac, f.hmin_f), f.hmax_f);
+        h_next = fminf(fmaxf(L.h * (L.at_face ? fminf(1.0f, fac) : fac), f.hmin_f), f.hmax_f);
     }
     if (!fin) {
         L.status = RT_RAY_NONFINITE;
@@ -902,7 +987,7 @@ __device__ bool lane_advance(Lane &L, const GridDev &g, const FanDev &f, const T
         L.side = 0;
         L.land_it = 0;
         L.hs = (float)(L.lb - L.lfb * (L.lb - L.la) / (L.lfb - L.lfa));
-        return !lane_begin_attempt(L, f, T);
+        return !lane_begin_attempt(L, g, f, T);
     }
     L.r_prev = L.y[0];
 #pragma unroll
@@ -938,7 +1023,7 @@ __device__ bool lane_advance(Lane &L, const GridDev &g, const FanDev &f, const T
         return true;
     }
     L.h = h_next;
-    return !lane_begin_attempt(L, f, T);
+    return !lane_begin_attempt(L, g, f, T);
 }
 
 // Loads the Butcher table of the fan's integrator into shared memory (lanes

@@ -131,6 +131,11 @@ def test_mixed_config1_all_rays(orc, kernel):
 
 
 def test_mixed_config2_full_size(orc):
+    """C2 at full size.  Kernel and stencil variants agree (same samples, same
+    per-ray arithmetic).  Accuracy is judged at rtol 1e-9: at the C2 setting of
+    1e-8 the integrator's own error reaches ~0.1 km on long-range rays (in FP64
+    too), so two runs whose step sequences differ (the mixed path's FP32 error
+    estimate sees round-off at the 1e-8 level) cannot agree to 0.05 km there."""
     w = wl.config2()
     g = rt.Grid(w.grid, w.ne, table=True)
     fan = rt.Fan(w.fan, rt.RT_MIXED)
@@ -139,24 +144,31 @@ def test_mixed_config2_full_size(orc):
         for kern in (rt.RT_KERNEL_PLAIN, rt.RT_KERNEL_PERSISTENT):
             outs[(st, kern)] = rt.rt_trace(g, fan, cfg=rt.launch_config(kernel=kern, stencil=st))
     base = outs[(rt.RT_STENCIL_QUAD, rt.RT_KERNEL_PERSISTENT)]
-    for k, v in outs.items():  # same samples and arithmetic up to FMA contraction
+    for k, v in outs.items():
         assert np.array_equal(v["status"], base["status"]), k
         for f in ("group_path_km", "ground_range_km"):
             assert np.abs(v[f] - base[f]).max() < 1e-7, (k, f)
         assert np.abs(v["az_dev_deg"] - base["az_dev_deg"]).max() < 1e-9, k
-    ref64 = rt.rt_trace(g, rt.Fan(w.fan, rt.RT_FP64))
-    ok = ~near_boundary(ref64, w.fan)
+    assert np.all(base["status"] != rt.RT_RAY_NOT_RUN)
+
+    spec = w.fan.replace(rtol=1e-9)
+    mixed = rt.rt_trace(g, rt.Fan(spec, rt.RT_MIXED))
+    fp64 = rt.rt_trace(g, rt.Fan(spec, rt.RT_FP64))
+    conv = rt.rt_trace(g, rt.Fan(w.fan.replace(rtol=1e-11, atol_km=1e-9), rt.RT_FP64))
+    ok = ~near_boundary(fp64, spec)
     assert ok.mean() > 0.9
-    same = base["status"] == ref64["status"]
+    same = (mixed["status"] == fp64["status"]) & (conv["status"] == fp64["status"])
     assert same[ok].mean() > 0.999
     m = ok & same
-    for f, tol in (("group_path_km", MIX_KM), ("ground_range_km", MIX_KM), ("az_dev_deg", MIX_DEG)):
-        d = np.abs(base[f] - ref64[f])[m]
-        assert np.all(d <= tol), (f, d.max())
+    for ref in (fp64, conv):
+        for f, tol in (("group_path_km", MIX_KM), ("ground_range_km", MIX_KM), ("az_dev_deg", MIX_DEG)):
+            d = np.abs(mixed[f] - ref[f])[m]
+            assert np.all(d <= tol), (f, d.max())
     idx = wl.sample_indices(w.fan.n_rays, 48, seed=22)
     idx = idx[m[idx]]
-    ref = orc.trace_fan(orc.Grid(w.grid, w.ne), w.fan, indices=idx)
-    _close64(base[idx], ref, km=MIX_KM, deg=MIX_DEG)
+    ref = orc.trace_fan(orc.Grid(w.grid, w.ne), spec, indices=idx)
+    _close64(mixed[idx], ref, km=MIX_KM, deg=MIX_DEG)
+    _close64(fp64[idx], ref)
 
 
 # --------------------------------------------------------- edge cases
@@ -168,10 +180,12 @@ def test_ragged_and_tiny_fans(orc):
         spec = w.fan.replace(el_deg=np.linspace(5.0, 55.0, n_el), az_deg=[17.0], freq_mhz=[9.0])
         ref = orc.trace_fan(og, spec)
         _close64(rt.rt_trace(g, rt.Fan(spec, rt.RT_FP64)), ref)
+        spec9 = spec.replace(rtol=1e-9)
+        ref9 = orc.trace_fan(og, spec9)
+        ok = ~near_boundary(ref9, spec9)
         for kern in (rt.RT_KERNEL_PLAIN, rt.RT_KERNEL_PERSISTENT):
-            gm = rt.rt_trace(g, rt.Fan(spec, rt.RT_MIXED), cfg=rt.launch_config(kernel=kern))
-            ok = ~near_boundary(ref, spec)
-            _close64(gm[ok], ref[ok], km=MIX_KM, deg=MIX_DEG)
+            gm = rt.rt_trace(g, rt.Fan(spec9, rt.RT_MIXED), cfg=rt.launch_config(kernel=kern))
+            _close64(gm[ok], ref9[ok], km=MIX_KM, deg=MIX_DEG)
 
 
 def test_statuses_match_oracle(orc):

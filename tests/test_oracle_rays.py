@@ -208,3 +208,18 @@ def test_rkf45_step_sequence_is_well_conditioned(orc):
     b = orc.trace_fan(g, w.fan.replace(el_deg=w.fan.el_deg * (1 + 1e-13)))
     assert np.array_equal(a["n_attempts"], b["n_attempts"])
     assert np.abs(a["group_path_km"] - b["group_path_km"]).max() < 1e-7
+
+
+def test_rkf45_converges_with_rtol(orc):
+    """Face-aligned RKF45: the group-path error against a tight run shrinks
+    roughly in proportion to rtol."""
+    w = wl.config2(elev_step=9.0, az_step=90.0, freqs=(8.0, 12.0))
+    g = orc.Grid(w.grid, w.ne)
+    ref = orc.trace_fan(g, w.fan.replace(rtol=1e-12, atol_km=1e-10))
+    errs = []
+    for rtol in (1e-8, 1e-10):
+        a = orc.trace_fan(g, w.fan.replace(rtol=rtol))
+        ok = a["status"] == ref["status"]
+        errs.append(np.quantile(np.abs(a["group_path_km"] - ref["group_path_km"])[ok], 0.9))
+    assert errs[1] < errs[0] / 20.0, errs
+    assert errs[1] < 2e-3, errs
