@@ -60,6 +60,9 @@ def parse_args():
     p.add_argument("--profile", action="store_true",
                    help="warm-up launches then one launch, nothing else (for ncu captures)")
     p.add_argument("--cpu-sample", type=int, default=512)
+    p.add_argument("--rtol", type=float, default=1e-9,
+                   help="RKF45 tolerance of the timed fan (1e-9: the integrator's own error "
+                        "stays below 0.05 km; C2's nominal 1e-8 is measured as a secondary line)")
     return p.parse_args()
 
 
@@ -199,10 +202,11 @@ def run_ours(args):
 
     rtbuild.build()
     w = wl.config2()
+    spec = w.fan.replace(rtol=args.rtol)
     prec = rt.RT_MIXED if args.precision == "mixed" else rt.RT_FP64
     grid = rt.Grid(w.grid, w.ne, table=(prec == rt.RT_MIXED and
                                         (args.kernel is None or args.stencil == "table")))
-    fan = rt.Fan(w.fan, prec)
+    fan = rt.Fan(spec, prec)
     n = fan.n_rays
     stream = torch.cuda.current_stream()
     sptr = stream.cuda_stream
@@ -282,17 +286,46 @@ def run_ours(args):
 
     line = None
     if rank == 0:
-        # accuracy of this precision against the all-FP64 GPU path, and its speed
-        fan64 = rt.Fan(w.fan, rt.RT_FP64)
-        grid64 = grid
+        # accuracy: against the all-FP64 GPU path at the same tolerance and against
+        # a converged FP64 run (rtol 1e-11), over rays not next to a skip/Pedersen
+        # boundary; the FP64 path's own throughput at this tolerance
         t0 = time.perf_counter()
-        ref64 = rt.rt_trace(grid64, fan64, stream=sptr)
+        ref64 = rt.rt_trace(grid, rt.Fan(spec, rt.RT_FP64), stream=sptr)
         fp64_s = time.perf_counter() - t0
-        ok = ~near_boundary(ref64, w.fan) & (ref64["status"] == res["status"])
-        acc = {f: float(np.abs(res[f] - ref64[f])[ok].max()) for f in
-               ("group_path_km", "ground_range_km", "az_dev_deg")}
-        acc["rays_compared"] = int(ok.sum())
-        acc["status_mismatch"] = int((ref64["status"] != res["status"]).sum())
+        conv = rt.rt_trace(grid, rt.Fan(w.fan.replace(rtol=1e-11, atol_km=1e-9), rt.RT_FP64), stream=sptr)
+        ok = ~near_boundary(conv, spec)
+
+        def errs(r, ref):
+            m = ok & (ref["status"] == r["status"])
+            e = {f: float(np.abs(r[f] - ref[f])[m].max()) for f in
+                 ("group_path_km", "ground_range_km", "az_dev_deg")}
+            e["rays_compared"] = int(m.sum())
+            e["status_mismatch"] = int((ref["status"] != r["status"]).sum())
+            return e
+
+        acc = {"vs_fp64_same_rtol": errs(res, ref64), "vs_converged_fp64": errs(res, conv),
+               "fp64_same_rtol_vs_converged": errs(ref64, conv), "converged": "FP64 GPU path, rtol 1e-11"}
+        # C2's nominal tolerance (1e-8): throughput and error of the same path
+        fan8 = rt.Fan(w.fan, prec)
+        out8 = torch.empty(n * 64, dtype=torch.uint8, device="cuda")
+        cfg8 = cfg
+        if args.kernel is None and prec == rt.RT_MIXED and not args.no_tune:
+            cfg8, _ = rt.rt_tune(grid, fan8, max_rays=8192, stream=sptr)
+        for _ in range(2):
+            rt.rt_trace_device(grid, fan8, out8.data_ptr(), n, cfg=cfg8, stream=sptr)
+        t8 = []
+        for _ in range(5):
+            flush.zero_()
+            a8, b8 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a8.record(stream)
+            rt.rt_trace_device(grid, fan8, out8.data_ptr(), n, cfg=cfg8, stream=sptr)
+            b8.record(stream)
+            torch.cuda.synchronize()
+            t8.append(a8.elapsed_time(b8))
+        res8 = rt.results_view(out8.cpu().numpy(), n)
+        nominal = {"rtol": 1e-8, "rays_per_s": n / (np.mean(t8) / 1e3), "ms_per_step": float(np.mean(t8)),
+                   "ray_steps_per_s": float(res8["n_steps"].sum()) / (np.mean(t8) / 1e3),
+                   "error_vs_converged_fp64": errs(res8, conv)}
         sec = mean_ms / 1e3
         flop = evals * FLOP_PER_EVAL[args.precision]
         if prec == rt.RT_MIXED:
@@ -308,7 +341,9 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64" if prec == rt.RT_MIXED else "f64", "data": "synthetic",
-            "config": {"workload": w.name, "rays": n, "precision": args.precision,
+            "config": {"workload": w.name, "rays": n, "precision": args.precision, "rtol": args.rtol,
+                       "rtol_note": "C2 inputs and fan; RKF45 tightened from 1e-8 to 1e-9 so the "
+                                    "integrator's own error meets the 0.05 km bar (see c2_nominal_rtol)",
                        "launch": None if cfg is None else {"kernel": cfg.kernel, "stencil": cfg.stencil,
                                                            "block_threads": cfg.block_threads,
                                                            "order": cfg.order},
@@ -318,7 +353,8 @@ def run_ours(args):
             "attempts_per_s": attempts * world / sec,
             "stage_evals_per_s": evals * world / sec,
             "fan_latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
-            "accuracy_vs_fp64_gpu": acc,
+            "accuracy": acc,
+            "c2_nominal_rtol": nominal,
             "fp64_gpu_path": {"rays_per_s": n / fp64_s, "seconds": fp64_s},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None, "peak_basis": bound_note,
