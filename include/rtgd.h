@@ -150,7 +150,7 @@ typedef struct rt_fan_desc {
 enum {
     RT_RAY_NOT_RUN = 0,
     RT_RAY_LANDED = 1,         /* returned to r = R_E (landing point solved to 1e-9 km in FP64) */
-    RT_RAY_ESCAPED = 2,        /* rose above the top of the grid */
+    RT_RAY_ESCAPED = 2,        /* left through the top of the grid (exit point solved like landing) */
     RT_RAY_LEFT_GRID = 3,      /* left the grid sideways inside its altitude span */
     RT_RAY_MAX_STEPS = 4,      /* max_steps attempts used */
     RT_RAY_STEP_UNDERFLOW = 5, /* RKF45 needed a step below h_min_km */
@@ -159,7 +159,8 @@ enum {
 };
 
 /* Per-ray result (64 bytes).  Quantities refer to the final state: the
- * landing point for LANDED rays, the last accepted state otherwise.
+ * landing point for LANDED rays, the exit point on the grid top for ESCAPED
+ * rays (both solved on the last step), the last accepted state otherwise.
  * ground_range_km = R_E times the central angle from the transmitter;
  * az_dev_deg = bearing of the final point from the transmitter minus the
  * launch azimuth, in [-180, 180); apogee_km = the reflection height (maximum

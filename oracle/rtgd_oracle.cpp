@@ -28,7 +28,8 @@
  * centred tilted dipole instead of IGRF; ghost nodes by quadratic
  * extrapolation; Ne = 0 outside the grid box; RKF45 (Fehlberg 4(5)) as the
  * adaptive option with the error norm and controller documented at rkf45_err;
- * landing by regula falsi (Illinois) on the size of the last step; reflection
+ * landing (and exit through the grid top) by regula falsi (Illinois) on the
+ * size of the last step; reflection
  * height from a cubic Hermite fit on the step where dr/dP' changes sign.
  */
 #include "rtgd_oracle.h"
@@ -598,8 +599,14 @@ void trace(const or_grid &g, const or_ray &ray, or_result *res, double *traj, in
             status = OR_NONFINITE;
             break;
         }
-        if (yn[0] < RE) { /* ground return: solve r(step(h*)) = R_E for h* in (0, hs] */
-            double a = 0.0, fa = y[0] - RE, b = hs, fb = yn[0] - RE, cc = b;
+        const bool lands = yn[0] < RE;
+        const bool exits = !lands && yn[0] - RE > top;
+        if (lands || exits) {
+            /* ground return or exit through the grid top inside this step: solve
+             * r(step(h*)) = R_E (or R_E + top) for h* in (0, hs]; sg makes the
+             * bracket function positive at the start of the step */
+            const double rt = lands ? RE : RE + top, sg = lands ? 1.0 : -1.0;
+            double a = 0.0, fa = sg * (y[0] - rt), b = hs, fb = sg * (yn[0] - rt), cc = b;
             double yc[6], ec[6];
             for (int i = 0; i < 6; ++i) yc[i] = yn[i];
             int side = 0;
@@ -608,7 +615,7 @@ void trace(const or_grid &g, const or_ray &ray, or_result *res, double *traj, in
                 if (adaptive) rkf45_step(c, y, k1, cc, yc, ec);
                 else rk4_step(c, y, k1, cc, yc);
                 ++n_att;
-                const double fc = yc[0] - RE;
+                const double fc = sg * (yc[0] - rt);
                 if (std::fabs(fc) < 1e-9) break;
                 if (fc < 0.0) {
                     b = cc;
@@ -625,10 +632,11 @@ void trace(const or_grid &g, const or_ray &ray, or_result *res, double *traj, in
             P += cc;
             ++n_steps;
             for (int i = 0; i < 6; ++i) y[i] = yc[i];
+            if (exits) apogee = std::max(apogee, y[0] - RE);
             double kk[6], H;
             rhs(c, y, kk, &H);
             push_traj(traj, cap, tlen, P, y, H);
-            status = OR_LANDED;
+            status = lands ? OR_LANDED : OR_ESCAPED;
             break;
         }
         P += hs;
@@ -644,12 +652,8 @@ void trace(const or_grid &g, const or_ray &ray, or_result *res, double *traj, in
             rhs(c, y, kk, &H);
             push_traj(traj, cap, tlen, P, y, H);
         }
-        /* leaving the ionospheric region (Sec. II-C) */
+        /* leaving the ionospheric region sideways (Sec. II-C) */
         const double alt = y[0] - RE;
-        if (alt > top) {
-            status = OR_ESCAPED;
-            break;
-        }
         if (alt >= g.alt0_km) {
             Dual xa, xb, xc;
             grid_coords(g, cst(y[0]), cst(y[1]), cst(y[2]), &xa, &xb, &xc);

@@ -453,9 +453,14 @@ __device__ void trace_ray_fp64(const GridDev &g, const FanDev &f, long long id, 
             status = RT_RAY_NONFINITE;
             break;
         }
-        if (yn[0] < RE) {
-            // ground return: r(step(h*)) = R_E for h* in (0, hs], Illinois regula falsi
-            double a = 0.0, fa = y[0] - RE, b = hs, fb = yn[0] - RE, c = b;
+        const bool lands = yn[0] < RE;
+        const bool exits = !lands && yn[0] - RE > g.top;
+        if (lands || exits) {
+            // ground return or exit through the grid top inside this step:
+            // r(step(h*)) = R_E (or R_E + top) for h* in (0, hs], Illinois regula
+            // falsi; sg makes the bracket function positive at the step start
+            const double rt = lands ? RE : RE + g.top, sg = lands ? 1.0 : -1.0;
+            double a = 0.0, fa = sg * (y[0] - rt), b = hs, fb = sg * (yn[0] - rt), c = b;
             double yc[6], ec[6];
 #pragma unroll
             for (int i = 0; i < 6; ++i) yc[i] = yn[i];
@@ -466,7 +471,7 @@ __device__ void trace_ray_fp64(const GridDev &g, const FanDev &f, long long id, 
                 else rk4_step64(g, rp, y, k1, c, yc);
                 ++n_att;
                 n_ev += ev_per_step;
-                const double fc = yc[0] - RE;
+                const double fc = sg * (yc[0] - rt);
                 if (fabs(fc) < 1e-9) break;
                 if (fc < 0.0) {
                     b = c;
@@ -484,7 +489,8 @@ __device__ void trace_ray_fp64(const GridDev &g, const FanDev &f, long long id, 
             ++n_steps;
 #pragma unroll
             for (int i = 0; i < 6; ++i) y[i] = yc[i];
-            status = RT_RAY_LANDED;
+            if (exits) apo = fmax(apo, y[0] - RE);
+            status = lands ? RT_RAY_LANDED : RT_RAY_ESCAPED;
             break;
         }
         P += hs;
@@ -498,10 +504,6 @@ __device__ void trace_ray_fp64(const GridDev &g, const FanDev &f, long long id, 
         for (int i = 0; i < 6; ++i) y[i] = yn[i];
         k1_valid = false;
         const double alt = y[0] - RE;
-        if (alt > g.top) {
-            status = RT_RAY_ESCAPED;
-            break;
-        }
         if (alt >= g.alt0 && !inside_latlon(g, y[1], y[2])) {
             status = RT_RAY_LEFT_GRID;
             break;
@@ -764,7 +766,8 @@ struct Lane {
     double y[6];
     double P;
     double r_prev;            // radius at the start of the last accepted step
-    double la, lfa, lb, lfb;  // landing bracket (step size, r - R_E)
+    double la, lfa, lb, lfb;  // crossing bracket (step size, signed r - target)
+    double r_target;          // R_E (ground) or R_E + top (exit through the grid top)
     float h, hs;              // next step / step of the current attempt (km)
     float h_prev, dr_prev;    // last accepted step and its dr/dP' at the start
     float apo;                // reflection height so far (km)
@@ -775,7 +778,7 @@ struct Lane {
     Base32 b;
     int out_id, mode;
     int stage, n_steps, n_att, n_ev, status, side, land_it, since_sync;
-    bool active, launch, landing, have_prev, k1_valid, at_face;
+    bool active, launch, landing, exiting, have_prev, k1_valid, at_face;
 };
 
 __device__ __forceinline__ RayPhys<float> lane_phys(const GridDev &g, const Lane &L) {
@@ -821,7 +824,7 @@ __device__ void lane_begin_ray(Lane &L, const GridDev &g, const FanDev &f, long 
     L.n_steps = L.n_att = L.n_ev = 0;
     L.since_sync = 0;
     L.status = RT_RAY_NOT_RUN;
-    L.have_prev = L.k1_valid = L.landing = false;
+    L.have_prev = L.k1_valid = L.landing = L.exiting = false;
     L.launch = true;
     L.stage = 0;
     base_from_state(g, L.y, L.b);
@@ -926,8 +929,9 @@ __device__ bool lane_advance(Lane &L, const GridDev &g, const FanDev &f, const T
         fin = fin && isfinite(dy4[c]);
     }
     if (L.landing) {
-        // Illinois regula falsi on the step size: f(h*) = r(step(h*)) - R_E
-        const double fc = (L.y[0] - RE) + (double)dy4[0];
+        // Illinois regula falsi on the step size: f(h*) = +-(r(step(h*)) - target)
+        const double sg = L.exiting ? -1.0 : 1.0;
+        const double fc = sg * ((L.y[0] - L.r_target) + (double)dy4[0]);
         ++L.land_it;
         const double c = (double)L.hs;
         const bool done = fabs(fc) < f.land_tol || L.land_it >= 60 || fabs(L.lb - L.la) < 1e-9 || !fin;
@@ -954,7 +958,8 @@ __device__ bool lane_advance(Lane &L, const GridDev &g, const FanDev &f, const T
         ++L.n_steps;
 #pragma unroll
         for (int i = 0; i < 6; ++i) L.y[i] += (double)dy4[i];
-        L.status = RT_RAY_LANDED;
+        if (L.exiting) L.apo = fmaxf(L.apo, (float)(L.y[0] - RE));
+        L.status = L.exiting ? RT_RAY_ESCAPED : RT_RAY_LANDED;
         return true;
     }
     float h_next = L.h;
@@ -978,12 +983,17 @@ __device__ bool lane_advance(Lane &L, const GridDev &g, const FanDev &f, const T
         return true;
     }
     const double r_new = L.y[0] + (double)dy4[0];
-    if (r_new < RE) {
+    const bool lands = r_new < RE;
+    if (lands || r_new - RE > g.top) {
+        // ground return or exit through the grid top inside this step
         L.landing = true;
+        L.exiting = !lands;
+        L.r_target = lands ? RE : RE + g.top;
+        const double sg = lands ? 1.0 : -1.0;
         L.la = 0.0;
-        L.lfa = L.y[0] - RE;
+        L.lfa = sg * (L.y[0] - L.r_target);
         L.lb = (double)L.hs;
-        L.lfb = r_new - RE;
+        L.lfb = sg * (r_new - L.r_target);
         L.side = 0;
         L.land_it = 0;
         L.hs = (float)(L.lb - L.lfb * (L.lb - L.la) / (L.lfb - L.lfa));
@@ -1000,10 +1010,6 @@ __device__ bool lane_advance(Lane &L, const GridDev &g, const FanDev &f, const T
     L.dr_prev = L.k1[0];
     L.h_prev = L.hs;
     L.k1_valid = false;
-    if (alt > g.top) {
-        L.status = RT_RAY_ESCAPED;
-        return true;
-    }
     if (++L.since_sync >= kResyncSteps) {
         L.since_sync = 0;
         base_from_state(g, L.y, L.b);

@@ -56,6 +56,7 @@ def test_free_space_ray_is_straight(orc, el, az):
     assert np.max(np.abs(k - k[0])) < 1e-12                                 # constant k
     np.testing.assert_allclose(np.linalg.norm(d, axis=1), traj[:, 0], rtol=1e-12, atol=1e-8)
     r = traj[-1, 1]
+    assert r == pytest.approx(RE + 660.0, abs=1e-9)  # exit point solved on the grid top
     e = np.radians(el)
     L = np.sqrt(r * r - RE * RE * np.cos(e) ** 2) - RE * np.sin(e)
     assert res["group_path_km"] == pytest.approx(L, abs=1e-8)
