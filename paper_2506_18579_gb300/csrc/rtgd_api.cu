@@ -300,6 +300,7 @@ rt_err queue_trace(const rt_grid *grid, const rt_fan_desc *fan, rt_ray_result *o
     f.h0_f = (float)f.h0;
     f.hmin_f = (float)f.hmin;
     f.hmax_f = (float)f.hmax;
+    f.has_max_path = f.max_path > 0.0 ? 1 : 0;
     if (e == cudaSuccess) e = launch_trace(grid->g, f, out_dev, counter, lp, st);
     const cudaError_t e2 = cudaFreeAsync(ws, st);
     if (e != cudaSuccess) return cuda_fail(e, "trace launch");
@@ -392,6 +393,8 @@ rt_err rt_grid_create(const rt_grid_desc *desc, const void *ne_host, rt_grid **o
     d.mf[0] = (float)d.m[0];
     d.mf[1] = (float)d.m[1];
     d.mf[2] = (float)d.m[2];
+    d.top_f = (float)d.top;
+    d.iso = d.b0 == 0.0 ? 1 : 0;
     d.pad64 = g->pad64;
     d.pad32 = g->pad32;
     d.quad = g->quad;

@@ -37,6 +37,8 @@ struct GridDev {
     double m[3];                     // unit vector to the geomagnetic north pole
     float sa, sb, sc;                // d(grid coord)/d(theta, phi, r): -rad2deg/dlat, rad2deg/dlon, 1/dalt
     float R_Ef, mf[3];               // float copies of R_E and m
+    float top_f;                     // top as float
+    int iso;                         // no field (b0 == 0)
     const double *pad64;             // (n_lat+2)(n_lon+2)(n_alt+2) doubles
     const float *pad32;              // same, rounded to float
     const float4 *quad;              // (n_lat+2)(n_lon+2)(n_alt-1): samples k-1..k+2 of cell k
@@ -156,7 +158,7 @@ __device__ __forceinline__ RayPhys<R> make_phys(const GridDev &g, double f_hz, i
     p.m[0] = R(g.m[0]);
     p.m[1] = R(g.m[1]);
     p.m[2] = R(g.m[2]);
-    p.iso = g.b0 == 0.0;
+    p.iso = g.iso != 0;
     p.mode = mode;
     return p;
 }

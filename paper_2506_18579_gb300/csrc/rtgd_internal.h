@@ -25,6 +25,7 @@ struct FanDev {
     double h0, rtol, atol, hmin, hmax, max_path;
     double land_tol;            // |r - R_E| accepted by the landing solve (km)
     float rtol_f, atol_f, h0_f, hmin_f, hmax_f;
+    int has_max_path;           // max_path > 0
 };
 
 struct LaunchPlan {

@@ -534,9 +534,11 @@ __global__ void __launch_bounds__(128) trace_fp64_kernel(GridDev g, FanDev f, rt
 // linear in r, theta, phi), and sin/cos of theta + delta by angle addition,
 // so everything after (weights, contraction, dipole, Appleton-Hartree, Eq. 1)
 // runs in float without losing the base's resolution.  An accepted step adds
-// the float increment to the double state (the only FP64 arithmetic of a
-// step besides the group-path sum and the ground test); the base follows by
-// the same increment in float and is recomputed from the double state every
+// the float increment to the double position (r, theta, phi) and the double
+// group path -- the only FP64 arithmetic of a step; the wave vector, a
+// quantity of order 1, accumulates as a compensated float pair (hi + lo).
+// The base (cells, altitude, radius, sines and cosines) follows by the same
+// increment in float and is recomputed from the double state every
 // kResyncSteps accepted steps.  GB300 issues FP64 at 1/64 of the FP32 rate,
 // so the step bookkeeping must stay out of double precision.
 constexpr int kResyncSteps = 16;
@@ -544,7 +546,7 @@ constexpr int kResyncSteps = 16;
 struct Base32 {
     int ia, ib, ic;            // cell of the base (may lie outside the grid)
     float ta, tb, tc;          // in-cell coordinates
-    float r;                   // radius (km)
+    float r, alt;              // radius and altitude (km)
     float sth, cth, sph, cph;  // sin/cos of colatitude and longitude
     float k[3];
 };
@@ -572,6 +574,7 @@ __device__ void base_from_state(const GridDev &g, const double y[6], Base32 &b) 
     b.tb = (float)(xb - fb);
     b.tc = (float)(xc - fc);
     b.r = (float)y[0];
+    b.alt = (float)(y[0] - g.R_E);
     sincosf((float)y[1], &b.sth, &b.cth);
     sincosf((float)y[2], &b.sph, &b.cph);
     b.k[0] = (float)y[3];
@@ -586,17 +589,43 @@ __device__ __forceinline__ void shift_axis(int &i, float &t, float dt) {
     t = u - fl;
 }
 
-// Moves the base by the accepted increment d; y is the new double state.
-__device__ __forceinline__ void advance_base(const GridDev &g, Base32 &b, const float d[6], const double y[6]) {
+// sin/cos of (x0 + d) from sin/cos of x0, for |d| well below 0.1 rad (series
+// error < d^7/5040).
+__device__ __forceinline__ void angle_add(float s0, float c0, float d, float &s, float &c) {
+    const float d2 = d * d;
+    const float sd = d * (1.0f - d2 * (1.0f / 6.0f) * (1.0f - d2 * 0.05f));
+    const float cd = 1.0f - 0.5f * d2 * (1.0f - d2 * (1.0f / 12.0f));
+    s = s0 * cd + c0 * sd;
+    c = c0 * cd - s0 * sd;
+}
+
+// Moves the base by the accepted increment d in float; k_hi is the new wave
+// vector (high parts).
+__device__ __forceinline__ void advance_base(const GridDev &g, Base32 &b, const float d[6], const float k_hi[3]) {
     shift_axis(b.ia, b.ta, g.sa * d[1]);
     shift_axis(b.ib, b.tb, g.sb * d[2]);
     shift_axis(b.ic, b.tc, g.sc * d[0]);
-    b.r = (float)y[0];
-    sincosf((float)y[1], &b.sth, &b.cth);
-    sincosf((float)y[2], &b.sph, &b.cph);
-    b.k[0] = (float)y[3];
-    b.k[1] = (float)y[4];
-    b.k[2] = (float)y[5];
+    b.r += d[0];
+    b.alt += d[0];
+    float s, c;
+    angle_add(b.sth, b.cth, d[1], s, c);
+    b.sth = s;
+    b.cth = c;
+    angle_add(b.sph, b.cph, d[2], s, c);
+    b.sph = s;
+    b.cph = c;
+    b.k[0] = k_hi[0];
+    b.k[1] = k_hi[1];
+    b.k[2] = k_hi[2];
+}
+
+// hi + lo += d with the rounding error of hi + d kept in lo (Knuth's TwoSum).
+__device__ __forceinline__ void two_sum_add(float &hi, float &lo, float d) {
+    const float s = hi + d;
+    const float bp = s - hi;
+    const float err = (hi - (s - bp)) + (d - bp);
+    hi = s;
+    lo += err;
 }
 
 // Stage cell along one axis from base cell i0 and offset coordinate t = t0 +
@@ -615,16 +644,6 @@ __device__ __forceinline__ bool stage_cell(int i0, float t, int n, int &i, float
     i = ii;
     tt = tr;
     return true;
-}
-
-// sin/cos of (x0 + d) from sin/cos of x0, for |d| well below 0.1 rad (series
-// error < d^7/5040).
-__device__ __forceinline__ void angle_add(float s0, float c0, float d, float &s, float &c) {
-    const float d2 = d * d;
-    const float sd = d * (1.0f - d2 * (1.0f / 6.0f) * (1.0f - d2 * 0.05f));
-    const float cd = 1.0f - 0.5f * d2 * (1.0f - d2 * (1.0f / 12.0f));
-    s = s0 * cd + c0 * sd;
-    c = c0 * cd - s0 * sd;
 }
 
 // dy/dP' (float) at base + delta.  STENCIL selects where the 64 samples come from.
@@ -763,9 +782,10 @@ __device__ __forceinline__ float face_distance_f(const GridDev &g, const Base32 
 
 // Per-lane state of the mixed tracer.
 struct Lane {
-    double y[6];
-    double P;
-    double r_prev;            // radius at the start of the last accepted step
+    double y[3];              // r (km), theta, phi (rad): the FP64 position
+    double P;                 // group path (km)
+    float k_hi[3], k_lo[3];   // wave vector as a compensated float pair
+    float r_prev;             // radius at the start of the last accepted step
     double la, lfa, lb, lfb;  // crossing bracket (step size, signed r - target)
     double r_target;          // R_E (ground) or R_E + top (exit through the grid top)
     float h, hs;              // next step / step of the current attempt (km)
@@ -817,7 +837,14 @@ __device__ void lane_begin_ray(Lane &L, const GridDev &g, const FanDev &f, long 
     L.xfac = (float)(kPlasmaHz2PerM3 / (p.f_hz * p.f_hz));
     L.ab0 = (float)(kGyroHzPerTesla / p.f_hz * g.b0);
     L.mode = p.mode;
-    launch_dir(f, p, L.y);
+    double y[6];
+    launch_dir(f, p, y);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        L.y[i] = y[i];
+        L.k_hi[i] = (float)y[3 + i];
+        L.k_lo[i] = 0.0f;
+    }
     L.P = 0.0;
     L.h = f.h0_f;
     L.apo = (float)(f.tx_r - g.R_E);
@@ -827,13 +854,24 @@ __device__ void lane_begin_ray(Lane &L, const GridDev &g, const FanDev &f, long 
     L.have_prev = L.k1_valid = L.landing = L.exiting = false;
     L.launch = true;
     L.stage = 0;
-    base_from_state(g, L.y, L.b);
+    base_from_state(g, y, L.b);
+}
+
+// Double copy of the full state (position, wave vector hi + lo).
+__device__ __forceinline__ void lane_state(const Lane &L, double y[6]) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        y[i] = L.y[i];
+        y[3 + i] = (double)L.k_hi[i] + (double)L.k_lo[i];
+    }
 }
 
 __device__ __forceinline__ void lane_finish(Lane &L, const GridDev &g, const FanDev &f, rt_ray_result *out) {
     rt_ray_result r;
     const double az = f.az[L.out_id % f.n_az] * kDeg2Rad;
-    finish_result(f, az, L.y, L.P, (double)L.apo, L.status, L.n_steps, L.n_att, L.n_ev, g.R_E, &r);
+    double y[6];
+    lane_state(L, y);
+    finish_result(f, az, y, L.P, (double)L.apo, L.status, L.n_steps, L.n_att, L.n_ev, g.R_E, &r);
     out[L.out_id] = r;
     L.active = false;
 }
@@ -849,7 +887,7 @@ __device__ __forceinline__ void lane_limit_step(Lane &L, const GridDev &g, const
             L.at_face = true;
         }
     }
-    if (f.max_path > 0.0 && L.P + (double)L.hs > f.max_path) L.hs = (float)(f.max_path - L.P);
+    if (f.has_max_path && L.P + (double)L.hs > f.max_path) L.hs = (float)(f.max_path - L.P);
 }
 
 // Starts the next step attempt from the current state; returns false when the
@@ -891,13 +929,17 @@ __device__ bool lane_advance(Lane &L, const GridDev &g, const FanDev &f, const T
             L.status = RT_RAY_NONFINITE;
             return true;
         }
+        // |k| = mu: rescale the launch direction (double), split into hi + lo
         const double mu = sqrt((double)mu2);
-        L.y[3] *= mu;
-        L.y[4] *= mu;
-        L.y[5] *= mu;
-        L.b.k[0] = (float)L.y[3];
-        L.b.k[1] = (float)L.y[4];
-        L.b.k[2] = (float)L.y[5];
+        double y[6];
+        lane_state(L, y);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const double k = y[3 + i] * mu;
+            L.k_hi[i] = (float)k;
+            L.k_lo[i] = (float)(k - (double)L.k_hi[i]);
+            L.b.k[i] = L.k_hi[i];
+        }
         return !lane_begin_attempt(L, g, f, T);
     }
 #pragma unroll
@@ -909,8 +951,8 @@ __device__ bool lane_advance(Lane &L, const GridDev &g, const FanDev &f, const T
         L.k1_valid = true;
         lane_limit_step(L, g, f);
         if (L.have_prev && L.dr_prev > 0.0f && ks[0] <= 0.0f) {
-            const float rise = hermite_rise_f((float)(L.y[0] - L.r_prev), L.h_prev * L.dr_prev, L.h_prev * ks[0]);
-            L.apo = fmaxf(L.apo, (float)(L.r_prev - RE) + rise);
+            const float rise = hermite_rise_f(L.b.r - L.r_prev, L.h_prev * L.dr_prev, L.h_prev * ks[0]);
+            L.apo = fmaxf(L.apo, L.b.alt - (L.b.r - L.r_prev) + rise);
         }
         L.have_prev = false;
     }
@@ -957,7 +999,10 @@ __device__ bool lane_advance(Lane &L, const GridDev &g, const FanDev &f, const T
         L.P += c;
         ++L.n_steps;
 #pragma unroll
-        for (int i = 0; i < 6; ++i) L.y[i] += (double)dy4[i];
+        for (int i = 0; i < 3; ++i) {
+            L.y[i] += (double)dy4[i];
+            two_sum_add(L.k_hi[i], L.k_lo[i], dy4[3 + i]);
+        }
         if (L.exiting) L.apo = fmaxf(L.apo, (float)(L.y[0] - RE));
         L.status = L.exiting ? RT_RAY_ESCAPED : RT_RAY_LANDED;
         return true;
@@ -982,10 +1027,11 @@ __device__ bool lane_advance(Lane &L, const GridDev &g, const FanDev &f, const T
         L.status = RT_RAY_NONFINITE;
         return true;
     }
-    const double r_new = L.y[0] + (double)dy4[0];
-    const bool lands = r_new < RE;
-    if (lands || r_new - RE > g.top) {
+    const float alt_new = L.b.alt + dy4[0];
+    const bool lands = alt_new < 0.0f;
+    if (lands || alt_new > g.top_f) {
         // ground return or exit through the grid top inside this step
+        const double r_new = L.y[0] + (double)dy4[0];
         L.landing = true;
         L.exiting = !lands;
         L.r_target = lands ? RE : RE + g.top;
@@ -999,24 +1045,28 @@ __device__ bool lane_advance(Lane &L, const GridDev &g, const FanDev &f, const T
         L.hs = (float)(L.lb - L.lfb * (L.lb - L.la) / (L.lfb - L.lfa));
         return !lane_begin_attempt(L, g, f, T);
     }
-    L.r_prev = L.y[0];
+    L.r_prev = L.b.r;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) L.y[i] += (double)dy4[i];
+    for (int i = 0; i < 3; ++i) {
+        L.y[i] += (double)dy4[i];
+        two_sum_add(L.k_hi[i], L.k_lo[i], dy4[3 + i]);
+    }
     L.P += (double)L.hs;
     ++L.n_steps;
-    const double alt = r_new - RE;
-    L.apo = fmaxf(L.apo, (float)alt);
+    L.apo = fmaxf(L.apo, alt_new);
     L.have_prev = true;
     L.dr_prev = L.k1[0];
     L.h_prev = L.hs;
     L.k1_valid = false;
     if (++L.since_sync >= kResyncSteps) {
         L.since_sync = 0;
-        base_from_state(g, L.y, L.b);
+        double y[6];
+        lane_state(L, y);
+        base_from_state(g, y, L.b);
     } else {
-        advance_base(g, L.b, dy4, L.y);
+        advance_base(g, L.b, dy4, L.k_hi);
     }
-    if (alt >= g.alt0) {
+    if (L.b.alt >= (float)g.alt0) {
         const bool in_lat = L.b.ia >= 0 && (L.b.ia < g.n_lat - 1 || (L.b.ia == g.n_lat - 1 && L.b.ta == 0.0f));
         const bool in_lon = L.b.ib >= 0 && (L.b.ib < g.n_lon - 1 || (L.b.ib == g.n_lon - 1 && L.b.tb == 0.0f));
         if (!(in_lat && in_lon)) {
@@ -1024,7 +1074,7 @@ __device__ bool lane_advance(Lane &L, const GridDev &g, const FanDev &f, const T
             return true;
         }
     }
-    if (f.max_path > 0.0 && L.P >= f.max_path - 1e-6) {
+    if (f.has_max_path && L.P >= f.max_path - 1e-6) {
         L.status = RT_RAY_MAX_PATH;
         return true;
     }
@@ -1044,7 +1094,7 @@ __device__ __forceinline__ void load_tableau(Tableau &T, int integrator) {
 
 // One ray per thread; each thread loops stage by stage until its ray ends.
 template <int STENCIL>
-__global__ void __launch_bounds__(128) trace_mixed_plain_kernel(GridDev g, FanDev f, rt_ray_result *__restrict__ out) {
+__global__ void __launch_bounds__(128, 3) trace_mixed_plain_kernel(GridDev g, FanDev f, rt_ray_result *__restrict__ out) {
     __shared__ Tableau T;
     load_tableau(T, f.integrator);
     const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -1063,7 +1113,7 @@ __global__ void __launch_bounds__(128) trace_mixed_plain_kernel(GridDev g, FanDe
 // Persistent kernel: resident blocks; every warp keeps its 32 lanes busy by
 // claiming new rays (one atomicAdd per warp for all idle lanes) as rays end.
 template <int STENCIL>
-__global__ void __launch_bounds__(128) trace_mixed_persistent_kernel(GridDev g, FanDev f,
+__global__ void __launch_bounds__(128, 3) trace_mixed_persistent_kernel(GridDev g, FanDev f,
                                                                      rt_ray_result *__restrict__ out,
                                                                      unsigned long long *__restrict__ counter) {
     __shared__ Tableau T;

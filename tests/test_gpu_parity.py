@@ -131,8 +131,8 @@ def test_mixed_config1_all_rays(orc, kernel):
 
 
 def test_mixed_config2_full_size(orc):
-    """C2 at full size.  Kernel and stencil variants agree (same samples, same
-    per-ray arithmetic).  Accuracy is judged at rtol 1e-9: at the C2 setting of
+    """C2 at full size, every kernel and stencil variant.  Accuracy is judged
+    at rtol 1e-9, for each variant: at the C2 setting of
     1e-8 the integrator's own error reaches ~0.1 km on long-range rays (in FP64
     too), so two runs whose step sequences differ (the mixed path's FP32 error
     estimate sees round-off at the 1e-8 level) cannot agree to 0.05 km there."""
