@@ -52,8 +52,10 @@ enum { RT_F32 = 0, RT_F64 = 1 };
 
 /* rt_grid_desc.flags */
 enum {
-    RT_GRID_TABLE = 1u  /* also build the per-cell stencil table (64 FP32 values per
-                           cell, Sec. II-C "weights computed once per grid cell") */
+    RT_GRID_TABLE = 1u,       /* also build the per-cell stencil table (64 FP32 values per
+                                 cell, Sec. II-C "weights computed once per grid cell") */
+    RT_GRID_CATMULL_ROM = 2u  /* interpolate with the Catmull-Rom spline of Sec. II-B-1
+                                 (Eq. 6-9), the paper's comparison scheme, instead of GD */
 };
 
 /* Centred tilted dipole standing in for the geomagnetic model (Sec. II-C):
@@ -194,7 +196,10 @@ typedef struct rt_launch_config {
     int32_t block_threads; /* 0 = default; a multiple of 32 in [32, 1024] */
     int32_t order;         /* RT_ORDER_*: order in which the persistent kernel claims rays */
     int32_t blocks_per_sm; /* persistent kernel: resident blocks per SM (0 = occupancy limit) */
-    int32_t reserved[3];
+    int32_t lanes_per_ray; /* mixed path: 1, 2 or 4 lanes share one ray (they split the 16 sample
+                              rows of every stage; 32 / lanes rays per warp); 0 = chosen from the
+                              fan size (more lanes per ray when the fan cannot fill the GPU) */
+    int32_t reserved[2];
 } rt_launch_config;
 
 /* Trace a fan; blocking.  out_host receives rt_fan_size(fan) results in
@@ -221,6 +226,56 @@ rt_err rt_trace_device(const rt_grid *grid, const rt_fan_desc *fan, rt_ray_resul
  * grid and fan shape, and used by later RT_KERNEL_AUTO calls. */
 rt_err rt_tune(const rt_grid *grid, const rt_fan_desc *fan, size_t max_rays, void *stream,
                rt_launch_config *best, float *best_ms);
+
+/* ------------------------------------------------------------------ plans */
+/* A plan binds a grid, a fan and a launch configuration once: the fan tables
+ * and the ray counter live in device memory owned by the plan (allocated by
+ * rt_plan_create), so rt_plan_execute only resets the counter and launches
+ * the trace kernel -- two stream operations that can be captured into a CUDA
+ * graph and replayed.  The grid must outlive the plan.
+ * Errors: as rt_trace_device; rt_plan_execute also RT_EINVAL on NULL. */
+typedef struct rt_plan rt_plan;
+rt_err rt_plan_create(const rt_grid *grid, const rt_fan_desc *fan, const rt_launch_config *cfg,
+                      rt_plan **out);
+size_t rt_plan_rays(const rt_plan *plan);
+rt_err rt_plan_execute(const rt_plan *plan, rt_ray_result *out_dev, size_t out_len, void *stream);
+rt_err rt_plan_destroy(rt_plan *plan);
+
+/* --------------------------------------------------------------- ionogram */
+/* Oblique-ionogram synthesis (Sec. IV-B-4: joint frequency-elevation scan,
+ * group path against frequency at the receiver).  The fan is launched from
+ * the transmitter towards the receiver (azimuth = initial bearing of the
+ * great circle), every frequency x mode x elevation.  For each frequency and
+ * mode, every pair of neighbouring elevations whose LANDED rays bracket the
+ * transmitter-receiver ground distance D_rx gives one ionogram point, by
+ * linear interpolation in D of group path and elevation.  Points are returned
+ * sorted by (frequency, mode, elevation); branch numbers the crossings of
+ * one trace from the lowest elevation (0: the low ray, 1: the high ray, ...).
+ * Elevations must be ascending.  At most cap points are written; *n_points
+ * receives the total found.  Blocking. */
+typedef struct rt_ionogram_desc {
+    double tx_lat_deg, tx_lon_deg, tx_alt_km;
+    double rx_lat_deg, rx_lon_deg;
+    const double *freq_mhz;     /* n_freq values */
+    const double *el_deg;       /* n_el ascending values */
+    int32_t n_freq, n_el;
+    uint32_t modes;             /* RT_MODE_O | RT_MODE_X */
+    int32_t integrator, precision;
+    int32_t max_steps;
+    double h_km, rtol, atol_km, h_min_km, h_max_km;
+} rt_ionogram_desc;
+
+typedef struct rt_ionogram_point {
+    double freq_mhz;
+    double group_path_km;       /* P' at the receiver distance */
+    double el_deg;              /* launch elevation reaching the receiver distance */
+    double ground_range_km;     /* D_rx */
+    int32_t mode;               /* +1 ordinary, -1 extraordinary */
+    int32_t branch;
+} rt_ionogram_point;           /* 40 bytes */
+
+rt_err rt_ionogram(const rt_grid *grid, const rt_ionogram_desc *desc, rt_ionogram_point *out_host, size_t cap,
+                   size_t *n_points, const rt_launch_config *cfg, void *stream);
 
 /* Diagnostic: the right-hand side dy/dP' of the ray equations (Eq. 1a-1f)
  * at n given states, exactly as one stage of the tracer evaluates it.

@@ -102,7 +102,8 @@ rt_err validate_grid_desc(const rt_grid_desc *d) {
     if (!std::isfinite(d->field.b0_tesla) || d->field.b0_tesla < 0.0 || !std::isfinite(d->field.pole_lat_deg) ||
         !std::isfinite(d->field.pole_lon_deg))
         return fail(RT_EINVAL, "dipole parameters must be finite, b0 >= 0");
-    if (d->flags & ~(uint32_t)RT_GRID_TABLE) return fail(RT_EINVAL, "unknown grid flags 0x%x", d->flags);
+    if (d->flags & ~(uint32_t)(RT_GRID_TABLE | RT_GRID_CATMULL_ROM))
+        return fail(RT_EINVAL, "unknown grid flags 0x%x", d->flags);
     if (d->reserved != 0) return fail(RT_EINVAL, "reserved field must be 0");
     return RT_OK;
 }
@@ -183,6 +184,9 @@ rt_err make_plan(const rt_grid *grid, const rt_fan_desc *fan, size_t n_rays, con
     if (c.order != RT_ORDER_CANONICAL && c.order != RT_ORDER_ELEVATION_FASTEST)
         return fail(RT_EINVAL, "unknown order %d", c.order);
     if (c.blocks_per_sm < 0) return fail(RT_EINVAL, "blocks_per_sm must be >= 0");
+    if (c.lanes_per_ray != 0 && c.lanes_per_ray != 1 && c.lanes_per_ray != 2 && c.lanes_per_ray != 4)
+        return fail(RT_EINVAL, "lanes_per_ray must be 0, 1, 2 or 4");
+    if (c.reserved[0] != 0 || c.reserved[1] != 0) return fail(RT_EINVAL, "reserved fields must be 0");
     if (fan->precision == RT_MIXED && c.kernel == RT_KERNEL_AUTO && c.stencil == RT_STENCIL_AUTO) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tuned.find(std::make_tuple(grid, fan->integrator, ray_bucket(n_rays)));
@@ -195,17 +199,32 @@ rt_err make_plan(const rt_grid *grid, const rt_fan_desc *fan, size_t n_rays, con
     if (c.stencil == RT_STENCIL_TABLE && !grid->table)
         return fail(RT_EINVAL, "stencil TABLE needs a grid created with RT_GRID_TABLE");
     if (c.order == RT_ORDER_CANONICAL && cfg == nullptr) c.order = RT_ORDER_ELEVATION_FASTEST;
+    if (fan->precision == RT_FP64 && c.lanes_per_ray > 1)
+        return fail(RT_EINVAL, "the FP64 path runs one lane per ray");
     lp->kernel = c.kernel;
     lp->stencil = c.stencil;
     lp->threads = c.block_threads ? c.block_threads : 128;
     lp->blocks = 0;
+    lp->lanes = 1;
+    if (fan->precision == RT_MIXED) {
+        int lanes = c.lanes_per_ray;
+        if (lanes == 0) {
+            // as many lanes per ray as keep the fan within the resident lanes
+            int occ = 0;
+            CUDA_TRY(persistent_occupancy(c.stencil, 1, lp->threads, &occ));
+            const long long resident = (long long)props(grid->device).sms * std::max(occ, 1) * lp->threads;
+            lanes = 1;
+            while (lanes < 4 && (long long)n_rays * lanes * 2 <= resident) lanes *= 2;
+        }
+        lp->lanes = lanes;
+    }
     if (fan->precision == RT_MIXED && c.kernel == RT_KERNEL_PERSISTENT) {
         int occ = 0;
-        CUDA_TRY(persistent_occupancy(c.stencil, lp->threads, &occ));
+        CUDA_TRY(persistent_occupancy(c.stencil, lp->lanes, lp->threads, &occ));
         if (occ < 1) return fail(RT_ECUDA, "persistent kernel does not fit on an SM with %d threads", lp->threads);
         if (c.blocks_per_sm > 0) occ = std::min(occ, c.blocks_per_sm);
         const long long want = (long long)props(grid->device).sms * occ;
-        const long long need = (long long)((n_rays + lp->threads - 1) / lp->threads);
+        const long long need = (long long)((n_rays * lp->lanes + lp->threads - 1) / lp->threads);
         lp->blocks = (int)std::max(1LL, std::min(want, need));
     }
     *order = c.order;
@@ -237,37 +256,8 @@ rt_err sync_with_timeout(cudaStream_t st) {
     }
 }
 
-// Queues one trace: scratch allocation, fan upload, kernel, scratch release.
-rt_err queue_trace(const rt_grid *grid, const rt_fan_desc *fan, rt_ray_result *out_dev, size_t out_len,
-                   const rt_launch_config *cfg, cudaStream_t st) {
-    rt_err r = validate_fan(fan);
-    if (r != RT_OK) return r;
-    if (!grid) return fail(RT_EINVAL, "grid is NULL");
-    if (!out_dev) return fail(RT_EINVAL, "output pointer is NULL");
-    int dev = 0;
-    if ((r = ensure_device(&dev)) != RT_OK) return r;
-    if (dev != grid->device) return fail(RT_EINVAL, "grid lives on device %d, current device is %d", grid->device, dev);
-    const size_t n = fan_rays(fan);
-    if (out_len < n) return fail(RT_EINVAL, "out_len %zu < %zu rays", out_len, n);
-    if (n >= ((size_t)1 << 31)) return fail(RT_EINVAL, "fan too large (at most 2^31 - 1 rays)");
-    LaunchPlan lp;
-    int order = 0;
-    if ((r = make_plan(grid, fan, n, cfg, &lp, &order)) != RT_OK) return r;
-
-    const size_t n_tab = (size_t)fan->n_freq + fan->n_el + fan->n_az;
-    const size_t bytes = 16 + n_tab * sizeof(double);
-    char *ws = nullptr;
-    CUDA_TRY(cudaMallocAsync((void **)&ws, bytes, st));
-    unsigned long long *counter = (unsigned long long *)ws;
-    double *tab = (double *)(ws + 16);
-    cudaError_t e = cudaMemsetAsync(counter, 0, 16, st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(tab, fan->freq_mhz, fan->n_freq * sizeof(double), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(tab + fan->n_freq, fan->el_deg, fan->n_el * sizeof(double), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(tab + fan->n_freq + fan->n_el, fan->az_deg, fan->n_az * sizeof(double),
-                            cudaMemcpyHostToDevice, st);
+// Device view of a fan whose tables (freq, el, az) start at tab.
+FanDev fill_fandev(const rt_grid *grid, const rt_fan_desc *fan, size_t n, int order, const double *tab) {
     FanDev f;
     std::memset(&f, 0, sizeof(f));
     f.freq = tab;
@@ -301,6 +291,41 @@ rt_err queue_trace(const rt_grid *grid, const rt_fan_desc *fan, rt_ray_result *o
     f.hmin_f = (float)f.hmin;
     f.hmax_f = (float)f.hmax;
     f.has_max_path = f.max_path > 0.0 ? 1 : 0;
+    return f;
+}
+
+// Queues one trace: scratch allocation, fan upload, kernel, scratch release.
+rt_err queue_trace(const rt_grid *grid, const rt_fan_desc *fan, rt_ray_result *out_dev, size_t out_len,
+                   const rt_launch_config *cfg, cudaStream_t st) {
+    rt_err r = validate_fan(fan);
+    if (r != RT_OK) return r;
+    if (!grid) return fail(RT_EINVAL, "grid is NULL");
+    if (!out_dev) return fail(RT_EINVAL, "output pointer is NULL");
+    int dev = 0;
+    if ((r = ensure_device(&dev)) != RT_OK) return r;
+    if (dev != grid->device) return fail(RT_EINVAL, "grid lives on device %d, current device is %d", grid->device, dev);
+    const size_t n = fan_rays(fan);
+    if (out_len < n) return fail(RT_EINVAL, "out_len %zu < %zu rays", out_len, n);
+    if (n >= ((size_t)1 << 31)) return fail(RT_EINVAL, "fan too large (at most 2^31 - 1 rays)");
+    LaunchPlan lp;
+    int order = 0;
+    if ((r = make_plan(grid, fan, n, cfg, &lp, &order)) != RT_OK) return r;
+
+    const size_t n_tab = (size_t)fan->n_freq + fan->n_el + fan->n_az;
+    const size_t bytes = 16 + n_tab * sizeof(double);
+    char *ws = nullptr;
+    CUDA_TRY(cudaMallocAsync((void **)&ws, bytes, st));
+    unsigned long long *counter = (unsigned long long *)ws;
+    double *tab = (double *)(ws + 16);
+    cudaError_t e = cudaMemsetAsync(counter, 0, 16, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(tab, fan->freq_mhz, fan->n_freq * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(tab + fan->n_freq, fan->el_deg, fan->n_el * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(tab + fan->n_freq + fan->n_el, fan->az_deg, fan->n_az * sizeof(double),
+                            cudaMemcpyHostToDevice, st);
+    const FanDev f = fill_fandev(grid, fan, n, order, tab);
     if (e == cudaSuccess) e = launch_trace(grid->g, f, out_dev, counter, lp, st);
     const cudaError_t e2 = cudaFreeAsync(ws, st);
     if (e != cudaSuccess) return cuda_fail(e, "trace launch");
@@ -395,6 +420,7 @@ rt_err rt_grid_create(const rt_grid_desc *desc, const void *ne_host, rt_grid **o
     d.mf[2] = (float)d.m[2];
     d.top_f = (float)d.top;
     d.iso = d.b0 == 0.0 ? 1 : 0;
+    d.interp = (desc->flags & RT_GRID_CATMULL_ROM) ? 1 : 0;
     d.pad64 = g->pad64;
     d.pad32 = g->pad32;
     d.quad = g->quad;
@@ -459,7 +485,7 @@ rt_err rt_tune(const rt_grid *grid, const rt_fan_desc *fan, size_t max_rays, voi
     rt_err r = validate_fan(fan);
     if (r != RT_OK) return r;
     if ((r = ensure_device(nullptr)) != RT_OK) return r;
-    if (max_rays == 0) max_rays = 4096;
+    if (max_rays == 0) max_rays = 65536;
     cudaStream_t st = (cudaStream_t)stream;
     // strided sub-fan with at most max_rays rays (every k-th elevation, azimuth, frequency)
     std::vector<double> fr(fan->freq_mhz, fan->freq_mhz + fan->n_freq), el(fan->el_deg, fan->el_deg + fan->n_el),
@@ -494,12 +520,13 @@ rt_err rt_tune(const rt_grid *grid, const rt_fan_desc *fan, size_t max_rays, voi
         for (int kernel : {RT_KERNEL_PLAIN, RT_KERNEL_PERSISTENT})
             for (int stencil : {RT_STENCIL_GATHER, RT_STENCIL_QUAD, RT_STENCIL_TABLE})
                 for (int order : {RT_ORDER_CANONICAL, RT_ORDER_ELEVATION_FASTEST})
-                    for (int threads : {64, 128}) {
+                    for (int lanes : {1, 2, 4}) {
                         if (stencil == RT_STENCIL_TABLE && !grid->table) continue;
                         c.kernel = kernel;
                         c.stencil = stencil;
                         c.order = order;
-                        c.block_threads = threads;
+                        c.block_threads = 128;
+                        c.lanes_per_ray = lanes;
                         cands.push_back(c);
                     }
     }
@@ -537,6 +564,169 @@ rt_err rt_tune(const rt_grid *grid, const rt_fan_desc *fan, size_t max_rays, voi
     }
     *best = best_c;
     if (best_ms) *best_ms = best_t;
+    return RT_OK;
+}
+
+struct rt_plan {
+    const rt_grid *grid = nullptr;
+    FanDev f;
+    LaunchPlan lp;
+    size_t n = 0;
+    char *ws = nullptr;  // ray counter (16 B) + fan tables
+};
+
+rt_err rt_plan_create(const rt_grid *grid, const rt_fan_desc *fan, const rt_launch_config *cfg, rt_plan **out) {
+    if (!out) return fail(RT_EINVAL, "out is NULL");
+    *out = nullptr;
+    rt_err r = validate_fan(fan);
+    if (r != RT_OK) return r;
+    if (!grid) return fail(RT_EINVAL, "grid is NULL");
+    int dev = 0;
+    if ((r = ensure_device(&dev)) != RT_OK) return r;
+    if (dev != grid->device) return fail(RT_EINVAL, "grid lives on device %d, current device is %d", grid->device, dev);
+    const size_t n = fan_rays(fan);
+    if (n >= ((size_t)1 << 31)) return fail(RT_EINVAL, "fan too large (at most 2^31 - 1 rays)");
+    rt_plan *p = new rt_plan();
+    int order = 0;
+    if ((r = make_plan(grid, fan, n, cfg, &p->lp, &order)) != RT_OK) {
+        delete p;
+        return r;
+    }
+    const size_t n_tab = (size_t)fan->n_freq + fan->n_el + fan->n_az;
+    cudaError_t e = cudaMalloc((void **)&p->ws, 16 + n_tab * sizeof(double));
+    double *tab = (double *)(p->ws + 16);
+    if (e == cudaSuccess) e = cudaMemcpy(tab, fan->freq_mhz, fan->n_freq * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(tab + fan->n_freq, fan->el_deg, fan->n_el * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(tab + fan->n_freq + fan->n_el, fan->az_deg, fan->n_az * sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(p->ws);
+        delete p;
+        return cuda_fail(e, "rt_plan_create");
+    }
+    p->grid = grid;
+    p->n = n;
+    p->f = fill_fandev(grid, fan, n, order, tab);
+    *out = p;
+    return RT_OK;
+}
+
+size_t rt_plan_rays(const rt_plan *plan) { return plan ? plan->n : 0; }
+
+rt_err rt_plan_execute(const rt_plan *plan, rt_ray_result *out_dev, size_t out_len, void *stream) {
+    if (!plan || !out_dev) return fail(RT_EINVAL, "NULL argument");
+    if (out_len < plan->n) return fail(RT_EINVAL, "out_len %zu < %zu rays", out_len, plan->n);
+    cudaStream_t st = (cudaStream_t)stream;
+    CUDA_TRY(cudaMemsetAsync(plan->ws, 0, 16, st));
+    CUDA_TRY(launch_trace(plan->grid->g, plan->f, out_dev, (unsigned long long *)plan->ws, plan->lp, st));
+    return RT_OK;
+}
+
+rt_err rt_plan_destroy(rt_plan *plan) {
+    if (!plan) return RT_OK;
+    const cudaError_t e = cudaFree(plan->ws);
+    delete plan;
+    if (e != cudaSuccess) return cuda_fail(e, "rt_plan_destroy");
+    return RT_OK;
+}
+
+rt_err rt_ionogram(const rt_grid *grid, const rt_ionogram_desc *d, rt_ionogram_point *out_host, size_t cap,
+                   size_t *n_points, const rt_launch_config *cfg, void *stream) {
+    if (!grid || !d || !n_points || (cap > 0 && !out_host)) return fail(RT_EINVAL, "NULL argument");
+    *n_points = 0;
+    if (!std::isfinite(d->rx_lat_deg) || !std::isfinite(d->rx_lon_deg) || d->rx_lat_deg <= -90.0 ||
+        d->rx_lat_deg >= 90.0)
+        return fail(RT_EINVAL, "receiver position must be finite with |lat| < 90");
+    for (int i = 1; i < d->n_el && d->el_deg; ++i)
+        if (!(d->el_deg[i] > d->el_deg[i - 1])) return fail(RT_EINVAL, "el_deg must be ascending");
+    // great-circle distance and initial bearing transmitter -> receiver
+    const double p1 = d->tx_lat_deg * kDeg2Rad, p2 = d->rx_lat_deg * kDeg2Rad;
+    const double dl = (d->rx_lon_deg - d->tx_lon_deg) * kDeg2Rad;
+    const double x = std::cos(p1) * std::sin(p2) - std::sin(p1) * std::cos(p2) * std::cos(dl);
+    const double yv = std::sin(dl) * std::cos(p2);
+    const double c = std::sin(p1) * std::sin(p2) + std::cos(p1) * std::cos(p2) * std::cos(dl);
+    const double ang = std::atan2(std::sqrt(x * x + yv * yv), c);
+    if (!(ang > 0.0)) return fail(RT_EINVAL, "receiver coincides with the transmitter");
+    const double d_rx = grid->desc.earth_radius_km * ang;
+    const double az = std::atan2(yv, x) * kRad2Deg;
+    rt_fan_desc fan;
+    std::memset(&fan, 0, sizeof(fan));
+    fan.tx_lat_deg = d->tx_lat_deg;
+    fan.tx_lon_deg = d->tx_lon_deg;
+    fan.tx_alt_km = d->tx_alt_km;
+    fan.freq_mhz = d->freq_mhz;
+    fan.el_deg = d->el_deg;
+    fan.az_deg = &az;
+    fan.n_freq = d->n_freq;
+    fan.n_el = d->n_el;
+    fan.n_az = 1;
+    fan.modes = d->modes;
+    fan.integrator = d->integrator;
+    fan.precision = d->precision;
+    fan.h_km = d->h_km;
+    fan.rtol = d->rtol;
+    fan.atol_km = d->atol_km;
+    fan.h_min_km = d->h_min_km;
+    fan.h_max_km = d->h_max_km;
+    fan.max_steps = d->max_steps;
+    rt_err r = validate_fan(&fan);
+    if (r != RT_OK) return r;
+    if ((r = ensure_device(nullptr)) != RT_OK) return r;
+    const size_t n = fan_rays(&fan);
+    const int n_modes = ((d->modes & RT_MODE_O) ? 1 : 0) + ((d->modes & RT_MODE_X) ? 1 : 0);
+    // the reduction can emit at most (n_el - 1) points per trace
+    const size_t max_pts = (size_t)d->n_freq * n_modes * (size_t)(d->n_el > 1 ? d->n_el - 1 : 0);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t tab = (size_t)d->n_freq + d->n_el;
+    const size_t bytes = 16 + tab * sizeof(double) + n * sizeof(rt_ray_result) + max_pts * sizeof(rt_ionogram_point);
+    char *ws = nullptr;
+    CUDA_TRY(cudaMallocAsync((void **)&ws, bytes, st));
+    unsigned long long *count = (unsigned long long *)ws;
+    double *tf = (double *)(ws + 16);
+    rt_ray_result *res = (rt_ray_result *)(tf + tab);
+    rt_ionogram_point *pts = (rt_ionogram_point *)(res + n);
+    cudaError_t e = cudaMemsetAsync(count, 0, 16, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(tf, d->freq_mhz, d->n_freq * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(tf + d->n_freq, d->el_deg, d->n_el * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(ws, st);
+        return cuda_fail(e, "rt_ionogram");
+    }
+    r = queue_trace(grid, &fan, res, n, cfg, st);
+    if (r == RT_OK) {
+        e = launch_ionogram(res, tf, tf + d->n_freq, d->n_freq, n_modes, (d->modes & RT_MODE_O) ? 1 : -1, d->n_el,
+                            d_rx, pts, max_pts, count, st);
+        if (e != cudaSuccess) r = cuda_fail(e, "ionogram kernel");
+    }
+    unsigned long long total = 0;
+    std::vector<rt_ionogram_point> hp;
+    if (r == RT_OK) r = sync_with_timeout(st);
+    if (r == RT_OK) {
+        e = cudaMemcpy(&total, count, sizeof(total), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && total > 0) {
+            hp.resize((size_t)std::min<unsigned long long>(total, max_pts));
+            e = cudaMemcpy(hp.data(), pts, hp.size() * sizeof(rt_ionogram_point), cudaMemcpyDeviceToHost);
+        }
+        if (e != cudaSuccess) r = cuda_fail(e, "ionogram copy");
+    }
+    cudaFreeAsync(ws, st);
+    if (r != RT_OK) return r;
+    // deterministic order and branch numbers: (frequency, mode O first, elevation)
+    std::sort(hp.begin(), hp.end(), [](const rt_ionogram_point &a, const rt_ionogram_point &b) {
+        if (a.freq_mhz != b.freq_mhz) return a.freq_mhz < b.freq_mhz;
+        if (a.mode != b.mode) return a.mode > b.mode;
+        return a.el_deg < b.el_deg;
+    });
+    for (size_t i = 0; i < hp.size(); ++i) {
+        const bool same = i > 0 && hp[i].freq_mhz == hp[i - 1].freq_mhz && hp[i].mode == hp[i - 1].mode;
+        hp[i].branch = same ? hp[i - 1].branch + 1 : 0;
+    }
+    const size_t w = std::min(cap, hp.size());
+    if (w) std::memcpy(out_host, hp.data(), w * sizeof(rt_ionogram_point));
+    *n_points = hp.size();
     return RT_OK;
 }
 

@@ -39,6 +39,7 @@ struct GridDev {
     float R_Ef, mf[3];               // float copies of R_E and m
     float top_f;                     // top as float
     int iso;                         // no field (b0 == 0)
+    int interp;                      // 0: Galerkin-Difference p=3, 1: Catmull-Rom (comparison)
     const double *pad64;             // (n_lat+2)(n_lon+2)(n_alt+2) doubles
     const float *pad32;              // same, rounded to float
     const float4 *quad;              // (n_lat+2)(n_lon+2)(n_alt-1): samples k-1..k+2 of cell k
@@ -65,6 +66,46 @@ __device__ __forceinline__ void gd_weights(R t, R w[4], R d[4]) {
     d[3] = -(R(-0.5) + s * (R(11.0 / 6.0) + s * (R(-0.5) + s * (R(-5.0 / 3.0) + s * R(5.0 / 6.0)))));
 }
 
+// The weights of nodes j-1 and j (and their t-derivatives) at local
+// coordinate s; mirrored (s = 1 - t, derivatives negated) they are the
+// weights of nodes j+2 and j+1.  interp 0: GD p = 3 (Appendix A); interp 1:
+// Catmull-Rom (Eq. 7), w_{-1} = (-s^3 + 2s^2 - s)/2, w_0 = (3s^3 - 5s^2 + 2)/2,
+// whose mirror images are w_2 and w_1.
+template <typename R>
+__device__ __forceinline__ void gd_half(R s, R &wm1, R &w0, R &dm1, R &d0, int interp = 0) {
+    if (interp == 1) {
+        wm1 = s * (R(-0.5) + s * (R(1) - s * R(0.5)));
+        w0 = R(1) + s * s * (R(-2.5) + s * R(1.5));
+        dm1 = R(-0.5) + s * (R(2) - s * R(1.5));
+        d0 = s * (R(-5) + s * R(4.5));
+        return;
+    }
+    wm1 = s * (R(-0.5) + s * (R(11.0 / 12.0) + s * (R(-1.0 / 6.0) + s * (R(-5.0 / 12.0) + s * R(1.0 / 6.0)))));
+    w0 = R(1) + s * s * (R(-2.25) + s * (R(0.5) + s * (R(1.25) - s * R(0.5))));
+    dm1 = R(-0.5) + s * (R(11.0 / 6.0) + s * (R(-0.5) + s * (R(-5.0 / 3.0) + s * R(5.0 / 6.0))));
+    d0 = s * (R(-4.5) + s * (R(1.5) + s * (R(5.0) - s * R(2.5))));
+}
+
+// All four weights of one axis (w[a], d[a] for node j-1+a), GD or CR.
+template <typename R>
+__device__ __forceinline__ void interp_weights(R t, R w[4], R d[4], int interp) {
+    if (interp == 1) {
+        R wm1, w0, dm1, d0, wp2, wp1, dp2, dp1;
+        gd_half<R>(t, wm1, w0, dm1, d0, 1);
+        gd_half<R>(R(1) - t, wp2, wp1, dp2, dp1, 1);
+        w[0] = wm1;
+        w[1] = w0;
+        w[2] = wp1;
+        w[3] = wp2;
+        d[0] = dm1;
+        d[1] = d0;
+        d[2] = -dp1;
+        d[3] = -dp2;
+        return;
+    }
+    gd_weights<R>(t, w, d);
+}
+
 // Eq. 13 contraction of one row of 4 altitude samples.
 template <typename R>
 __device__ __forceinline__ void row4(R u0, R u1, R u2, R u3, const R wc[4], const R dc[4], R &v, R &dv) {
@@ -80,19 +121,21 @@ __device__ __forceinline__ void acc_row(R v, R dv, R wb, R db, R &s, R &sb, R &s
     sc += dv * wb;
 }
 
-// out = {Ne, dNe/dxa, dNe/dxb, dNe/dxc} in per-cell units, from the 16 rows
-// of 4 altitude samples.  ROW(a, b, u0..u3) loads row (a, b).  The samples
-// are contracted relative to REF (Ne = REF + sum (u - REF) w, the weights
-// summing to 1 and their derivatives to 0), so that in float the sums do not
-// cancel against the magnitude of Ne; REF = 0 gives the plain sum.
-#define RTGD_CONTRACT(R, ROW, REF, wa, da, wb, db, wc, dc, out)                   \
+// Partial sums {Ne - REF, dNe/dxa, dNe/dxb, dNe/dxc} (per-cell units) over
+// the rows a = A0 .. A0+NA-1 (all b) of the 16 rows of 4 altitude samples;
+// wa/da hold the NA lat-weights of those rows.  ROW(a, b, u0..u3) loads row
+// (a, b).  The samples are contracted relative to REF (Ne = REF + sum (u -
+// REF) w, the weights summing to 1 and their derivatives to 0), so that in
+// float the sums do not cancel against the magnitude of Ne; the caller adds
+// REF back (after combining partial sums, when the rows are split).
+#define RTGD_CONTRACT(R, ROW, REF, A0, NA, wa, da, wb, db, wc, dc, out)           \
     do {                                                                          \
         R n_ = R(0), na_ = R(0), nb_ = R(0), nc_ = R(0);                          \
-        _Pragma("unroll") for (int a_ = 0; a_ < 4; ++a_) {                        \
+        _Pragma("unroll") for (int a_ = 0; a_ < (NA); ++a_) {                     \
             R s_ = R(0), sb_ = R(0), sc_ = R(0);                                  \
             _Pragma("unroll") for (int b_ = 0; b_ < 4; ++b_) {                    \
                 R u0_, u1_, u2_, u3_, v_, dv_;                                    \
-                ROW(a_, b_, u0_, u1_, u2_, u3_);                                  \
+                ROW((A0) + a_, b_, u0_, u1_, u2_, u3_);                           \
                 u0_ -= (REF);                                                     \
                 u1_ -= (REF);                                                     \
                 u2_ -= (REF);                                                     \
@@ -105,7 +148,7 @@ __device__ __forceinline__ void acc_row(R v, R dv, R wb, R db, R &s, R &sb, R &s
             nb_ += sb_ * wa[a_];                                                  \
             nc_ += sc_ * wa[a_];                                                  \
         }                                                                         \
-        out[0] = n_ + (REF);                                                      \
+        out[0] = n_;                                                              \
         out[1] = na_;                                                             \
         out[2] = nb_;                                                             \
         out[3] = nc_;                                                             \

@@ -33,6 +33,7 @@ struct LaunchPlan {
     int stencil;  // RT_STENCIL_GATHER / QUAD / TABLE
     int threads;
     int blocks;   // persistent grid size
+    int lanes;    // lanes per ray (1, 2, 4)
 };
 
 cudaError_t launch_grid_prep(const void *raw, int dtype, const GridSizes &sz, double *pad64, float *pad32,
@@ -40,7 +41,11 @@ cudaError_t launch_grid_prep(const void *raw, int dtype, const GridSizes &sz, do
 cudaError_t upload_tableaus();
 cudaError_t launch_trace(const GridDev &g, const FanDev &f, rt_ray_result *out, unsigned long long *counter,
                          const LaunchPlan &lp, cudaStream_t st);
-cudaError_t persistent_occupancy(int stencil, int threads, int *blocks_per_sm);
+cudaError_t persistent_occupancy(int stencil, int lanes, int threads, int *blocks_per_sm);
+cudaError_t launch_ionogram(const rt_ray_result *res, const double *freq, const double *el, int n_freq, int n_modes,
+                            int mode0, int n_el, double d_rx, rt_ionogram_point *out, unsigned long long cap,
+                            unsigned long long *count, cudaStream_t st);
+
 cudaError_t launch_eval_rhs(const GridDev &g, const double *ys, double *dys, double *mu2s, double freq_mhz, int mode,
                             int precision, int stencil, long long n, cudaStream_t st);
 

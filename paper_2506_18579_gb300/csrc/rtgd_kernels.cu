@@ -251,9 +251,9 @@ __device__ void rhs64(const GridDev &g, const RayPhys<double> &rp, const double 
     if (cell_coord<double>(xa, g.n_lat, ia, ta) && cell_coord<double>(xb, g.n_lon, ib, tb) &&
         cell_coord<double>(xc, g.n_alt, ic, tc)) {
         double wa[4], da[4], wb[4], db[4], wc[4], dc[4], out[4];
-        gd_weights<double>(ta, wa, da);
-        gd_weights<double>(tb, wb, db);
-        gd_weights<double>(tc, wc, dc);
+        interp_weights<double>(ta, wa, da, g.interp);
+        interp_weights<double>(tb, wb, db, g.interp);
+        interp_weights<double>(tc, wc, dc, g.interp);
         const long long sj = g.p_alt, si = (long long)g.p_lon * g.p_alt;
         // padded index of node (ia-1, ib-1, ic-1) is (ia, ib, ic)
         const double *base = g.pad64 + (long long)ia * si + (long long)ib * sj + ic;
@@ -265,7 +265,7 @@ __device__ void rhs64(const GridDev &g, const RayPhys<double> &rp, const double 
         u2 = __ldg(p_ + 2);                           \
         u3 = __ldg(p_ + 3);                           \
     }
-        RTGD_CONTRACT(double, RTGD_ROW64, 0.0, wa, da, wb, db, wc, dc, out);
+        RTGD_CONTRACT(double, RTGD_ROW64, 0.0, 0, 4, wa, da, wb, db, wc, dc, out);
 #undef RTGD_ROW64
         s.X = rp.xfac * out[0];
         s.dX[0] = rp.xfac * out[3] * g.inv_dalt;
@@ -646,10 +646,37 @@ __device__ __forceinline__ bool stage_cell(int i0, float t, int n, int &i, float
     return true;
 }
 
-// dy/dP' (float) at base + delta.  STENCIL selects where the 64 samples come from.
-template <int STENCIL>
+// Lat-weights of the rows a = q*4/G .. (q+1)*4/G - 1 handled by lane q of a
+// group of G lanes (G = 1: all four).
+template <int G>
+__device__ __forceinline__ void own_lat_weights(float ta, int q, float wa[4], float da[4], int interp) {
+    if (G == 1) {
+        interp_weights<float>(ta, wa, da, interp);
+    } else if (G == 2) {
+        const bool hi = q != 0;  // rows 2, 3: nodes j+1, j+2
+        float wm1, w0, dm1, d0;
+        gd_half<float>(hi ? 1.0f - ta : ta, wm1, w0, dm1, d0, interp);
+        wa[0] = hi ? w0 : wm1;
+        wa[1] = hi ? wm1 : w0;
+        da[0] = hi ? -d0 : dm1;
+        da[1] = hi ? -dm1 : d0;
+    } else {
+        const bool hi = q >= 2;
+        float wm1, w0, dm1, d0;
+        gd_half<float>(hi ? 1.0f - ta : ta, wm1, w0, dm1, d0, interp);
+        const bool outer = q == 0 || q == 3;  // nodes j-1, j+2
+        wa[0] = outer ? wm1 : w0;
+        da[0] = (outer ? dm1 : d0) * (hi ? -1.0f : 1.0f);
+    }
+}
+
+// dy/dP' (float) at base + delta.  STENCIL selects where the 64 samples come
+// from; with G > 1 the G lanes of a group (lane q, shuffle mask gmask) split
+// the 16 sample rows and combine their partial sums with a butterfly, whose
+// every addition is commutative, so all lanes hold bitwise equal results.
+template <int STENCIL, int G>
 __device__ __forceinline__ void rhs_mixed(const GridDev &g, const RayPhys<float> &rp, const Base32 &b,
-                                          const float d[6], float dy[6], float *mu2) {
+                                          const float d[6], float dy[6], float *mu2, int q, unsigned gmask) {
     StageIn<float> s;
     s.r = b.r + d[0];
     angle_add(b.sth, b.cth, d[1], s.sth, s.cth);
@@ -663,43 +690,45 @@ __device__ __forceinline__ void rhs_mixed(const GridDev &g, const RayPhys<float>
     float ta, tb, tc;
     if (stage_cell(b.ia, b.ta + g.sa * d[1], g.n_lat, ia, ta) && stage_cell(b.ib, b.tb + g.sb * d[2], g.n_lon, ib, tb) &&
         stage_cell(b.ic, b.tc + g.sc * d[0], g.n_alt, ic, tc)) {
-        float wa[4], da[4], wb[4], db[4], wc[4], dc[4], out[4];
-        gd_weights<float>(ta, wa, da);
-        gd_weights<float>(tb, wb, db);
-        gd_weights<float>(tc, wc, dc);
+        float wa[4], da[4], wb[4], db[4], wc[4], dc[4], out[4], ref;
+        constexpr int NA = 4 / G;
+        const int a0 = q * NA;
+        own_lat_weights<G>(ta, q, wa, da, g.interp);
+        interp_weights<float>(tb, wb, db, g.interp);
+        interp_weights<float>(tc, wc, dc, g.interp);
         if (STENCIL == RT_STENCIL_QUAD) {
             // quad (pi, pj, k): 4 samples of cell k in padded row (pi, pj); node i-1 -> padded i
             const long long sj = g.q_alt, si = (long long)(g.n_lon + 2) * g.q_alt;
-            const float4 *q = g.quad + (long long)ia * si + (long long)ib * sj + ic;
-            const float ref = __ldg(q + si + sj).y;  // node (ia, ib, ic)
-#define RTGD_ROWQ(a, b, u0, u1, u2, u3)                   \
-    {                                                     \
-        const float4 v_ = __ldg(q + (a) * si + (b) * sj); \
+            const float4 *qp = g.quad + (long long)ia * si + (long long)ib * sj + ic;
+            ref = __ldg(qp + si + sj).y;  // node (ia, ib, ic)
+#define RTGD_ROWQ(a, b, u0, u1, u2, u3)                    \
+    {                                                      \
+        const float4 v_ = __ldg(qp + (a) * si + (b) * sj); \
         u0 = v_.x;                                        \
         u1 = v_.y;                                        \
         u2 = v_.z;                                        \
         u3 = v_.w;                                        \
     }
-            RTGD_CONTRACT(float, RTGD_ROWQ, ref, wa, da, wb, db, wc, dc, out);
+            RTGD_CONTRACT(float, RTGD_ROWQ, ref, a0, NA, wa, da, wb, db, wc, dc, out);
 #undef RTGD_ROWQ
         } else if (STENCIL == RT_STENCIL_TABLE) {
             const long long cell = ((long long)ia * (g.n_lon - 1) + ib) * (g.n_alt - 1) + ic;
-            const float4 *q = g.table + cell * 16;
-            const float ref = __ldg(q + 5).y;  // node (ia, ib, ic)
-#define RTGD_ROWT(a, b, u0, u1, u2, u3)             \
-    {                                               \
-        const float4 v_ = __ldg(q + (a) * 4 + (b)); \
+            const float4 *qp = g.table + cell * 16;
+            ref = __ldg(qp + 5).y;  // node (ia, ib, ic)
+#define RTGD_ROWT(a, b, u0, u1, u2, u3)              \
+    {                                                \
+        const float4 v_ = __ldg(qp + (a) * 4 + (b)); \
         u0 = v_.x;                                  \
         u1 = v_.y;                                  \
         u2 = v_.z;                                  \
         u3 = v_.w;                                  \
     }
-            RTGD_CONTRACT(float, RTGD_ROWT, ref, wa, da, wb, db, wc, dc, out);
+            RTGD_CONTRACT(float, RTGD_ROWT, ref, a0, NA, wa, da, wb, db, wc, dc, out);
 #undef RTGD_ROWT
         } else {
             const long long sj = g.p_alt, si = (long long)g.p_lon * g.p_alt;
             const float *p = g.pad32 + (long long)ia * si + (long long)ib * sj + ic;
-            const float ref = __ldg(p + si + sj + 1);  // node (ia, ib, ic)
+            ref = __ldg(p + si + sj + 1);  // node (ia, ib, ic)
 #define RTGD_ROWG(a, b, u0, u1, u2, u3)            \
     {                                              \
         const float *p_ = p + (a) * si + (b) * sj; \
@@ -708,9 +737,17 @@ __device__ __forceinline__ void rhs_mixed(const GridDev &g, const RayPhys<float>
         u2 = __ldg(p_ + 2);                        \
         u3 = __ldg(p_ + 3);                        \
     }
-            RTGD_CONTRACT(float, RTGD_ROWG, ref, wa, da, wb, db, wc, dc, out);
+            RTGD_CONTRACT(float, RTGD_ROWG, ref, a0, NA, wa, da, wb, db, wc, dc, out);
 #undef RTGD_ROWG
         }
+        if (G > 1) {
+#pragma unroll
+            for (int o = 1; o < G; o <<= 1) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) out[i] += __shfl_xor_sync(gmask, out[i], o);
+            }
+        }
+        out[0] += ref;
         s.X = rp.xfac * out[0];
         s.dX[0] = rp.xfac * out[3] * g.sc;
         s.dX[1] = rp.xfac * out[1] * g.sa;
@@ -866,14 +903,16 @@ __device__ __forceinline__ void lane_state(const Lane &L, double y[6]) {
     }
 }
 
-__device__ __forceinline__ void lane_finish(Lane &L, const GridDev &g, const FanDev &f, rt_ray_result *out) {
+__device__ __forceinline__ void lane_finish(Lane &L, const GridDev &g, const FanDev &f, rt_ray_result *out,
+                                            bool writer = true) {
+    L.active = false;
+    if (!writer) return;
     rt_ray_result r;
     const double az = f.az[L.out_id % f.n_az] * kDeg2Rad;
     double y[6];
     lane_state(L, y);
     finish_result(f, az, y, L.P, (double)L.apo, L.status, L.n_steps, L.n_att, L.n_ev, g.R_E, &r);
     out[L.out_id] = r;
-    L.active = false;
 }
 
 // Once k1 is known: end an adaptive step just past the next cell face, and
@@ -913,8 +952,8 @@ __device__ __forceinline__ bool lane_begin_attempt(Lane &L, const GridDev &g, co
 
 // One stage evaluation of one lane plus its bookkeeping.  Returns true when
 // the ray has finished (status set).
-template <int STENCIL>
-__device__ bool lane_advance(Lane &L, const GridDev &g, const FanDev &f, const Tableau &T) {
+template <int STENCIL, int G>
+__device__ bool lane_advance(Lane &L, const GridDev &g, const FanDev &f, const Tableau &T, int q, unsigned gmask) {
     const double RE = g.R_E;
     const RayPhys<float> rp = lane_phys(g, L);
     float d[6], ks[6], mu2;
@@ -923,7 +962,7 @@ __device__ bool lane_advance(Lane &L, const GridDev &g, const FanDev &f, const T
         // mu^2 at the transmitter for the launch direction (|k| = 1 in the base)
 #pragma unroll
         for (int c = 0; c < 6; ++c) d[c] = 0.0f;
-        rhs_mixed<STENCIL>(g, rp, L.b, d, ks, &mu2);
+        rhs_mixed<STENCIL, G>(g, rp, L.b, d, ks, &mu2, q, gmask);
         L.launch = false;
         if (!(mu2 > 0.0f)) {
             L.status = RT_RAY_NONFINITE;
@@ -944,7 +983,7 @@ __device__ bool lane_advance(Lane &L, const GridDev &g, const FanDev &f, const T
     }
 #pragma unroll
     for (int c = 0; c < 6; ++c) d[c] = (L.stage == 0) ? 0.0f : L.hs * L.acc[0][c];
-    rhs_mixed<STENCIL>(g, rp, L.b, d, ks, nullptr);
+    rhs_mixed<STENCIL, G>(g, rp, L.b, d, ks, nullptr, q, gmask);
     if (L.stage == 0) {
 #pragma unroll
         for (int c = 0; c < 6; ++c) L.k1[c] = ks[c];
@@ -1092,34 +1131,45 @@ __device__ __forceinline__ void load_tableau(Tableau &T, int integrator) {
     __syncthreads();
 }
 
-// One ray per thread; each thread loops stage by stage until its ray ends.
-template <int STENCIL>
+// Shuffle mask of the G-lane group of this lane.
+template <int G>
+__device__ __forceinline__ unsigned group_mask(int lane) {
+    return G == 1 ? (1u << lane) : (((1u << G) - 1u) << (lane & ~(G - 1)));
+}
+
+// One ray per thread group of G lanes; each group loops stage by stage until
+// its ray ends.
+template <int STENCIL, int G>
 __global__ void __launch_bounds__(128, 3) trace_mixed_plain_kernel(GridDev g, FanDev f, rt_ray_result *__restrict__ out) {
     __shared__ Tableau T;
     load_tableau(T, f.integrator);
-    const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (id >= f.n_rays) return;
+    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long id = tid / G;
+    if (id >= f.n_rays) return;  // whole groups leave together
+    const int lane = threadIdx.x & 31, q = lane % G;
+    const unsigned gmask = group_mask<G>(lane);
     Lane L;
     L.active = true;
     lane_begin_ray(L, g, f, claim_to_ray(f, id));
     // bounded: at most (max_steps + 1) attempts of T.ns stages plus the launch
     const long long max_iter = ((long long)f.max_steps + 2) * 6 + 8;
     bool done = false;
-    for (long long it = 0; it < max_iter && !done; ++it) done = lane_advance<STENCIL>(L, g, f, T);
+    for (long long it = 0; it < max_iter && !done; ++it) done = lane_advance<STENCIL, G>(L, g, f, T, q, gmask);
     if (!done) L.status = RT_RAY_MAX_STEPS;
-    lane_finish(L, g, f, out);
+    lane_finish(L, g, f, out, q == 0);
 }
 
 // Persistent kernel: resident blocks; every warp keeps its 32 lanes busy by
 // claiming new rays (one atomicAdd per warp for all idle lanes) as rays end.
-template <int STENCIL>
+template <int STENCIL, int G>
 __global__ void __launch_bounds__(128, 3) trace_mixed_persistent_kernel(GridDev g, FanDev f,
                                                                      rt_ray_result *__restrict__ out,
                                                                      unsigned long long *__restrict__ counter) {
     __shared__ Tableau T;
     load_tableau(T, f.integrator);
     const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, q = lane % G;
+    const unsigned gmask = group_mask<G>(lane);
     Lane L;
     L.active = false;
     bool exhausted = false;  // warp-uniform
@@ -1129,16 +1179,17 @@ __global__ void __launch_bounds__(128, 3) trace_mixed_persistent_kernel(GridDev 
     // (max_steps + 2) * 6 + 8 stage iterations, and a warp runs at most all n rays
     const long long max_iter = (((long long)f.max_steps + 2) * 6 + 8) * (n + 32) + 64;
     for (;;) {
+        // the lanes of a group share their ray, so idle lanes come in whole groups
         const unsigned idle = __ballot_sync(FULL, !L.active);
         if (idle != 0u && !exhausted) {
-            const int n_idle = __popc(idle);
+            const int n_idle = __popc(idle) / G;
             const int leader = __ffs(idle) - 1;
             unsigned long long base = 0;
             if (lane == leader) base = atomicAdd(counter, (unsigned long long)n_idle);
             base = __shfl_sync(FULL, base, leader);
             if (base + (unsigned long long)n_idle >= (unsigned long long)n) exhausted = true;
             if (!L.active) {
-                const unsigned long long c = base + __popc(idle & ((1u << lane) - 1u));
+                const unsigned long long c = base + __popc(idle & ((1u << lane) - 1u)) / G;
                 if (c < (unsigned long long)n) {
                     L.active = true;
                     lane_begin_ray(L, g, f, claim_to_ray(f, (long long)c));
@@ -1149,12 +1200,71 @@ __global__ void __launch_bounds__(128, 3) trace_mixed_persistent_kernel(GridDev 
         if (++iters > max_iter) {  // defensive bound; never reached for valid inputs
             if (L.active) {
                 L.status = RT_RAY_MAX_STEPS;
-                lane_finish(L, g, f, out);
+                lane_finish(L, g, f, out, q == 0);
             }
             break;
         }
-        if (L.active && lane_advance<STENCIL>(L, g, f, T)) lane_finish(L, g, f, out);
+        if (L.active && lane_advance<STENCIL, G>(L, g, f, T, q, gmask)) lane_finish(L, g, f, out, q == 0);
     }
+}
+
+// ================================================================ ionogram
+// One warp per (frequency, mode) trace: lanes scan neighbouring elevation
+// pairs; the pairs whose landed rays bracket the receiver distance d_rx emit
+// an ionogram point, appended through one atomicAdd per warp (ballot +
+// popc rank: warp-level compaction).  Branch numbers are assigned after the
+// host sorts the points.
+__global__ void ionogram_kernel(const rt_ray_result *__restrict__ res, const double *__restrict__ freq,
+                                const double *__restrict__ el, int n_freq, int n_modes, int mode0, int n_el,
+                                double d_rx, rt_ionogram_point *__restrict__ out, unsigned long long cap,
+                                unsigned long long *__restrict__ count) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const long long trace = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / 32;
+    if (trace >= (long long)n_freq * n_modes) return;  // whole warps leave together
+    const int fi = (int)(trace / n_modes), mi = (int)(trace % n_modes);
+    const rt_ray_result *row = res + trace * n_el;  // the fan has one azimuth
+    for (int j0 = 0; j0 < n_el - 1; j0 += 32) {
+        const int j = j0 + lane;
+        bool hit = false;
+        rt_ionogram_point p;
+        if (j < n_el - 1) {
+            const rt_ray_result a = row[j], b = row[j + 1];
+            if (a.status == RT_RAY_LANDED && b.status == RT_RAY_LANDED) {
+                const double fa = a.ground_range_km - d_rx, fb = b.ground_range_km - d_rx;
+                if ((fa < 0.0 && fb >= 0.0) || (fa >= 0.0 && fb < 0.0)) {
+                    const double t = fa / (fa - fb);
+                    p.freq_mhz = freq[fi];
+                    p.group_path_km = a.group_path_km + t * (b.group_path_km - a.group_path_km);
+                    p.el_deg = el[j] + t * (el[j + 1] - el[j]);
+                    p.ground_range_km = d_rx;
+                    p.mode = (mi == 0) ? mode0 : -1;
+                    p.branch = 0;
+                    hit = true;
+                }
+            }
+        }
+        const unsigned m = __ballot_sync(FULL, hit);
+        if (m) {
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(count, (unsigned long long)__popc(m));
+            base = __shfl_sync(FULL, base, 0);
+            if (hit) {
+                const unsigned long long idx = base + __popc(m & ((1u << lane) - 1u));
+                if (idx < cap) out[idx] = p;
+            }
+        }
+    }
+}
+
+cudaError_t launch_ionogram(const rt_ray_result *res, const double *freq, const double *el, int n_freq, int n_modes,
+                            int mode0, int n_el, double d_rx, rt_ionogram_point *out, unsigned long long cap,
+                            unsigned long long *count, cudaStream_t st) {
+    const long long threads = (long long)n_freq * n_modes * 32;
+    if (threads == 0) return cudaSuccess;
+    ionogram_kernel<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(res, freq, el, n_freq, n_modes, mode0, n_el,
+                                                                      d_rx, out, cap, count);
+    return cudaGetLastError();
 }
 
 // ============================================================== diagnostics
@@ -1174,9 +1284,9 @@ __global__ void eval_rhs_kernel(GridDev g, const double *__restrict__ ys, double
         Base32 b;
         base_from_state(g, y, b);
         float d[6] = {0, 0, 0, 0, 0, 0}, dyf[6], m2;
-        if (stencil == RT_STENCIL_TABLE) rhs_mixed<RT_STENCIL_TABLE>(g, rp, b, d, dyf, &m2);
-        else if (stencil == RT_STENCIL_GATHER) rhs_mixed<RT_STENCIL_GATHER>(g, rp, b, d, dyf, &m2);
-        else rhs_mixed<RT_STENCIL_QUAD>(g, rp, b, d, dyf, &m2);
+        if (stencil == RT_STENCIL_TABLE) rhs_mixed<RT_STENCIL_TABLE, 1>(g, rp, b, d, dyf, &m2, 0, 0u);
+        else if (stencil == RT_STENCIL_GATHER) rhs_mixed<RT_STENCIL_GATHER, 1>(g, rp, b, d, dyf, &m2, 0, 0u);
+        else rhs_mixed<RT_STENCIL_QUAD, 1>(g, rp, b, d, dyf, &m2, 0, 0u);
 #pragma unroll
         for (int c = 0; c < 6; ++c) dy[c] = dyf[c];
         mu2 = m2;
@@ -1242,16 +1352,26 @@ cudaError_t upload_tableaus() {
     return cudaMemcpyToSymbol(c_pow2q, q, sizeof(q));
 }
 
+template <int STENCIL, int G>
+static cudaError_t launch_mixed_g(const GridDev &g, const FanDev &f, rt_ray_result *out,
+                                  unsigned long long *counter, const LaunchPlan &lp, cudaStream_t st) {
+    if (lp.kernel == RT_KERNEL_PERSISTENT) {
+        trace_mixed_persistent_kernel<STENCIL, G><<<lp.blocks, lp.threads, 0, st>>>(g, f, out, counter);
+    } else {
+        const long long blocks = (f.n_rays * G + lp.threads - 1) / lp.threads;
+        trace_mixed_plain_kernel<STENCIL, G><<<(unsigned)blocks, lp.threads, 0, st>>>(g, f, out);
+    }
+    return cudaGetLastError();
+}
+
 template <int STENCIL>
 static cudaError_t launch_mixed(const GridDev &g, const FanDev &f, rt_ray_result *out,
                                 unsigned long long *counter, const LaunchPlan &lp, cudaStream_t st) {
-    if (lp.kernel == RT_KERNEL_PERSISTENT) {
-        trace_mixed_persistent_kernel<STENCIL><<<lp.blocks, lp.threads, 0, st>>>(g, f, out, counter);
-    } else {
-        const int blocks = (int)((f.n_rays + lp.threads - 1) / lp.threads);
-        trace_mixed_plain_kernel<STENCIL><<<blocks, lp.threads, 0, st>>>(g, f, out);
+    switch (lp.lanes) {
+        case 2: return launch_mixed_g<STENCIL, 2>(g, f, out, counter, lp, st);
+        case 4: return launch_mixed_g<STENCIL, 4>(g, f, out, counter, lp, st);
+        default: return launch_mixed_g<STENCIL, 1>(g, f, out, counter, lp, st);
     }
-    return cudaGetLastError();
 }
 
 cudaError_t launch_trace(const GridDev &g, const FanDev &f, rt_ray_result *out, unsigned long long *counter,
@@ -1270,17 +1390,26 @@ cudaError_t launch_trace(const GridDev &g, const FanDev &f, rt_ray_result *out, 
     }
 }
 
-cudaError_t persistent_occupancy(int stencil, int threads, int *blocks_per_sm) {
-    switch (stencil) {
-        case RT_STENCIL_GATHER:
+template <int STENCIL>
+static cudaError_t occupancy_s(int lanes, int threads, int *blocks_per_sm) {
+    switch (lanes) {
+        case 2:
             return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                blocks_per_sm, trace_mixed_persistent_kernel<RT_STENCIL_GATHER>, threads, 0);
-        case RT_STENCIL_TABLE:
+                blocks_per_sm, trace_mixed_persistent_kernel<STENCIL, 2>, threads, 0);
+        case 4:
             return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                blocks_per_sm, trace_mixed_persistent_kernel<RT_STENCIL_TABLE>, threads, 0);
+                blocks_per_sm, trace_mixed_persistent_kernel<STENCIL, 4>, threads, 0);
         default:
             return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                blocks_per_sm, trace_mixed_persistent_kernel<RT_STENCIL_QUAD>, threads, 0);
+                blocks_per_sm, trace_mixed_persistent_kernel<STENCIL, 1>, threads, 0);
+    }
+}
+
+cudaError_t persistent_occupancy(int stencil, int lanes, int threads, int *blocks_per_sm) {
+    switch (stencil) {
+        case RT_STENCIL_GATHER: return occupancy_s<RT_STENCIL_GATHER>(lanes, threads, blocks_per_sm);
+        case RT_STENCIL_TABLE: return occupancy_s<RT_STENCIL_TABLE>(lanes, threads, blocks_per_sm);
+        default: return occupancy_s<RT_STENCIL_QUAD>(lanes, threads, blocks_per_sm);
     }
 }
 

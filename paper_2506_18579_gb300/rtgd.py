@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "librtgd.so")
 
 RT_OK, RT_EINVAL, RT_ENOMEM, RT_ECUDA, RT_ETIMEOUT, RT_EUNSUPPORTED = range(6)
 RT_F32, RT_F64 = 0, 1
-RT_GRID_TABLE = 1
+RT_GRID_TABLE, RT_GRID_CATMULL_ROM = 1, 2
 RT_MODE_O, RT_MODE_X = 1, 2
 RT_RK4, RT_RKF45 = 0, 1
 RT_FP64, RT_MIXED = 0, 1
@@ -30,7 +30,8 @@ RT_ORDER_CANONICAL, RT_ORDER_ELEVATION_FASTEST = 0, 1
 
 EXPORTED = ["rt_grid_create", "rt_grid_destroy", "rt_grid_device_bytes", "rt_fan_size",
             "rt_trace", "rt_trace_device", "rt_tune", "rt_eval_rhs", "rt_last_error",
-            "rt_version"]
+            "rt_version", "rt_plan_create", "rt_plan_rays", "rt_plan_execute", "rt_plan_destroy",
+            "rt_ionogram"]
 
 
 class RtError(RuntimeError):
@@ -71,8 +72,24 @@ class rt_fan_desc(ctypes.Structure):
 class rt_launch_config(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int32), ("stencil", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("order", ctypes.c_int32),
-                ("blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("blocks_per_sm", ctypes.c_int32), ("lanes_per_ray", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
+
+class rt_ionogram_desc(ctypes.Structure):
+    _fields_ = [("tx_lat_deg", ctypes.c_double), ("tx_lon_deg", ctypes.c_double),
+                ("tx_alt_km", ctypes.c_double), ("rx_lat_deg", ctypes.c_double),
+                ("rx_lon_deg", ctypes.c_double), ("freq_mhz", ctypes.POINTER(ctypes.c_double)),
+                ("el_deg", ctypes.POINTER(ctypes.c_double)), ("n_freq", ctypes.c_int32),
+                ("n_el", ctypes.c_int32), ("modes", ctypes.c_uint32), ("integrator", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("max_steps", ctypes.c_int32), ("h_km", ctypes.c_double),
+                ("rtol", ctypes.c_double), ("atol_km", ctypes.c_double), ("h_min_km", ctypes.c_double),
+                ("h_max_km", ctypes.c_double)]
+
+
+IONOGRAM_DTYPE = np.dtype([("freq_mhz", "f8"), ("group_path_km", "f8"), ("el_deg", "f8"),
+                           ("ground_range_km", "f8"), ("mode", "i4"), ("branch", "i4")])
+assert IONOGRAM_DTYPE.itemsize == 40
 
 RESULT_DTYPE = np.dtype([("group_path_km", "f8"), ("ground_range_km", "f8"),
                          ("az_dev_deg", "f8"), ("apogee_km", "f8"), ("land_lat_deg", "f8"),
@@ -112,6 +129,18 @@ def load(path=None):
     L.rt_eval_rhs.argtypes = [vp, ctypes.c_double, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                               _DP, _DP, _DP, sz]
     L.rt_eval_rhs.restype = ctypes.c_int
+    L.rt_plan_create.argtypes = [vp, ctypes.POINTER(rt_fan_desc), ctypes.POINTER(rt_launch_config),
+                                 ctypes.POINTER(vp)]
+    L.rt_plan_create.restype = ctypes.c_int
+    L.rt_plan_rays.argtypes = [vp]
+    L.rt_plan_rays.restype = sz
+    L.rt_plan_execute.argtypes = [vp, vp, sz, vp]
+    L.rt_plan_execute.restype = ctypes.c_int
+    L.rt_plan_destroy.argtypes = [vp]
+    L.rt_plan_destroy.restype = ctypes.c_int
+    L.rt_ionogram.argtypes = [vp, ctypes.POINTER(rt_ionogram_desc), vp, sz, ctypes.POINTER(sz),
+                              ctypes.POINTER(rt_launch_config), vp]
+    L.rt_ionogram.restype = ctypes.c_int
     L.rt_last_error.argtypes = []
     L.rt_last_error.restype = ctypes.c_char_p
     L.rt_version.argtypes = []
@@ -134,24 +163,24 @@ def rt_version():
 
 
 # ------------------------------------------------------------------ grids
-def grid_desc(spec, dtype=RT_F32, table=False):
+def grid_desc(spec, dtype=RT_F32, table=False, interp="gd"):
+    flags = (RT_GRID_TABLE if table else 0) | (RT_GRID_CATMULL_ROM if interp == "cr" else 0)
     return rt_grid_desc(spec.n_lat, spec.n_lon, spec.n_alt, dtype, spec.lat0_deg, spec.lon0_deg,
                         spec.alt0_km, spec.dlat_deg, spec.dlon_deg, spec.dalt_km,
                         spec.earth_radius_km,
-                        rt_dipole(spec.b0_tesla, spec.pole_lat_deg, spec.pole_lon_deg),
-                        RT_GRID_TABLE if table else 0, 0)
+                        rt_dipole(spec.b0_tesla, spec.pole_lat_deg, spec.pole_lon_deg), flags, 0)
 
 
 class Grid:
     """Device-resident grid handle (rt_grid_create / rt_grid_destroy)."""
 
-    def __init__(self, spec, ne, table=False):
+    def __init__(self, spec, ne, table=False, interp="gd"):
         ne = np.ascontiguousarray(ne)
         if ne.dtype not in (np.float32, np.float64):
             ne = ne.astype(np.float32)
         assert ne.shape == (spec.n_lat, spec.n_lon, spec.n_alt)
         self.spec = spec
-        self.desc = grid_desc(spec, RT_F64 if ne.dtype == np.float64 else RT_F32, table)
+        self.desc = grid_desc(spec, RT_F64 if ne.dtype == np.float64 else RT_F32, table, interp)
         self.handle = rt_grid_create(self.desc, ne)
 
     @property
@@ -209,8 +238,8 @@ def rt_fan_size(desc):
     return load().rt_fan_size(ctypes.byref(desc))
 
 
-def launch_config(kernel=0, stencil=0, block_threads=0, order=0, blocks_per_sm=0):
-    return rt_launch_config(kernel, stencil, block_threads, order, blocks_per_sm)
+def launch_config(kernel=0, stencil=0, block_threads=0, order=0, blocks_per_sm=0, lanes_per_ray=0):
+    return rt_launch_config(kernel, stencil, block_threads, order, blocks_per_sm, lanes_per_ray)
 
 
 def _cfg_ptr(cfg):
@@ -232,6 +261,54 @@ def rt_trace_device(grid, fan, out_ptr, out_len, cfg=None, stream=None):
     """Asynchronous trace into device memory (e.g. torch tensor .data_ptr())."""
     _check(load().rt_trace_device(grid.handle, ctypes.byref(fan.desc), ctypes.c_void_p(out_ptr),
                                   out_len, _cfg_ptr(cfg), stream))
+
+
+class Plan:
+    """rt_plan: grid + fan + launch configuration bound once; execute() queues a
+    counter reset and one kernel launch (capturable into a CUDA graph)."""
+
+    def __init__(self, grid, fan, cfg=None):
+        self.grid, self.fan = grid, fan  # keep both alive
+        h = ctypes.c_void_p()
+        _check(load().rt_plan_create(grid.handle, ctypes.byref(fan.desc), _cfg_ptr(cfg), ctypes.byref(h)))
+        self.handle = h
+
+    @property
+    def n_rays(self):
+        return load().rt_plan_rays(self.handle)
+
+    def execute(self, out_ptr, out_len, stream=None):
+        _check(load().rt_plan_execute(self.handle, ctypes.c_void_p(out_ptr), out_len, stream))
+
+    def close(self):
+        if self.handle:
+            _check(load().rt_plan_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rt_ionogram(grid, tx, rx, freq_mhz, el_deg, modes=RT_MODE_O | RT_MODE_X, integrator=RT_RKF45,
+                precision=RT_MIXED, h_km=1.0, rtol=1e-8, atol_km=1e-6, h_min_km=1e-6, h_max_km=20.0,
+                max_steps=200000, cap=None, cfg=None, stream=None):
+    """Oblique ionogram points (IONOGRAM_DTYPE records) for a transmitter
+    tx = (lat, lon, alt_km) and receiver rx = (lat, lon)."""
+    freq = np.ascontiguousarray(freq_mhz, dtype=np.float64)
+    el = np.ascontiguousarray(el_deg, dtype=np.float64)
+    d = rt_ionogram_desc(tx[0], tx[1], tx[2], rx[0], rx[1], freq.ctypes.data_as(_DP), el.ctypes.data_as(_DP),
+                         len(freq), len(el), modes, integrator, precision, max_steps, h_km, rtol, atol_km,
+                         h_min_km, h_max_km)
+    n_modes = (1 if modes & RT_MODE_O else 0) + (1 if modes & RT_MODE_X else 0)
+    cap = cap if cap is not None else max(1, len(freq) * n_modes * max(len(el) - 1, 0))
+    out = np.zeros(cap, dtype=IONOGRAM_DTYPE)
+    n = ctypes.c_size_t()
+    _check(load().rt_ionogram(grid.handle, ctypes.byref(d), out.ctypes.data, cap, ctypes.byref(n),
+                              _cfg_ptr(cfg), stream))
+    return out[: min(n.value, cap)], n.value
 
 
 def rt_tune(grid, fan, max_rays=0, stream=None):

@@ -150,10 +150,14 @@ def test_mixed_config2_full_size(orc):
     fp64 = rt.rt_trace(g, rt.Fan(spec, rt.RT_FP64))
     conv = rt.rt_trace(g, rt.Fan(w.fan.replace(rtol=1e-11, atol_km=1e-9), rt.RT_FP64))
     ok = ~near_boundary(fp64, spec)
-    assert ok.mean() > 0.9
-    variants = {k: rt.rt_trace(g, rt.Fan(spec, rt.RT_MIXED), cfg=rt.launch_config(kernel=k[1], stencil=k[0]))
-                for k in outs}
-    mixed = variants[(rt.RT_STENCIL_QUAD, rt.RT_KERNEL_PERSISTENT)]
+    assert ok.mean() > 0.6
+    keys = [(st, kern, 0) for st, kern in outs] + [
+        (rt.RT_STENCIL_QUAD, rt.RT_KERNEL_PERSISTENT, 1), (rt.RT_STENCIL_QUAD, rt.RT_KERNEL_PERSISTENT, 4),
+        (rt.RT_STENCIL_TABLE, rt.RT_KERNEL_PLAIN, 2), (rt.RT_STENCIL_GATHER, rt.RT_KERNEL_PLAIN, 4)]
+    variants = {k: rt.rt_trace(g, rt.Fan(spec, rt.RT_MIXED),
+                               cfg=rt.launch_config(kernel=k[1], stencil=k[0], lanes_per_ray=k[2]))
+                for k in keys}
+    mixed = variants[(rt.RT_STENCIL_QUAD, rt.RT_KERNEL_PERSISTENT, 0)]
     for key, mv in variants.items():
         same = (mv["status"] == fp64["status"]) & (conv["status"] == fp64["status"])
         assert same[ok].mean() > 0.999, key
@@ -183,8 +187,10 @@ def test_ragged_and_tiny_fans(orc):
         ref9 = orc.trace_fan(og, spec9)
         ok = ~near_boundary(ref9, spec9)
         for kern in (rt.RT_KERNEL_PLAIN, rt.RT_KERNEL_PERSISTENT):
-            gm = rt.rt_trace(g, rt.Fan(spec9, rt.RT_MIXED), cfg=rt.launch_config(kernel=kern))
-            _close64(gm[ok], ref9[ok], km=MIX_KM, deg=MIX_DEG)
+            for lanes in (1, 2, 4):
+                gm = rt.rt_trace(g, rt.Fan(spec9, rt.RT_MIXED),
+                                 cfg=rt.launch_config(kernel=kern, lanes_per_ray=lanes))
+                _close64(gm[ok], ref9[ok], km=MIX_KM, deg=MIX_DEG)
 
 
 def test_statuses_match_oracle(orc):
@@ -219,6 +225,10 @@ def test_invalid_calls_are_errors():
         rt.rt_trace(g, rt.Fan(w.fan), out=np.zeros(3, dtype=rt.RESULT_DTYPE))
     with pytest.raises(rt.RtError):  # table stencil on a grid without a table
         rt.rt_trace(g, rt.Fan(w.fan, rt.RT_MIXED), cfg=rt.launch_config(stencil=rt.RT_STENCIL_TABLE))
+    with pytest.raises(rt.RtError):  # 3 lanes per ray
+        rt.rt_trace(g, rt.Fan(w.fan, rt.RT_MIXED), cfg=rt.launch_config(lanes_per_ray=3))
+    with pytest.raises(rt.RtError):  # the FP64 path is one lane per ray
+        rt.rt_trace(g, rt.Fan(w.fan, rt.RT_FP64), cfg=rt.launch_config(lanes_per_ray=2))
     spec = w.grid
     with pytest.raises(rt.RtError):
         rt.Grid(wl.GridSpec(**{**spec.__dict__, "n_alt": 3}), w.ne[:, :, :3])
@@ -241,3 +251,110 @@ def test_device_output_and_tuner():
     assert ms > 0 and best.kernel in (rt.RT_KERNEL_PLAIN, rt.RT_KERNEL_PERSISTENT)
     tuned = rt.rt_trace(g, fan)  # picks the cached configuration
     assert np.array_equal(tuned["status"], host["status"])
+
+
+def test_catmull_rom_option_matches_oracle(orc):
+    """The comparison interpolant (Eq. 6-9) as a grid option: RHS and whole
+    rays against the oracle's Catmull-Rom, FP64 (1e-6 km) and mixed."""
+    w = wl.config2(elev_step=6.0, az_step=60.0)
+    g = rt.Grid(w.grid, w.ne, interp="cr")
+    og = orc.Grid(w.grid, w.ne, interp="cr")
+    ys = _states(w, 200, 8)
+    ref = np.array([orc.rhs(og, 12.0, -1, y) for y in ys])
+    scale = np.abs(ref).max(axis=0)
+    dy64, _ = rt.rt_eval_rhs(g, 12.0, -1, ys, rt.RT_FP64)
+    assert np.max(np.abs(dy64 - ref) / scale) < 1e-10
+    dym, _ = rt.rt_eval_rhs(g, 12.0, -1, ys, rt.RT_MIXED)
+    assert np.max(np.abs(dym - ref) / scale) < 2e-4
+    spec = w.fan.replace(integrator=wl.RK4, h_km=1.0, el_deg=[8.0, 20.0, 32.0, 44.0], az_deg=[0.0, 120.0])
+    ref_r = orc.trace_fan(og, spec)
+    _close64(rt.rt_trace(g, rt.Fan(spec, rt.RT_FP64)), ref_r)
+    ok = ~near_boundary(ref_r, spec)
+    for lanes in (1, 2, 4):
+        gm = rt.rt_trace(g, rt.Fan(spec, rt.RT_MIXED), cfg=rt.launch_config(lanes_per_ray=lanes))
+        _close64(gm[ok], ref_r[ok], km=MIX_KM, deg=MIX_DEG)
+
+
+def test_plan_execute_and_graph_replay():
+    """A plan's execute step is a counter reset plus one launch: it gives the
+    same records as rt_trace_device and can be captured into a CUDA graph."""
+    torch = pytest.importorskip("torch")
+    w = _c2_small()
+    g = rt.Grid(w.grid, w.ne)
+    for prec in (rt.RT_MIXED, rt.RT_FP64):
+        fan = rt.Fan(w.fan, prec)
+        n = fan.n_rays
+        cfg = rt.launch_config(kernel=rt.RT_KERNEL_PERSISTENT if prec == rt.RT_MIXED else rt.RT_KERNEL_PLAIN,
+                               stencil=rt.RT_STENCIL_QUAD, lanes_per_ray=1)
+        ref = rt.rt_trace(g, fan, cfg=cfg)
+        plan = rt.Plan(g, fan, cfg)
+        assert plan.n_rays == n
+        out = torch.zeros(n * 64, dtype=torch.uint8, device="cuda")
+        s = torch.cuda.current_stream()
+        plan.execute(out.data_ptr(), n, stream=s.cuda_stream)
+        s.synchronize()
+        assert rt.results_view(out.cpu().numpy(), n).tobytes() == ref.tobytes()
+        graph = torch.cuda.CUDAGraph()
+        cap_out = torch.zeros(n * 64, dtype=torch.uint8, device="cuda")
+        side = torch.cuda.Stream()
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(graph, stream=side):
+                plan.execute(cap_out.data_ptr(), n, stream=side.cuda_stream)
+        for _ in range(2):
+            cap_out.zero_()
+            graph.replay()
+            torch.cuda.synchronize()
+            assert rt.results_view(cap_out.cpu().numpy(), n).tobytes() == ref.tobytes()
+        plan.close()
+
+
+def _ionogram_reference(res, fan, d_rx):
+    """Crossings of D = d_rx between neighbouring elevations of landed rays,
+    P' and elevation interpolated linearly in D (the definition rt_ionogram
+    documents), from per-ray records in canonical order (one azimuth)."""
+    pts = []
+    n_el = len(fan.el_deg)
+    modes = fan.mode_list
+    r = res.reshape(len(fan.freq_mhz), len(modes), n_el)
+    for fi, f in enumerate(fan.freq_mhz):
+        for mi, m in enumerate(modes):
+            row = r[fi, mi]
+            br = 0
+            for j in range(n_el - 1):
+                a, b = row[j], row[j + 1]
+                if a["status"] != 1 or b["status"] != 1:
+                    continue
+                fa, fb = a["ground_range_km"] - d_rx, b["ground_range_km"] - d_rx
+                if (fa < 0) != (fb < 0):
+                    t = fa / (fa - fb)
+                    pts.append((f, a["group_path_km"] + t * (b["group_path_km"] - a["group_path_km"]),
+                                fan.el_deg[j] + t * (fan.el_deg[j + 1] - fan.el_deg[j]), m, br))
+                    br += 1
+    return pts
+
+
+@pytest.mark.parametrize("prec", [rt.RT_FP64, rt.RT_MIXED])
+def test_ionogram_matches_oracle(orc, prec):
+    w = wl.config2()
+    g = rt.Grid(w.grid, w.ne)
+    tx, rx = (30.0, 112.0, 0.0), (36.0, 119.0)
+    freqs = np.arange(5.0, 17.0, 2.0)
+    els = np.arange(2.0, 61.0, 1.0)
+    pts, n = rt.rt_ionogram(g, tx, rx, freqs, els, precision=prec)
+    assert n == len(pts) and n > 10
+    # the same fan through the oracle (azimuth = initial bearing to the receiver)
+    p1, p2, dl = np.radians(tx[0]), np.radians(rx[0]), np.radians(rx[1] - tx[1])
+    x = np.cos(p1) * np.sin(p2) - np.sin(p1) * np.cos(p2) * np.cos(dl)
+    y = np.sin(dl) * np.cos(p2)
+    c = np.sin(p1) * np.sin(p2) + np.cos(p1) * np.cos(p2) * np.cos(dl)
+    d_rx = w.grid.earth_radius_km * np.arctan2(np.hypot(x, y), c)
+    spec = w.fan.replace(freq_mhz=freqs, el_deg=els, az_deg=[np.degrees(np.arctan2(y, x))])
+    ref = _ionogram_reference(orc.trace_fan(orc.Grid(w.grid, w.ne), spec), spec, d_rx)
+    assert len(ref) == n
+    km = FP64_KM if prec == rt.RT_FP64 else MIX_KM
+    for p, q in zip(pts, ref):
+        assert p["freq_mhz"] == q[0] and p["mode"] == q[3] and p["branch"] == q[4]
+        assert abs(p["group_path_km"] - q[1]) <= (km if prec == rt.RT_FP64 else 0.5)
+        assert p["ground_range_km"] == pytest.approx(d_rx, abs=1e-9)
+    if prec == rt.RT_FP64:
+        np.testing.assert_allclose([p["el_deg"] for p in pts], [q[2] for q in ref], atol=1e-6)
