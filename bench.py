@@ -345,7 +345,8 @@ def run_ours(args):
             "config": {"workload": w.name, "rays": n, "precision": args.precision, "rtol": args.rtol,
                        "launch": None if cfg is None else {"kernel": cfg.kernel, "stencil": cfg.stencil,
                                                            "block_threads": cfg.block_threads,
-                                                           "order": cfg.order},
+                                                           "order": cfg.order,
+                                                           "lanes_per_ray": cfg.lanes_per_ray},
                        "l2": "flushed (512 MiB write) before every timed step",
                        "parallelism": "replicas" if world > 1 else "single"},
             "ray_steps_per_s": ray_steps * world / sec,
