@@ -219,6 +219,24 @@ rt_err rt_trace(const rt_grid *grid, const rt_fan_desc *fan, rt_ray_result *out_
 rt_err rt_trace_device(const rt_grid *grid, const rt_fan_desc *fan, rt_ray_result *out_dev,
                        size_t out_len, const rt_launch_config *cfg, void *stream);
 
+/* Same as rt_trace_device, for callers that cannot allocate device memory
+ * while they trace (an allocator that must not be re-entered, a fixed device
+ * memory budget, device memory owned by another runtime).  This call makes no
+ * cudaMalloc/cudaFree (or other allocating) call: its scratch -- the ray
+ * counter and the fan tables -- is a fixed array inside the library (16 bytes
+ * + 4096 doubles, about 32 KiB, held on every GPU that loads the library until
+ * the process exits).  The paper has no counterpart; it is an interface
+ * variant of rt_trace_device.  Limits and rules:
+ *   - n_freq + n_el + n_az must not exceed 4096 (RT_EINVAL otherwise).
+ *   - All calls share the scratch: work queued by one call must be finished
+ *     on the GPU before another call's work starts (calls that overlap on the
+ *     GPU, e.g. on two streams, race and give wrong results).
+ *   - The first call on a device looks up the scratch's device address; make
+ *     that first call before any stream capture on the device.
+ * Results, errors and stream semantics are those of rt_trace_device. */
+rt_err rt_trace_device_noalloc(const rt_grid *grid, const rt_fan_desc *fan, rt_ray_result *out_dev,
+                               size_t out_len, const rt_launch_config *cfg, void *stream);
+
 /* Autotuner: times the candidate launch configurations for this grid and fan
  * shape on `stream` (each candidate on a seeded subsample of at most
  * max_rays rays; 0 = 4096) and returns the fastest in *best and its time in

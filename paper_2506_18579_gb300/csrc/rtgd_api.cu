@@ -730,6 +730,42 @@ rt_err rt_ionogram(const rt_grid *grid, const rt_ionogram_desc *d, rt_ionogram_p
     return RT_OK;
 }
 
+rt_err rt_trace_device_noalloc(const rt_grid *grid, const rt_fan_desc *fan, rt_ray_result *out_dev,
+                               size_t out_len, const rt_launch_config *cfg, void *stream) {
+    rt_err r = validate_fan(fan);
+    if (r != RT_OK) return r;
+    if (!grid) return fail(RT_EINVAL, "grid is NULL");
+    if (!out_dev) return fail(RT_EINVAL, "output pointer is NULL");
+    int dev = 0;
+    if ((r = ensure_device(&dev)) != RT_OK) return r;
+    if (dev != grid->device) return fail(RT_EINVAL, "grid lives on device %d, current device is %d", grid->device, dev);
+    const size_t n = fan_rays(fan);
+    if (out_len < n) return fail(RT_EINVAL, "out_len %zu < %zu rays", out_len, n);
+    if (n >= ((size_t)1 << 31)) return fail(RT_EINVAL, "fan too large (at most 2^31 - 1 rays)");
+    const size_t n_tab = (size_t)fan->n_freq + fan->n_el + fan->n_az;
+    if (n_tab > (size_t)kNoallocMaxTable)
+        return fail(RT_EINVAL, "rt_trace_device_noalloc: n_freq + n_el + n_az = %zu exceeds the fixed scratch of %d entries",
+                    n_tab, kNoallocMaxTable);
+    LaunchPlan lp;
+    int order = 0;
+    if ((r = make_plan(grid, fan, n, cfg, &lp, &order)) != RT_OK) return r;
+    void *scratch = nullptr;
+    size_t cap = 0;
+    CUDA_TRY(noalloc_scratch(dev, &scratch, &cap));
+    if (16 + n_tab * sizeof(double) > cap) return fail(RT_EINVAL, "fan tables exceed the fixed scratch");
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned long long *counter = (unsigned long long *)scratch;
+    double *tab = (double *)((char *)scratch + 16);
+    CUDA_TRY(cudaMemsetAsync(counter, 0, 16, st));  // the array keeps the last call's contents
+    CUDA_TRY(cudaMemcpyAsync(tab, fan->freq_mhz, fan->n_freq * sizeof(double), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(tab + fan->n_freq, fan->el_deg, fan->n_el * sizeof(double), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(tab + fan->n_freq + fan->n_el, fan->az_deg, fan->n_az * sizeof(double),
+                             cudaMemcpyHostToDevice, st));
+    const FanDev f = fill_fandev(grid, fan, n, order, tab);
+    CUDA_TRY(launch_trace(grid->g, f, out_dev, counter, lp, st));
+    return RT_OK;
+}
+
 rt_err rt_eval_rhs(const rt_grid *grid, double freq_mhz, int32_t mode, int32_t precision, int32_t stencil,
                    const double *y_host, double *dy_host, double *mu2_host, size_t n) {
     if (!grid || !y_host || !dy_host || !mu2_host) return fail(RT_EINVAL, "NULL argument");

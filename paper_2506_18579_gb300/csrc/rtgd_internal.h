@@ -46,6 +46,11 @@ cudaError_t launch_ionogram(const rt_ray_result *res, const double *freq, const 
                             int mode0, int n_el, double d_rx, rt_ionogram_point *out, unsigned long long cap,
                             unsigned long long *count, cudaStream_t st);
 
+// Scratch of rt_trace_device_noalloc (rtgd_noalloc.cu): ray counter + at
+// most kNoallocMaxTable fan-table entries.
+constexpr int kNoallocMaxTable = 4096;
+cudaError_t noalloc_scratch(int device, void **ptr, size_t *bytes);
+
 cudaError_t launch_eval_rhs(const GridDev &g, const double *ys, double *dys, double *mu2s, double freq_mhz, int mode,
                             int precision, int stencil, long long n, cudaStream_t st);
 

@@ -31,7 +31,7 @@ RT_ORDER_CANONICAL, RT_ORDER_ELEVATION_FASTEST = 0, 1
 EXPORTED = ["rt_grid_create", "rt_grid_destroy", "rt_grid_device_bytes", "rt_fan_size",
             "rt_trace", "rt_trace_device", "rt_tune", "rt_eval_rhs", "rt_last_error",
             "rt_version", "rt_plan_create", "rt_plan_rays", "rt_plan_execute", "rt_plan_destroy",
-            "rt_ionogram"]
+            "rt_ionogram", "rt_trace_device_noalloc"]
 
 
 class RtError(RuntimeError):
@@ -123,6 +123,9 @@ def load(path=None):
     L.rt_trace_device.argtypes = [vp, ctypes.POINTER(rt_fan_desc), vp, sz,
                                   ctypes.POINTER(rt_launch_config), vp]
     L.rt_trace_device.restype = ctypes.c_int
+    L.rt_trace_device_noalloc.argtypes = [vp, ctypes.POINTER(rt_fan_desc), vp, sz,
+                                          ctypes.POINTER(rt_launch_config), vp]
+    L.rt_trace_device_noalloc.restype = ctypes.c_int
     L.rt_tune.argtypes = [vp, ctypes.POINTER(rt_fan_desc), sz, vp, ctypes.POINTER(rt_launch_config),
                           ctypes.POINTER(ctypes.c_float)]
     L.rt_tune.restype = ctypes.c_int
@@ -309,6 +312,12 @@ def rt_ionogram(grid, tx, rx, freq_mhz, el_deg, modes=RT_MODE_O | RT_MODE_X, int
     _check(load().rt_ionogram(grid.handle, ctypes.byref(d), out.ctypes.data, cap, ctypes.byref(n),
                               _cfg_ptr(cfg), stream))
     return out[: min(n.value, cap)], n.value
+
+
+def rt_trace_device_noalloc(grid, fan, out_ptr, out_len, cfg=None, stream=None):
+    """rt_trace_device without any device allocation (fixed in-library scratch)."""
+    _check(load().rt_trace_device_noalloc(grid.handle, ctypes.byref(fan.desc), ctypes.c_void_p(out_ptr),
+                                          out_len, _cfg_ptr(cfg), stream))
 
 
 def rt_tune(grid, fan, max_rays=0, stream=None):
