@@ -295,6 +295,49 @@ typedef struct rt_ionogram_point {
 rt_err rt_ionogram(const rt_grid *grid, const rt_ionogram_desc *desc, rt_ionogram_point *out_host, size_t cap,
                    size_t *n_points, const rt_launch_config *cfg, void *stream);
 
+/* ---------------------------------------------------------------- serving */
+/* A request server for fans of uneven size against resident grids
+ * (continuous batching).  Submitted requests wait in a FIFO; a dispatcher
+ * thread admits them as soon as one of max_inflight stream slots is free and
+ * cudaMemGetInfo reports at least mem_reserve_bytes of device memory free
+ * after the request's own needs (results + fan tables), so requests that
+ * arrive while others run are traced concurrently with them on the GPU.  A
+ * completion thread copies each result to the caller's host buffer (through
+ * pinned staging) and wakes rt_server_wait.  Every request uses the launch
+ * configuration given at creation, so its records equal those of rt_trace
+ * with that configuration whatever else is in flight.  The paper has no
+ * counterpart (it traces one scan at a time on a CPU). */
+typedef struct rt_server rt_server;
+
+typedef struct rt_server_config {
+    int32_t max_inflight;        /* stream slots, 1..64 (0 = 8) */
+    int32_t reserved;            /* must be 0 */
+    size_t mem_reserve_bytes;    /* device memory kept free by admission */
+    rt_launch_config launch;     /* kernel choice for every request (zero = library defaults) */
+} rt_server_config;
+
+typedef struct rt_request_stats {
+    double queue_s;              /* submit -> admitted */
+    double run_s;                /* admitted -> result in the caller's buffer */
+    double total_s;              /* submit -> result in the caller's buffer */
+    int64_t n_rays;
+    int32_t status;              /* rt_err of the request */
+    int32_t reserved;
+} rt_request_stats;
+
+/* Creates a server on the current device (threads start immediately). */
+rt_err rt_server_create(const rt_server_config *cfg, rt_server **out);
+/* Queues a request; the fan arrays are copied, out_host (rt_fan_size(fan)
+ * records) must stay valid until rt_server_wait returns for the ticket. */
+rt_err rt_server_submit(rt_server *srv, const rt_grid *grid, const rt_fan_desc *fan, rt_ray_result *out_host,
+                        size_t out_len, uint64_t *ticket);
+/* Waits for a request (timeout_s <= 0: no limit); RT_ETIMEOUT if it has not
+ * finished in time (the request stays queued or running).  A waited ticket
+ * is released.  stats may be NULL. */
+rt_err rt_server_wait(rt_server *srv, uint64_t ticket, double timeout_s, rt_request_stats *stats);
+/* Finishes every queued and running request, then stops the threads. */
+rt_err rt_server_destroy(rt_server *srv);
+
 /* Diagnostic: the right-hand side dy/dP' of the ray equations (Eq. 1a-1f)
  * at n given states, exactly as one stage of the tracer evaluates it.
  * y_host: n x 6 doubles (r km, theta rad colatitude, phi rad longitude,

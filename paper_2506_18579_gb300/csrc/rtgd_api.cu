@@ -335,6 +335,13 @@ rt_err queue_trace(const rt_grid *grid, const rt_fan_desc *fan, rt_ray_result *o
 
 }  // namespace
 
+rt_err rtgd_queue_trace(const rt_grid *grid, const rt_fan_desc *fan, rt_ray_result *out_dev, size_t out_len,
+                        const rt_launch_config *cfg, cudaStream_t st) {
+    return queue_trace(grid, fan, out_dev, out_len, cfg, st);
+}
+
+rt_err rtgd_set_error(rt_err code, const char *msg) { return fail(code, "%s", msg); }
+
 extern "C" {
 
 int32_t rt_version(void) { return RTGD_API_VERSION; }

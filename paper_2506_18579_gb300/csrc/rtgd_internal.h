@@ -42,6 +42,16 @@ cudaError_t upload_tableaus();
 cudaError_t launch_trace(const GridDev &g, const FanDev &f, rt_ray_result *out, unsigned long long *counter,
                          const LaunchPlan &lp, cudaStream_t st);
 cudaError_t persistent_occupancy(int stencil, int lanes, int threads, int *blocks_per_sm);
+}  // namespace rtgd
+
+// Entry points shared between the translation units of the host library
+// (defined in rtgd_api.cu).
+rt_err rtgd_queue_trace(const rt_grid *grid, const rt_fan_desc *fan, rt_ray_result *out_dev, size_t out_len,
+                        const rt_launch_config *cfg, cudaStream_t st);
+rt_err rtgd_set_error(rt_err code, const char *msg);
+
+namespace rtgd {
+
 cudaError_t launch_ionogram(const rt_ray_result *res, const double *freq, const double *el, int n_freq, int n_modes,
                             int mode0, int n_el, double d_rx, rt_ionogram_point *out, unsigned long long cap,
                             unsigned long long *count, cudaStream_t st);

@@ -1,0 +1,281 @@
+// rtgd_server.cu -- request server with continuous batching (host code).
+//
+// Requests (a grid + a fan + the caller's host output buffer) enter a FIFO.
+// The dispatcher thread admits the head request when a stream slot is free
+// and the device keeps mem_reserve_bytes free after the request's own needs;
+// it queues the trace and the device-to-pinned copy of the records on the
+// slot's stream and records an event.  The completion thread polls the
+// in-flight events, copies finished records to the caller's buffer and wakes
+// the waiters.  Requests therefore join the GPU while others are running.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "rtgd.h"
+#include "rtgd_internal.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+    uint64_t ticket = 0;
+    const rt_grid *grid = nullptr;
+    rt_fan_desc fan;
+    std::vector<double> freq, el, az;  // copies of the fan arrays
+    rt_ray_result *out_host = nullptr;
+    size_t n = 0;
+    Clock::time_point t_submit, t_admit, t_done;
+    rt_err status = RT_OK;
+    std::string msg;                   // rt_last_error text of a failed request
+    bool done = false;
+};
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t event = nullptr;
+    rt_ray_result *dev = nullptr;   // device records (cudaMallocAsync per request)
+    rt_ray_result *pinned = nullptr;
+    size_t pinned_cap = 0;
+    std::shared_ptr<Request> req;   // null when free
+};
+
+}  // namespace
+
+struct rt_server {
+    rt_server_config cfg;
+    int device = 0;
+    std::vector<Slot> slots;
+    std::deque<std::shared_ptr<Request>> queue;
+    std::map<uint64_t, std::shared_ptr<Request>> tickets;
+    std::mutex mu;
+    std::condition_variable cv_dispatch, cv_done;
+    std::thread dispatcher, completer;
+    uint64_t next_ticket = 1;
+    int inflight = 0;
+    bool stopping = false;
+};
+
+namespace {
+
+double seconds(Clock::time_point a, Clock::time_point b) { return std::chrono::duration<double>(b - a).count(); }
+
+void finish_locked(rt_server *s, Slot &slot, rt_err status) {
+    auto &r = *slot.req;
+    r.status = status;
+    if (status != RT_OK) r.msg = rt_last_error();  // the message is thread-local: keep it for the waiter
+    r.t_done = Clock::now();
+    r.done = true;
+    slot.req.reset();
+    --s->inflight;
+    s->cv_done.notify_all();
+    s->cv_dispatch.notify_all();
+}
+
+// Starts request r on slot sl (called by the dispatcher with the lock released).
+rt_err start(rt_server *s, Slot &sl, Request &r) {
+    cudaSetDevice(s->device);
+    r.fan.freq_mhz = r.freq.data();
+    r.fan.el_deg = r.el.data();
+    r.fan.az_deg = r.az.data();
+    if (sl.pinned_cap < r.n) {
+        // grow by powers of two: freeing pinned memory synchronises the device
+        size_t cap = 1024;
+        while (cap < r.n) cap *= 2;
+        if (sl.pinned) cudaFreeHost(sl.pinned);
+        sl.pinned = nullptr;
+        sl.pinned_cap = 0;
+        if (cudaMallocHost((void **)&sl.pinned, cap * sizeof(rt_ray_result)) != cudaSuccess)
+            return rtgd_set_error(RT_ENOMEM, "server: pinned staging allocation failed");
+        sl.pinned_cap = cap;
+    }
+    if (cudaMallocAsync((void **)&sl.dev, r.n * sizeof(rt_ray_result), sl.stream) != cudaSuccess)
+        return rtgd_set_error(RT_ENOMEM, "server: device allocation failed");
+    const rt_launch_config *lc = &s->cfg.launch;
+    rt_err e = rtgd_queue_trace(r.grid, &r.fan, sl.dev, r.n, lc, sl.stream);
+    if (e == RT_OK && cudaMemcpyAsync(sl.pinned, sl.dev, r.n * sizeof(rt_ray_result), cudaMemcpyDeviceToHost,
+                                      sl.stream) != cudaSuccess)
+        e = rtgd_set_error(RT_ECUDA, "server: result copy failed");
+    cudaFreeAsync(sl.dev, sl.stream);
+    sl.dev = nullptr;
+    if (e == RT_OK && cudaEventRecord(sl.event, sl.stream) != cudaSuccess)
+        e = rtgd_set_error(RT_ECUDA, "server: event record failed");
+    return e;
+}
+
+void dispatch_loop(rt_server *s) {
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    for (;;) {
+        s->cv_dispatch.wait(lk, [&] { return s->stopping || (!s->queue.empty() && s->inflight < (int)s->slots.size()); });
+        if (s->queue.empty() && s->stopping) return;
+        if (s->queue.empty() || s->inflight >= (int)s->slots.size()) continue;
+        // admission by device memory: the request's records + tables must fit above the reserve
+        size_t free_b = 0, total_b = 0;
+        auto req = s->queue.front();
+        const size_t need = req->n * sizeof(rt_ray_result) * 2 + 4096;
+        lk.unlock();
+        cudaMemGetInfo(&free_b, &total_b);
+        lk.lock();
+        if (free_b < need + s->cfg.mem_reserve_bytes && s->inflight > 0) {
+            // wait for a running request to release memory
+            s->cv_dispatch.wait_for(lk, std::chrono::milliseconds(2));
+            continue;
+        }
+        s->queue.pop_front();
+        int idx = -1;
+        for (size_t i = 0; i < s->slots.size(); ++i)
+            if (!s->slots[i].req) {
+                idx = (int)i;
+                break;
+            }
+        Slot &sl = s->slots[idx];
+        sl.req = req;
+        ++s->inflight;
+        req->t_admit = Clock::now();
+        lk.unlock();
+        const rt_err e = start(s, sl, *req);
+        lk.lock();
+        if (e != RT_OK) finish_locked(s, sl, e);
+    }
+}
+
+void complete_loop(rt_server *s) {
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    for (;;) {
+        if (s->stopping && s->inflight == 0 && s->queue.empty()) return;
+        bool any = false;
+        for (auto &sl : s->slots) {
+            if (!sl.req || sl.req->done) continue;
+            any = true;
+            const cudaError_t q = cudaEventQuery(sl.event);
+            if (q == cudaErrorNotReady) continue;
+            rt_err st = RT_OK;
+            if (q == cudaSuccess) std::memcpy(sl.req->out_host, sl.pinned, sl.req->n * sizeof(rt_ray_result));
+            else st = rtgd_set_error(RT_ECUDA, cudaGetErrorString(q));
+            finish_locked(s, sl, st);
+        }
+        lk.unlock();
+        std::this_thread::sleep_for(std::chrono::microseconds(any ? 50 : 500));
+        lk.lock();
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+rt_err rt_server_create(const rt_server_config *cfg, rt_server **out) {
+    if (!out) return rtgd_set_error(RT_EINVAL, "out is NULL");
+    *out = nullptr;
+    rt_server_config c;
+    std::memset(&c, 0, sizeof(c));
+    if (cfg) c = *cfg;
+    if (c.max_inflight == 0) c.max_inflight = 8;
+    if (c.max_inflight < 1 || c.max_inflight > 64) return rtgd_set_error(RT_EINVAL, "max_inflight must be in 1..64");
+    if (c.reserved != 0) return rtgd_set_error(RT_EINVAL, "reserved field must be 0");
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) return rtgd_set_error(RT_EUNSUPPORTED, "no CUDA device available");
+    auto *s = new rt_server();
+    s->cfg = c;
+    cudaGetDevice(&s->device);
+    s->slots.resize(c.max_inflight);
+    for (auto &sl : s->slots) {
+        if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&sl.event, cudaEventDisableTiming) != cudaSuccess) {
+            for (auto &t : s->slots) {
+                if (t.stream) cudaStreamDestroy(t.stream);
+                if (t.event) cudaEventDestroy(t.event);
+            }
+            delete s;
+            return rtgd_set_error(RT_ECUDA, "server: stream creation failed");
+        }
+    }
+    s->dispatcher = std::thread(dispatch_loop, s);
+    s->completer = std::thread(complete_loop, s);
+    *out = s;
+    return RT_OK;
+}
+
+rt_err rt_server_submit(rt_server *s, const rt_grid *grid, const rt_fan_desc *fan, rt_ray_result *out_host,
+                        size_t out_len, uint64_t *ticket) {
+    if (!s || !grid || !fan || !out_host || !ticket) return rtgd_set_error(RT_EINVAL, "NULL argument");
+    const size_t n = rt_fan_size(fan);
+    if (n == 0) return rtgd_set_error(RT_EINVAL, "empty or invalid fan");
+    if (out_len < n) return rtgd_set_error(RT_EINVAL, "out_len smaller than the fan");
+    if (!fan->freq_mhz || !fan->el_deg || !fan->az_deg) return rtgd_set_error(RT_EINVAL, "fan arrays must not be NULL");
+    auto r = std::make_shared<Request>();
+    r->grid = grid;
+    r->fan = *fan;
+    r->freq.assign(fan->freq_mhz, fan->freq_mhz + fan->n_freq);
+    r->el.assign(fan->el_deg, fan->el_deg + fan->n_el);
+    r->az.assign(fan->az_deg, fan->az_deg + fan->n_az);
+    r->out_host = out_host;
+    r->n = n;
+    r->t_submit = Clock::now();
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stopping) return rtgd_set_error(RT_EINVAL, "server is stopping");
+    r->ticket = s->next_ticket++;
+    s->tickets[r->ticket] = r;
+    s->queue.push_back(r);
+    *ticket = r->ticket;
+    s->cv_dispatch.notify_all();
+    return RT_OK;
+}
+
+rt_err rt_server_wait(rt_server *s, uint64_t ticket, double timeout_s, rt_request_stats *stats) {
+    if (!s) return rtgd_set_error(RT_EINVAL, "server is NULL");
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->tickets.find(ticket);
+    if (it == s->tickets.end()) return rtgd_set_error(RT_EINVAL, "unknown ticket");
+    auto r = it->second;
+    auto pred = [&] { return r->done; };
+    if (timeout_s > 0) {
+        if (!s->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), pred))
+            return rtgd_set_error(RT_ETIMEOUT, "request not finished in time");
+    } else {
+        s->cv_done.wait(lk, pred);
+    }
+    s->tickets.erase(it);
+    if (stats) {
+        stats->queue_s = seconds(r->t_submit, r->t_admit);
+        stats->run_s = seconds(r->t_admit, r->t_done);
+        stats->total_s = seconds(r->t_submit, r->t_done);
+        stats->n_rays = (int64_t)r->n;
+        stats->status = r->status;
+        stats->reserved = 0;
+    }
+    if (r->status != RT_OK) return rtgd_set_error(r->status, r->msg.c_str());
+    return r->status;
+}
+
+rt_err rt_server_destroy(rt_server *s) {
+    if (!s) return RT_OK;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stopping = true;
+        s->cv_dispatch.notify_all();
+    }
+    s->dispatcher.join();
+    s->completer.join();
+    for (auto &sl : s->slots) {
+        cudaStreamSynchronize(sl.stream);
+        cudaStreamDestroy(sl.stream);
+        cudaEventDestroy(sl.event);
+        if (sl.pinned) cudaFreeHost(sl.pinned);
+    }
+    delete s;
+    return RT_OK;
+}
+
+}  // extern "C"

@@ -31,7 +31,8 @@ RT_ORDER_CANONICAL, RT_ORDER_ELEVATION_FASTEST = 0, 1
 EXPORTED = ["rt_grid_create", "rt_grid_destroy", "rt_grid_device_bytes", "rt_fan_size",
             "rt_trace", "rt_trace_device", "rt_tune", "rt_eval_rhs", "rt_last_error",
             "rt_version", "rt_plan_create", "rt_plan_rays", "rt_plan_execute", "rt_plan_destroy",
-            "rt_ionogram", "rt_trace_device_noalloc"]
+            "rt_ionogram", "rt_trace_device_noalloc", "rt_server_create", "rt_server_submit",
+            "rt_server_wait", "rt_server_destroy"]
 
 
 class RtError(RuntimeError):
@@ -85,6 +86,16 @@ class rt_ionogram_desc(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("max_steps", ctypes.c_int32), ("h_km", ctypes.c_double),
                 ("rtol", ctypes.c_double), ("atol_km", ctypes.c_double), ("h_min_km", ctypes.c_double),
                 ("h_max_km", ctypes.c_double)]
+
+
+class rt_server_config(ctypes.Structure):
+    _fields_ = [("max_inflight", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("mem_reserve_bytes", ctypes.c_size_t), ("launch", rt_launch_config)]
+
+
+class rt_request_stats(ctypes.Structure):
+    _fields_ = [("queue_s", ctypes.c_double), ("run_s", ctypes.c_double), ("total_s", ctypes.c_double),
+                ("n_rays", ctypes.c_int64), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 IONOGRAM_DTYPE = np.dtype([("freq_mhz", "f8"), ("group_path_km", "f8"), ("el_deg", "f8"),
@@ -144,6 +155,14 @@ def load(path=None):
     L.rt_ionogram.argtypes = [vp, ctypes.POINTER(rt_ionogram_desc), vp, sz, ctypes.POINTER(sz),
                               ctypes.POINTER(rt_launch_config), vp]
     L.rt_ionogram.restype = ctypes.c_int
+    L.rt_server_create.argtypes = [ctypes.POINTER(rt_server_config), ctypes.POINTER(vp)]
+    L.rt_server_create.restype = ctypes.c_int
+    L.rt_server_submit.argtypes = [vp, vp, ctypes.POINTER(rt_fan_desc), vp, sz, ctypes.POINTER(ctypes.c_uint64)]
+    L.rt_server_submit.restype = ctypes.c_int
+    L.rt_server_wait.argtypes = [vp, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(rt_request_stats)]
+    L.rt_server_wait.restype = ctypes.c_int
+    L.rt_server_destroy.argtypes = [vp]
+    L.rt_server_destroy.restype = ctypes.c_int
     L.rt_last_error.argtypes = []
     L.rt_last_error.restype = ctypes.c_char_p
     L.rt_version.argtypes = []
@@ -318,6 +337,47 @@ def rt_trace_device_noalloc(grid, fan, out_ptr, out_len, cfg=None, stream=None):
     """rt_trace_device without any device allocation (fixed in-library scratch)."""
     _check(load().rt_trace_device_noalloc(grid.handle, ctypes.byref(fan.desc), ctypes.c_void_p(out_ptr),
                                           out_len, _cfg_ptr(cfg), stream))
+
+
+class Server:
+    """rt_server: continuous-batching request server on the current device."""
+
+    def __init__(self, max_inflight=8, mem_reserve_bytes=0, cfg=None):
+        c = rt_server_config(max_inflight, 0, mem_reserve_bytes, cfg if cfg is not None else rt_launch_config())
+        h = ctypes.c_void_p()
+        _check(load().rt_server_create(ctypes.byref(c), ctypes.byref(h)))
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, grid, fan, out=None):
+        """Queue a fan; returns (ticket, out) where out receives the records."""
+        n = fan.n_rays
+        out = np.zeros(n, dtype=RESULT_DTYPE) if out is None else out
+        t = ctypes.c_uint64()
+        _check(load().rt_server_submit(self.handle, grid.handle, ctypes.byref(fan.desc), out.ctypes.data, len(out),
+                                       ctypes.byref(t)))
+        self._keep[t.value] = (grid, fan, out)
+        return t.value, out
+
+    def wait(self, ticket, timeout_s=0.0):
+        st = rt_request_stats()
+        code = load().rt_server_wait(self.handle, ticket, timeout_s, ctypes.byref(st))
+        if code != RT_ETIMEOUT:
+            self._keep.pop(ticket, None)
+        _check(code)
+        return st
+
+    def close(self):
+        if self.handle:
+            _check(load().rt_server_destroy(self.handle))
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def rt_tune(grid, fan, max_rays=0, stream=None):

@@ -259,3 +259,52 @@ def sample_indices(n_total, n_sample, seed):
     rng = np.random.default_rng(seed)
     n_sample = min(n_sample, n_total)
     return np.sort(rng.choice(n_total, size=n_sample, replace=False))
+
+
+SERVING_MAX_RAYS = 100_000
+
+
+def serving_mean_rays(max_rays=SERVING_MAX_RAYS):
+    """Expected size of a log-uniform request size on [1, max_rays]."""
+    return (max_rays - 1.0) / np.log(max_rays)
+
+
+def serving_requests(n, seed, grid_specs, max_rays=SERVING_MAX_RAYS):
+    """Seeded stream of fan requests for the serving loop.
+
+    Each request picks one of the resident grids, a transmitter within 5 deg
+    of that grid's centre, one magnetoionic mode, and a target size drawn
+    log-uniformly from 1..max_rays rays.  Half are ionogram-synthesis shaped
+    (one azimuth, a list of 3-30 MHz frequencies x an elevation scan), half
+    OTHR coordinate-registration shaped (one or two frequencies x an elevation
+    x azimuth fan).  Integration as in the anisotropic fan case (RKF45,
+    rtol 1e-8), mixed precision.  Returns a list of (grid index, FanSpec).
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        gi = int(rng.integers(len(grid_specs)))
+        g = grid_specs[gi]
+        lat_c = g.lat0_deg + 0.5 * g.dlat_deg * (g.n_lat - 1)
+        lon_c = g.lon0_deg + 0.5 * g.dlon_deg * (g.n_lon - 1)
+        target = int(np.clip(np.round(np.exp(rng.uniform(0.0, np.log(max_rays)))), 1, max_rays))
+        if rng.random() < 0.5:  # ionogram synthesis: frequencies x elevations, one azimuth
+            n_freq = int(min(target, rng.integers(1, 65)))
+            n_az = 1
+        else:  # OTHR registration: one or two frequencies x elevation x azimuth
+            n_freq = int(min(target, rng.integers(1, 3)))
+            n_az = int(max(1, min(36, target // (8 * n_freq))))
+            n_az = int(rng.integers(1, n_az + 1))
+        n_el = max(1, int(np.ceil(target / (n_freq * n_az))))
+        el_lo = rng.uniform(1.0, 30.0)
+        el_hi = min(89.0, el_lo + rng.uniform(5.0, 60.0))
+        az0 = rng.uniform(0.0, 360.0)
+        az_span = rng.uniform(10.0, 120.0) if n_az > 1 else 0.0
+        fan = FanSpec(tx_lat_deg=lat_c + rng.uniform(-5.0, 5.0), tx_lon_deg=lon_c + rng.uniform(-5.0, 5.0),
+                      tx_alt_km=0.0, freq_mhz=np.sort(rng.uniform(3.0, 30.0, n_freq)),
+                      el_deg=np.linspace(el_lo, el_hi, n_el),
+                      az_deg=np.mod(az0 + np.linspace(0.0, az_span, n_az), 360.0),
+                      modes=MODE_O if rng.random() < 0.5 else MODE_X, integrator=RKF45, h_km=1.0, rtol=1e-8,
+                      atol_km=1e-6, h_min_km=1e-6, h_max_km=20.0, max_steps=200000, precision=MIXED)
+        out.append((gi, fan))
+    return out

@@ -358,3 +358,37 @@ def test_ionogram_matches_oracle(orc, prec):
         assert p["ground_range_km"] == pytest.approx(d_rx, abs=1e-9)
     if prec == rt.RT_FP64:
         np.testing.assert_allclose([p["el_deg"] for p in pts], [q[2] for q in ref], atol=1e-6)
+
+
+def test_config4_batched_fan_in_captured_graph(orc):
+    """The ionogram-synthesis batch at full size: 181x361x301 grid, 281
+    frequencies x 881 elevations x O/X = 495,122 rays of 50-5000 steps, run as
+    one plan captured in a CUDA graph (mixed) and by the FP64 kernel; sampled
+    rays against the oracle."""
+    torch = pytest.importorskip("torch")
+    w = wl.config4()
+    assert w.fan.n_rays == 495122
+    g = rt.Grid(w.grid, w.ne)
+    n = w.fan.n_rays
+    plan = rt.Plan(g, rt.Fan(w.fan, rt.RT_MIXED))
+    out = torch.zeros(n * 64, dtype=torch.uint8, device="cuda")
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(graph, stream=side):
+            plan.execute(out.data_ptr(), n, stream=side.cuda_stream)
+    graph.replay()
+    torch.cuda.synchronize()
+    mixed = rt.results_view(out.cpu().numpy(), n).copy()
+    assert np.all(mixed["status"] != rt.RT_RAY_NOT_RUN)
+    st = np.bincount(mixed["status"], minlength=8)
+    assert st[rt.RT_RAY_LANDED] > 0.1 * n and st[rt.RT_RAY_ESCAPED] > 0.1 * n  # mixed outcomes
+    steps = mixed["n_steps"]
+    assert steps.min() < 100 and steps.max() > 1000  # uneven ray lengths
+    fp64 = rt.rt_trace(g, rt.Fan(w.fan, rt.RT_FP64))
+    idx = wl.sample_indices(n, 24, seed=44)
+    ref = orc.trace_fan(orc.Grid(w.grid, w.ne), w.fan, indices=idx)
+    _close64(fp64[idx], ref)
+    ok = ~near_boundary(fp64, w.fan)[idx] & (mixed["status"][idx] == ref["status"])
+    _close64(mixed[idx][ok], ref[ok], km=MIX_KM, deg=MIX_DEG)
+    plan.close()

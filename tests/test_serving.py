@@ -1,0 +1,103 @@
+"""The request server (continuous batching over resident grids).
+
+Requests of uneven size against four resident grids are submitted together
+and staggered; each result must equal the same request traced alone with the
+same launch configuration (identical per-ray arithmetic, so byte-identical
+records), and the latency statistics must be consistent.
+"""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2506_18579_gb300 import build as rtbuild
+from paper_2506_18579_gb300 import rtgd as rt
+from paper_2506_18579_gb300 import workloads as wl
+
+
+def test_server_needs_a_gpu_or_fails_loudly():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    rtbuild.build()
+    with pytest.raises(rt.RtError) as ei:
+        rt.Server()
+    assert ei.value.code == rt.RT_EUNSUPPORTED
+
+
+def _requests(seed):
+    rng = np.random.default_rng(seed)
+    grids = wl.serving_grids()[:3]  # the largest (181x361x301) is exercised by the C4 test
+    reqs = []
+    for i in range(14):
+        gi = int(rng.integers(len(grids)))
+        n_el = int(np.exp(rng.uniform(np.log(1), np.log(120))))
+        n_az = int(rng.integers(1, 8))
+        f0 = rng.uniform(3.0, 20.0)
+        spec = wl.FanSpec(tx_lat_deg=30.0 + rng.uniform(-3, 3), tx_lon_deg=112.0 + rng.uniform(-3, 3), tx_alt_km=0.0,
+                          freq_mhz=[f0, f0 + 2.0], el_deg=np.linspace(3.0, 60.0, n_el),
+                          az_deg=np.linspace(0.0, 300.0, n_az), modes=wl.MODE_O if i % 2 else wl.MODE_X,
+                          integrator=wl.RKF45, rtol=1e-8, precision=wl.MIXED)
+        reqs.append((gi, spec))
+    return grids, reqs
+
+
+@pytest.mark.gpu
+def test_results_in_the_mix_equal_solo_results():
+    rtbuild.build()
+    grids, reqs = _requests(5)
+    handles = [rt.Grid(g, ne) for g, ne in grids]
+    cfg = rt.launch_config(kernel=rt.RT_KERNEL_PERSISTENT, stencil=rt.RT_STENCIL_QUAD, lanes_per_ray=1)
+    solo = [rt.rt_trace(handles[gi], rt.Fan(spec), cfg=cfg) for gi, spec in reqs]
+    srv = rt.Server(max_inflight=4, cfg=cfg)
+    fans = [rt.Fan(spec) for _, spec in reqs]
+    tickets = []
+    for k, (gi, spec) in enumerate(reqs):  # half at once, half staggered while others run
+        tickets.append(srv.submit(handles[gi], fans[k]))
+        if k >= len(reqs) // 2:
+            time.sleep(0.002)
+    for k, (t, out) in enumerate(tickets):
+        st = srv.wait(t, timeout_s=300.0)
+        assert st.status == rt.RT_OK and st.n_rays == fans[k].n_rays
+        assert st.total_s >= st.run_s > 0 and st.queue_s >= 0
+        assert out.tobytes() == solo[k].tobytes(), k
+    srv.close()
+
+
+@pytest.mark.gpu
+def test_unknown_ticket_and_invalid_fan():
+    rtbuild.build()
+    w = wl.config1()
+    g = rt.Grid(w.grid, w.ne)
+    srv = rt.Server(max_inflight=2)
+    with pytest.raises(rt.RtError):
+        srv.wait(12345)
+    bad = rt.Fan(w.fan)
+    bad.desc.n_el = 0
+    with pytest.raises(rt.RtError):
+        srv.submit(g, bad, out=np.zeros(16, dtype=rt.RESULT_DTYPE))
+    t, out = srv.submit(g, rt.Fan(w.fan))
+    assert srv.wait(t).status == rt.RT_OK
+    assert np.all(out["status"] == rt.RT_RAY_LANDED)
+    srv.close()
+
+
+def test_request_stream_is_seeded_and_shaped():
+    specs = [g for g, _ in (
+        (wl.centred_grid(*wl.TX[:2], 21, 21, 61, 2.0, 2.0, 10.0), None),
+        (wl.centred_grid(*wl.TX[:2], 181, 361, 301, 0.5, 0.5, 2.0), None))]
+    a = wl.serving_requests(400, 9, specs)
+    b = wl.serving_requests(400, 9, specs)
+    assert [(g, f.n_rays, f.tx_lat_deg) for g, f in a] == [(g, f.n_rays, f.tx_lat_deg) for g, f in b]
+    n = np.array([f.n_rays for _, f in a])
+    assert n.min() >= 1 and n.max() <= wl.SERVING_MAX_RAYS
+    assert np.median(n) < 2000 < n.mean()  # log-uniform: heavy tail of large requests
+    assert {g for g, _ in a} == {0, 1}
+    for g, f in a:
+        assert f.mode_list in ([1], [-1]) and f.integrator == wl.RKF45 and f.precision == wl.MIXED
+        assert 3.0 <= min(f.freq_mhz) and max(f.freq_mhz) <= 30.0
+        assert 1.0 <= f.el_deg[0] <= f.el_deg[-1] <= 89.0
+        gs = specs[g]
+        assert abs(f.tx_lat_deg - (gs.lat0_deg + 0.5 * gs.dlat_deg * (gs.n_lat - 1))) <= 5.0
+    shapes = {(len(f.az_deg) == 1) for _, f in a}
+    assert shapes == {True, False}  # both ionogram-synthesis and OTHR-registration requests
