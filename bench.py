@@ -16,6 +16,7 @@ bounded sample of the same fan per step); it is the baseline arm.
 from __future__ import annotations
 
 import argparse
+import faulthandler
 import json
 import os
 import statistics
@@ -525,6 +526,7 @@ def run_serving(rt, wl, seconds, seed=9):
 
 
 def main():
+    faulthandler.enable()  # a native crash prints every thread's Python stack
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -47,6 +47,7 @@ struct Slot {
     rt_ray_result *pinned = nullptr;
     size_t pinned_cap = 0;
     std::shared_ptr<Request> req;   // null when free
+    bool armed = false;             // the request's work and event are queued: the completer may poll
 };
 
 }  // namespace
@@ -76,6 +77,7 @@ void finish_locked(rt_server *s, Slot &slot, rt_err status) {
     r.t_done = Clock::now();
     r.done = true;
     slot.req.reset();
+    slot.armed = false;
     --s->inflight;
     s->cv_done.notify_all();
     s->cv_dispatch.notify_all();
@@ -116,9 +118,10 @@ void dispatch_loop(rt_server *s) {
     cudaSetDevice(s->device);
     std::unique_lock<std::mutex> lk(s->mu);
     for (;;) {
-        s->cv_dispatch.wait(lk, [&] { return s->stopping || (!s->queue.empty() && s->inflight < (int)s->slots.size()); });
-        if (s->queue.empty() && s->stopping) return;
-        if (s->queue.empty() || s->inflight >= (int)s->slots.size()) continue;
+        s->cv_dispatch.wait(lk, [&] {
+            return (s->stopping && s->queue.empty()) || (!s->queue.empty() && s->inflight < (int)s->slots.size());
+        });
+        if (s->queue.empty()) return;  // stopping, nothing left to admit
         // admission by device memory: the request's records + tables must fit above the reserve
         size_t free_b = 0, total_b = 0;
         auto req = s->queue.front();
@@ -145,7 +148,10 @@ void dispatch_loop(rt_server *s) {
         lk.unlock();
         const rt_err e = start(s, sl, *req);
         lk.lock();
+        // until start() has recorded the slot's event, a query of that event
+        // reports the previous request (or success, if never recorded)
         if (e != RT_OK) finish_locked(s, sl, e);
+        else sl.armed = true;
     }
 }
 
@@ -156,8 +162,9 @@ void complete_loop(rt_server *s) {
         if (s->stopping && s->inflight == 0 && s->queue.empty()) return;
         bool any = false;
         for (auto &sl : s->slots) {
-            if (!sl.req || sl.req->done) continue;
+            if (!sl.req) continue;
             any = true;
+            if (!sl.armed) continue;  // still being started by the dispatcher
             const cudaError_t q = cudaEventQuery(sl.event);
             if (q == cudaErrorNotReady) continue;
             rt_err st = RT_OK;

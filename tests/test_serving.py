@@ -101,3 +101,29 @@ def test_request_stream_is_seeded_and_shaped():
         assert abs(f.tx_lat_deg - (gs.lat0_deg + 0.5 * gs.dlat_deg * (gs.n_lat - 1))) <= 5.0
     shapes = {(len(f.az_deg) == 1) for _, f in a}
     assert shapes == {True, False}  # both ionogram-synthesis and OTHR-registration requests
+
+
+@pytest.mark.gpu
+def test_many_small_requests_through_few_slots():
+    """Hundreds of 1-3 ray requests through 3 slots: slots are reused while
+    others run, so a request must never be reported finished before its own
+    work is queued (each record must equal its solo trace)."""
+    rtbuild.build()
+    w = wl.config1()
+    g = rt.Grid(w.grid, w.ne)
+    rng = np.random.default_rng(11)
+    specs = []
+    for i in range(240):
+        k = int(rng.integers(1, 4))
+        specs.append(w.fan.replace(el_deg=np.sort(rng.uniform(5.0, 50.0, k)), az_deg=[rng.uniform(0.0, 360.0)],
+                                   integrator=wl.RKF45, rtol=1e-8, precision=wl.MIXED))
+    cfg = rt.launch_config(kernel=rt.RT_KERNEL_PLAIN, stencil=rt.RT_STENCIL_QUAD, lanes_per_ray=1)
+    solo = [rt.rt_trace(g, rt.Fan(s), cfg=cfg) for s in specs]
+    srv = rt.Server(max_inflight=3, cfg=cfg)
+    fans = [rt.Fan(s) for s in specs]
+    tickets = [srv.submit(g, f) for f in fans]
+    for k, (t, out) in enumerate(tickets):
+        st = srv.wait(t, timeout_s=300.0)
+        assert st.status == rt.RT_OK
+        assert out.tobytes() == solo[k].tobytes(), k
+    srv.close()
