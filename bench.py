@@ -40,6 +40,9 @@ METRIC = "rays/s and ray-steps/s at ≤0.05 km P'/D error; p50/p99 fan latency"
 # ~60, Hamiltonian partials + ray equations ~70, stage offsets and RK
 # accumulation ~90 (mixed path; the FP64 path accumulates inside rk*_step64).
 FLOP_PER_EVAL = {"mixed": 1000.0, "fp64": 910.0}
+# Grid samples one stage evaluation reads: 64 samples (16 rows of 4) plus the
+# reference node, FP32 in the mixed path and FP64 in the all-FP64 path.
+GATHER_BYTES = {"mixed": 65 * 4, "fp64": 64 * 8}
 SMS = 152
 FP32_LANES_PER_SM = 128
 FP64_FMA_PER_SM_CLK = 2  # GB300: FP64 issue rate is 1/64 of FP32
@@ -254,6 +257,7 @@ def run_ours(args):
     def step():
         rt.rt_trace_device(grid, fan, out.data_ptr(), n, cfg=cfg, stream=sptr)
 
+    peaks = rt.rt_measure_peaks()  # this GPU's FP32/FP64 FMA and L2 read ceilings (own kernels)
     args.warmup = max(args.warmup, 3)  # at least 3 untimed warm-up steps
     for _ in range(args.warmup):
         step()
@@ -388,7 +392,13 @@ def run_ours(args):
             "fp64_gpu_path": {"rays_per_s": n / fp64_s, "seconds": fp64_s},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None, "peak_basis": bound_note,
-                         "flop_per_stage_eval": FLOP_PER_EVAL[args.precision]},
+                         "flop_per_stage_eval": FLOP_PER_EVAL[args.precision],
+                         "measured_peaks": peaks,
+                         "frac_of_measured": achieved / (peaks["fp32_fma_tflops"] if prec == rt.RT_MIXED
+                                                         else peaks["fp64_fma_tflops"]),
+                         "gather": {"bytes_per_stage_eval": GATHER_BYTES[args.precision],
+                                    "achieved_gbs": evals * GATHER_BYTES[args.precision] / sec / 1e9,
+                                    "l2_read_peak_gbs": peaks["l2_read_gbs"]}},
             "cpu_baseline": cpu,
             "e2e": {"value": n * world / e2e_s, "unit": "rays/s", "h2d_bytes_per_step": fan.host_bytes,
                     "d2h_bytes_per_step": n * 64},

@@ -338,6 +338,25 @@ rt_err rt_server_wait(rt_server *srv, uint64_t ticket, double timeout_s, rt_requ
 /* Finishes every queued and running request, then stops the threads. */
 rt_err rt_server_destroy(rt_server *srv);
 
+/* ------------------------------------------------------------ measurement */
+/* Ceilings of the current GPU measured with kernels of this library: FP32 and
+ * FP64 fused multiply-add throughput (independent FMA chains on every lane of
+ * every SM; an FMA counts 2 flop) and L2 read bandwidth (a 48 MiB buffer read
+ * repeatedly through L2, bypassing L1).  Takes about a second.  The paper has
+ * no counterpart: the benchmark uses these as the roofline ceilings of the
+ * tracer (FP32 issue for the mixed path, FP64 for the all-FP64 path, L2 for
+ * the sample gathers). */
+typedef struct rt_peaks {
+    double fp32_fma_flops;       /* flop/s */
+    double fp64_fma_flops;       /* flop/s */
+    double l2_read_bytes_per_s;  /* bytes/s */
+    int32_t sm_count;
+    int32_t reserved;
+    double max_sm_mhz;           /* the device's maximum SM clock */
+} rt_peaks;
+
+rt_err rt_measure_peaks(rt_peaks *out);
+
 /* Diagnostic: the right-hand side dy/dP' of the ray equations (Eq. 1a-1f)
  * at n given states, exactly as one stage of the tracer evaluates it.
  * y_host: n x 6 doubles (r km, theta rad colatitude, phi rad longitude,

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librtgd.so")
-SOURCES = ["rtgd_api.cu", "rtgd_kernels.cu", "rtgd_noalloc.cu", "rtgd_server.cu"]
+SOURCES = ["rtgd_api.cu", "rtgd_kernels.cu", "rtgd_noalloc.cu", "rtgd_server.cu", "rtgd_peaks.cu"]
 HEADERS = [os.path.join(INCLUDE, "rtgd.h"), os.path.join(CSRC, "rtgd_device.cuh"),
            os.path.join(CSRC, "rtgd_internal.h")]
 NVCC = os.environ.get("NVCC", "nvcc")

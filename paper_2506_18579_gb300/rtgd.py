@@ -32,7 +32,7 @@ EXPORTED = ["rt_grid_create", "rt_grid_destroy", "rt_grid_device_bytes", "rt_fan
             "rt_trace", "rt_trace_device", "rt_tune", "rt_eval_rhs", "rt_last_error",
             "rt_version", "rt_plan_create", "rt_plan_rays", "rt_plan_execute", "rt_plan_destroy",
             "rt_ionogram", "rt_trace_device_noalloc", "rt_server_create", "rt_server_submit",
-            "rt_server_wait", "rt_server_destroy"]
+            "rt_server_wait", "rt_server_destroy", "rt_measure_peaks"]
 
 
 class RtError(RuntimeError):
@@ -96,6 +96,12 @@ class rt_server_config(ctypes.Structure):
 class rt_request_stats(ctypes.Structure):
     _fields_ = [("queue_s", ctypes.c_double), ("run_s", ctypes.c_double), ("total_s", ctypes.c_double),
                 ("n_rays", ctypes.c_int64), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class rt_peaks(ctypes.Structure):
+    _fields_ = [("fp32_fma_flops", ctypes.c_double), ("fp64_fma_flops", ctypes.c_double),
+                ("l2_read_bytes_per_s", ctypes.c_double), ("sm_count", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("max_sm_mhz", ctypes.c_double)]
 
 
 IONOGRAM_DTYPE = np.dtype([("freq_mhz", "f8"), ("group_path_km", "f8"), ("el_deg", "f8"),
@@ -163,6 +169,8 @@ def load(path=None):
     L.rt_server_wait.restype = ctypes.c_int
     L.rt_server_destroy.argtypes = [vp]
     L.rt_server_destroy.restype = ctypes.c_int
+    L.rt_measure_peaks.argtypes = [ctypes.POINTER(rt_peaks)]
+    L.rt_measure_peaks.restype = ctypes.c_int
     L.rt_last_error.argtypes = []
     L.rt_last_error.restype = ctypes.c_char_p
     L.rt_version.argtypes = []
@@ -378,6 +386,14 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def rt_measure_peaks():
+    """This GPU's FP32/FP64 FMA flop/s and L2 read bytes/s (rt_peaks)."""
+    p = rt_peaks()
+    _check(load().rt_measure_peaks(ctypes.byref(p)))
+    return {"fp32_fma_tflops": p.fp32_fma_flops / 1e12, "fp64_fma_tflops": p.fp64_fma_flops / 1e12,
+            "l2_read_gbs": p.l2_read_bytes_per_s / 1e9, "sm_count": p.sm_count, "max_sm_mhz": p.max_sm_mhz}
 
 
 def rt_tune(grid, fan, max_rays=0, stream=None):

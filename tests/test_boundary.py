@@ -65,6 +65,38 @@ int main(void) {
     assert vals[2] == 64
 
 
+def test_every_struct_size_and_field_offset_matches(tmp_path):
+    """Every ctypes mirror of a header struct: size and each field's offset."""
+    mirrors = {"rt_dipole": rt.rt_dipole, "rt_grid_desc": rt.rt_grid_desc, "rt_fan_desc": rt.rt_fan_desc,
+               "rt_launch_config": rt.rt_launch_config, "rt_ionogram_desc": rt.rt_ionogram_desc,
+               "rt_server_config": rt.rt_server_config, "rt_request_stats": rt.rt_request_stats,
+               "rt_peaks": rt.rt_peaks}
+    lines = []
+    for name, cls in mirrors.items():
+        lines.append('  printf("%%zu\\n", sizeof(%s));' % name)
+        for fname, _ in cls._fields_:
+            lines.append('  printf("%%zu\\n", offsetof(%s, %s));' % (name, fname))
+    for dt_name, dt, cname in (("RESULT", rt.RESULT_DTYPE, "rt_ray_result"),
+                               ("IONO", rt.IONOGRAM_DTYPE, "rt_ionogram_point")):
+        lines.append('  printf("%%zu\\n", sizeof(%s));' % cname)
+        for fname in dt.names:
+            lines.append('  printf("%%zu\\n", offsetof(%s, %s));' % (cname, fname))
+    src = tmp_path / "probe_all.c"
+    src.write_text("#include <stdio.h>\n#include <stddef.h>\n#include \"rtgd.h\"\nint main(void) {\n" +
+                   "\n".join(lines) + "\n  return 0;\n}\n")
+    exe = tmp_path / "probe_all"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    vals = iter(int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split())
+    for name, cls in mirrors.items():
+        assert next(vals) == ctypes.sizeof(cls), name
+        for fname, _ in cls._fields_:
+            assert next(vals) == getattr(cls, fname).offset, (name, fname)
+    for dt in (rt.RESULT_DTYPE, rt.IONOGRAM_DTYPE):
+        assert next(vals) == dt.itemsize
+        for fname in dt.names:
+            assert next(vals) == dt.fields[fname][1], fname
+
+
 def test_version_and_fan_size(lib):
     from paper_2506_18579_gb300 import workloads as wl
     assert rt.rt_version() == 1
