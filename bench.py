@@ -61,6 +61,11 @@ def parse_args():
     p.add_argument("--stencil", choices=["gather", "quad", "table"], default="quad")
     p.add_argument("--order", choices=["canonical", "elevation"], default="elevation")
     p.add_argument("--threads", type=int, default=128)
+    p.add_argument("--lanes", type=int, default=0, choices=[0, 1, 2, 4],
+                   help="lanes per ray with --kernel (0 = the library's choice)")
+    p.add_argument("--one-ray", type=int, default=None,
+                   help="latency mode: trace only this canonical ray of the fan (alone) --steps times "
+                        "and print its time per stage evaluation")
     p.add_argument("--profile", action="store_true",
                    help="warm-up launches then one launch, nothing else (for ncu captures)")
     p.add_argument("--cpu-sample", type=int, default=512)
@@ -240,9 +245,14 @@ def run_ours(args):
             stencil={"gather": rt.RT_STENCIL_GATHER, "quad": rt.RT_STENCIL_QUAD,
                      "table": rt.RT_STENCIL_TABLE}[args.stencil],
             block_threads=args.threads,
-            order=rt.RT_ORDER_CANONICAL if args.order == "canonical" else rt.RT_ORDER_ELEVATION_FASTEST)
+            order=rt.RT_ORDER_CANONICAL if args.order == "canonical" else rt.RT_ORDER_ELEVATION_FASTEST,
+            lanes_per_ray=args.lanes)
     elif prec == rt.RT_MIXED and not args.no_tune:
         cfg, tune_ms = rt.rt_tune(grid, fan, max_rays=8192, stream=sptr)
+    if args.one_ray is not None:
+        run_one_ray(args, rt, wl, torch, grid, spec, prec, cfg)
+        grid.close()
+        return
     if args.profile:
         for _ in range(max(args.warmup, 1) + 1):
             rt.rt_trace_device(grid, fan, out.data_ptr(), n, cfg=cfg, stream=sptr)
@@ -414,6 +424,40 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_one_ray(args, rt, wl, torch, grid, spec, prec, cfg):
+    """Latency of one ray traced alone (a one-ray fan): the fan's critical path
+    when its longest ray dominates.  Prints the time per stage evaluation."""
+    freq, el, az = np.atleast_1d(spec.freq_mhz), np.atleast_1d(spec.el_deg), np.atleast_1d(spec.az_deg)
+    modes = [m for m in (wl.MODE_O, wl.MODE_X) if spec.modes & m]
+    i = args.one_ray
+    ia, i = i % len(az), i // len(az)
+    ie, i = i % len(el), i // len(el)
+    im, fi = i % len(modes), i // len(modes)
+    one = spec.replace(freq_mhz=np.array([freq[fi]]), modes=modes[im], el_deg=np.array([el[ie]]),
+                       az_deg=np.array([az[ia]]))
+    fan = rt.Fan(one, prec)
+    st = torch.cuda.current_stream()
+    buf = torch.empty(64, dtype=torch.uint8, device="cuda")
+    for _ in range(max(args.warmup, 1)):
+        rt.rt_trace_device(grid, fan, buf.data_ptr(), 1, cfg=cfg, stream=st.cuda_stream)
+    ts = []
+    for _ in range(args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        rt.rt_trace_device(grid, fan, buf.data_ptr(), 1, cfg=cfg, stream=st.cuda_stream)
+        b.record(st)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    r = rt.results_view(buf.cpu().numpy(), 1)
+    ms = float(np.median(ts))
+    print(json.dumps({"one_ray": args.one_ray, "freq_mhz": float(freq[fi]), "mode": "O" if modes[im] == wl.MODE_O else "X",
+                      "el_deg": float(el[ie]), "az_deg": float(az[ia]), "status": int(r["status"][0]),
+                      "stage_evals": int(r["n_evals"][0]), "ms": ms,
+                      "ns_per_stage_eval": ms * 1e6 / max(int(r["n_evals"][0]), 1),
+                      "launch": None if cfg is None else {"kernel": cfg.kernel, "stencil": cfg.stencil,
+                                                          "lanes_per_ray": cfg.lanes_per_ray}}), flush=True)
 
 
 def run_batch(rt, wl, torch, flush, steps=3):

@@ -279,12 +279,8 @@ __device__ __forceinline__ void ray_rhs(const RayPhys<R> &rp, const StageIn<R> &
         const R q = rp.R_E * ir;
         const R A = rp.ab0 * q * q * q;  // Y = A (-2 m_r, m_th, m_ph)
         const R Y0 = R(-2) * A * mr, Y1 = A * mt, Y2 = A * mp;
-        // Jacobian dY_i/d(r, theta, phi) from dm_r/dth = m_th, dm_r/dph = sin m_ph,
-        // dm_th/dth = -m_r, dm_th/dph = cos m_ph, dm_ph/dph = -(sin m_r + cos m_th)
-        const R J00 = R(6) * A * mr * ir, J01 = R(-2) * A * mt, J02 = R(-2) * A * s.sth * mp;
-        const R J10 = R(-3) * A * mt * ir, J11 = -A * mr, J12 = A * s.cth * mp;
-        const R J20 = R(-3) * A * mp * ir, J21 = R(0), J22 = -A * (s.sth * mr + s.cth * mt);
-        const R YY = Y0 * Y0 + Y1 * Y1 + Y2 * Y2;
+        const R A2 = A * A;
+        const R YY = A2 * (R(1) + R(3) * mr * mr);  // |Y|^2, m being a unit vector
         const R kY = kr * Y0 + kt * Y1 + kp * Y2;
         const R ikk = recip(kk);
         const R L = kY * kY * ikk;
@@ -296,12 +292,21 @@ __device__ __forceinline__ void ray_rhs(const RayPhys<R> &rp, const StageIn<R> &
         // mu^2 = F(X, L, T) with T = Y^2 - L: d/dY^2 = F_T, d/dL|_{Y^2} = F_L - F_T
         const R FYL = FL - FT;
         const R c2 = R(2) * kY * ikk;
-        const R gY2_0 = R(2) * (Y0 * J00 + Y1 * J10 + Y2 * J20);
-        const R gY2_1 = R(2) * (Y0 * J01 + Y1 * J11 + Y2 * J21);
-        const R gY2_2 = R(2) * (Y0 * J02 + Y1 * J12 + Y2 * J22);
-        const R gL_0 = c2 * (kr * J00 + kt * J10 + kp * J20);
-        const R gL_1 = c2 * (kr * J01 + kt * J11 + kp * J21);
-        const R gL_2 = c2 * (kr * J02 + kt * J12 + kp * J22);
+        // Partials of Y along (r, theta, phi), from dm_r/dth = m_th, dm_th/dth = -m_r,
+        // dm_ph/dth = 0, dm_r/dph = sin m_ph, dm_th/dph = cos m_ph,
+        // dm_ph/dph = -(sin m_r + cos m_th):
+        //   dY/dr = -3 Y / r,  dY/dth = A (-2 m_th, -m_r, 0),
+        //   dY/dph = A (-2 sin m_ph, cos m_ph, -(sin m_r + cos m_th)).
+        // Then d|Y|^2/dx = 2 Y . dY/dx = (-6 |Y|^2 / r, 6 A^2 m_r m_th, 6 A^2 m_r sin m_ph)
+        // and dL/dx at fixed k = c2 k . dY/dx.
+        const R smp = s.sth * mp;
+        const R A6mr = R(6) * A2 * mr;
+        const R gY2_0 = R(-6) * YY * ir;
+        const R gY2_1 = A6mr * mt;
+        const R gY2_2 = A6mr * smp;
+        const R gL_0 = R(-3) * c2 * kY * ir;
+        const R gL_1 = c2 * A * (R(-2) * kr * mt - kt * mr);
+        const R gL_2 = c2 * A * (R(-2) * kr * smp + kt * s.cth * mp - kp * (s.sth * mr + s.cth * mt));
         Hr = R(-0.5) * (FX * s.dX[0] + FT * gY2_0 + FYL * gL_0);
         Ht = R(-0.5) * (FX * s.dX[1] + FT * gY2_1 + FYL * gL_1);
         Hp = R(-0.5) * (FX * s.dX[2] + FT * gY2_2 + FYL * gL_2);

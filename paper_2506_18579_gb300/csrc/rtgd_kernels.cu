@@ -834,7 +834,7 @@ struct Lane {
     float xfac, ab0;
     Base32 b;
     int out_id, mode;
-    int stage, n_steps, n_att, n_ev, status, side, land_it, since_sync;
+    int n_steps, n_att, n_ev, status, side, land_it, since_sync;
     bool active, launch, landing, exiting, have_prev, k1_valid, at_face;
 };
 
@@ -851,9 +851,23 @@ __device__ __forceinline__ RayPhys<float> lane_phys(const GridDev &g, const Lane
     return p;
 }
 
-// Fills acc/y4/e from stage s output ks.
-__device__ __forceinline__ void accumulate(Lane &L, const Tableau &T, int s, const float ks[6]) {
-    const bool first = s == 0;  // stage 0 starts a fresh attempt
+// Stage 0 of an attempt: acc/y4/e start from k1.
+__device__ __forceinline__ void accumulate_first(Lane &L, const Tableau &T, const float k1[6]) {
+    float A[5];
+#pragma unroll
+    for (int t = 0; t < 5; ++t) A[t] = T.A[0][t];
+    const float b4 = T.B4[0], e = T.E[0];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+#pragma unroll
+        for (int t = 0; t < 5; ++t) L.acc[t][c] = A[t] * k1[c];
+        L.y4[c] = b4 * k1[c];
+        L.e[c] = e * k1[c];
+    }
+}
+
+// Stage s >= 1: shift the accumulators and add stage s's output ks.
+__device__ __forceinline__ void accumulate_next(Lane &L, const Tableau &T, int s, const float ks[6]) {
     float A[5];
 #pragma unroll
     for (int t = 0; t < 5; ++t) A[t] = T.A[s][t];
@@ -861,10 +875,10 @@ __device__ __forceinline__ void accumulate(Lane &L, const Tableau &T, int s, con
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
 #pragma unroll
-        for (int t = 0; t < 4; ++t) L.acc[t][c] = (first ? 0.0f : L.acc[t + 1][c]) + A[t] * ks[c];
+        for (int t = 0; t < 4; ++t) L.acc[t][c] = L.acc[t + 1][c] + A[t] * ks[c];
         L.acc[4][c] = A[4] * ks[c];
-        L.y4[c] = (first ? 0.0f : L.y4[c]) + b4 * ks[c];
-        L.e[c] = (first ? 0.0f : L.e[c]) + e * ks[c];
+        L.y4[c] += b4 * ks[c];
+        L.e[c] += e * ks[c];
     }
 }
 
@@ -890,7 +904,6 @@ __device__ void lane_begin_ray(Lane &L, const GridDev &g, const FanDev &f, long 
     L.status = RT_RAY_NOT_RUN;
     L.have_prev = L.k1_valid = L.landing = L.exiting = false;
     L.launch = true;
-    L.stage = 0;
     base_from_state(g, y, L.b);
 }
 
@@ -929,9 +942,9 @@ __device__ __forceinline__ void lane_limit_step(Lane &L, const GridDev &g, const
     if (f.has_max_path && L.P + (double)L.hs > f.max_path) L.hs = (float)(f.max_path - L.P);
 }
 
-// Starts the next step attempt from the current state; returns false when the
-// ray stops (step budget).
-__device__ __forceinline__ bool lane_begin_attempt(Lane &L, const GridDev &g, const FanDev &f, const Tableau &T) {
+// Sets up the next step attempt from the current state; returns false when
+// the ray stops (step budget).
+__device__ __forceinline__ bool lane_next_attempt(Lane &L, const FanDev &f) {
     if (L.n_att >= f.max_steps) {
         L.status = RT_RAY_MAX_STEPS;
         return false;
@@ -940,65 +953,76 @@ __device__ __forceinline__ bool lane_begin_attempt(Lane &L, const GridDev &g, co
         L.hs = L.h;
         L.at_face = false;
     }
-    if (L.k1_valid) {  // k1 at this state is known: start at stage 1
-        lane_limit_step(L, g, f);
-        accumulate(L, T, 0, L.k1);
-        L.stage = 1;
-    } else {
-        L.stage = 0;
-    }
     return true;
 }
 
-// One stage evaluation of one lane plus its bookkeeping.  Returns true when
-// the ray has finished (status set).
+// The launch evaluation: mu^2 at the transmitter for the launch direction,
+// then |k| = mu.  Returns true when the ray has finished (status set).
 template <int STENCIL, int G>
-__device__ bool lane_advance(Lane &L, const GridDev &g, const FanDev &f, const Tableau &T, int q, unsigned gmask) {
-    const double RE = g.R_E;
+__device__ bool lane_launch(Lane &L, const GridDev &g, const FanDev &f, int q, unsigned gmask) {
     const RayPhys<float> rp = lane_phys(g, L);
     float d[6], ks[6], mu2;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) d[c] = 0.0f;
+    rhs_mixed<STENCIL, G>(g, rp, L.b, d, ks, &mu2, q, gmask);
     ++L.n_ev;
-    if (L.launch) {
-        // mu^2 at the transmitter for the launch direction (|k| = 1 in the base)
+    L.launch = false;
+    if (!(mu2 > 0.0f)) {
+        L.status = RT_RAY_NONFINITE;
+        return true;
+    }
+    // |k| = mu: rescale the launch direction (double), split into hi + lo
+    const double mu = sqrt((double)mu2);
+    double y[6];
+    lane_state(L, y);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const double k = y[3 + i] * mu;
+        L.k_hi[i] = (float)k;
+        L.k_lo[i] = (float)(k - (double)L.k_hi[i]);
+        L.b.k[i] = L.k_hi[i];
+    }
+    return !lane_next_attempt(L, f);
+}
+
+// The stages of one step attempt.  Every lane of a warp runs its attempt in
+// the same loop, so the stage index is warp-uniform: the lanes stay converged
+// and the Butcher coefficients are broadcast reads.  Stage 0 is evaluated
+// only when k1 at the current state is not yet known (after a rejected
+// attempt or during the landing solve it is).
+template <int STENCIL, int G>
+__device__ __forceinline__ void lane_attempt(Lane &L, const GridDev &g, const FanDev &f, const Tableau &T, int q,
+                                             unsigned gmask) {
+    const RayPhys<float> rp = lane_phys(g, L);
+    float d[6], ks[6];
+    if (!L.k1_valid) {
 #pragma unroll
         for (int c = 0; c < 6; ++c) d[c] = 0.0f;
-        rhs_mixed<STENCIL, G>(g, rp, L.b, d, ks, &mu2, q, gmask);
-        L.launch = false;
-        if (!(mu2 > 0.0f)) {
-            L.status = RT_RAY_NONFINITE;
-            return true;
-        }
-        // |k| = mu: rescale the launch direction (double), split into hi + lo
-        const double mu = sqrt((double)mu2);
-        double y[6];
-        lane_state(L, y);
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            const double k = y[3 + i] * mu;
-            L.k_hi[i] = (float)k;
-            L.k_lo[i] = (float)(k - (double)L.k_hi[i]);
-            L.b.k[i] = L.k_hi[i];
-        }
-        return !lane_begin_attempt(L, g, f, T);
-    }
-#pragma unroll
-    for (int c = 0; c < 6; ++c) d[c] = (L.stage == 0) ? 0.0f : L.hs * L.acc[0][c];
-    rhs_mixed<STENCIL, G>(g, rp, L.b, d, ks, nullptr, q, gmask);
-    if (L.stage == 0) {
-#pragma unroll
-        for (int c = 0; c < 6; ++c) L.k1[c] = ks[c];
+        rhs_mixed<STENCIL, G>(g, rp, L.b, d, L.k1, nullptr, q, gmask);
+        ++L.n_ev;
         L.k1_valid = true;
-        lane_limit_step(L, g, f);
-        if (L.have_prev && L.dr_prev > 0.0f && ks[0] <= 0.0f) {
-            const float rise = hermite_rise_f(L.b.r - L.r_prev, L.h_prev * L.dr_prev, L.h_prev * ks[0]);
+        if (L.have_prev && L.dr_prev > 0.0f && L.k1[0] <= 0.0f) {
+            const float rise = hermite_rise_f(L.b.r - L.r_prev, L.h_prev * L.dr_prev, L.h_prev * L.k1[0]);
             L.apo = fmaxf(L.apo, L.b.alt - (L.b.r - L.r_prev) + rise);
         }
         L.have_prev = false;
     }
-    accumulate(L, T, L.stage, ks);
-    if (++L.stage < T.ns) return false;
+    lane_limit_step(L, g, f);
+    accumulate_first(L, T, L.k1);
+#pragma unroll 1
+    for (int s = 1; s < T.ns; ++s) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) d[c] = L.hs * L.acc[0][c];
+        rhs_mixed<STENCIL, G>(g, rp, L.b, d, ks, nullptr, q, gmask);
+        ++L.n_ev;
+        accumulate_next(L, T, s, ks);
+    }
+}
 
-    // ---- attempt complete: increments in float, state update in double
+// Bookkeeping after an attempt: landing/exit solve, accept or reject, state
+// update in double.  Returns true when the ray has finished (status set).
+__device__ bool lane_end_attempt(Lane &L, const GridDev &g, const FanDev &f) {
+    const double RE = g.R_E;
     const float hf = L.hs;
     ++L.n_att;
     float dy4[6], ef[6];
@@ -1029,7 +1053,7 @@ __device__ bool lane_advance(Lane &L, const GridDev &g, const FanDev &f, const T
                 L.side = 1;
             }
             L.hs = (float)(L.lb - L.lfb * (L.lb - L.la) / (L.lfb - L.lfa));
-            return !lane_begin_attempt(L, g, f, T);
+            return !lane_next_attempt(L, f);
         }
         if (!fin) {
             L.status = RT_RAY_NONFINITE;
@@ -1058,7 +1082,7 @@ __device__ bool lane_advance(Lane &L, const GridDev &g, const FanDev &f, const T
                 L.status = RT_RAY_STEP_UNDERFLOW;
                 return true;
             }
-            return !lane_begin_attempt(L, g, f, T);
+            return !lane_next_attempt(L, f);
         }
         h_next = fminf(fmaxf(L.h * (L.at_face ? fminf(1.0f, fac) : fac), f.hmin_f), f.hmax_f);
     }
@@ -1082,7 +1106,7 @@ __device__ bool lane_advance(Lane &L, const GridDev &g, const FanDev &f, const T
         L.side = 0;
         L.land_it = 0;
         L.hs = (float)(L.lb - L.lfb * (L.lb - L.la) / (L.lfb - L.lfa));
-        return !lane_begin_attempt(L, g, f, T);
+        return !lane_next_attempt(L, f);
     }
     L.r_prev = L.b.r;
 #pragma unroll
@@ -1118,7 +1142,7 @@ __device__ bool lane_advance(Lane &L, const GridDev &g, const FanDev &f, const T
         return true;
     }
     L.h = h_next;
-    return !lane_begin_attempt(L, g, f, T);
+    return !lane_next_attempt(L, f);
 }
 
 // Loads the Butcher table of the fan's integrator into shared memory (lanes
@@ -1137,8 +1161,8 @@ __device__ __forceinline__ unsigned group_mask(int lane) {
     return G == 1 ? (1u << lane) : (((1u << G) - 1u) << (lane & ~(G - 1)));
 }
 
-// One ray per thread group of G lanes; each group loops stage by stage until
-// its ray ends.
+// One ray per thread group of G lanes; each group loops attempt by attempt
+// until its ray ends.
 template <int STENCIL, int G>
 __global__ void __launch_bounds__(128, 3) trace_mixed_plain_kernel(GridDev g, FanDev f, rt_ray_result *__restrict__ out) {
     __shared__ Tableau T;
@@ -1151,16 +1175,20 @@ __global__ void __launch_bounds__(128, 3) trace_mixed_plain_kernel(GridDev g, Fa
     Lane L;
     L.active = true;
     lane_begin_ray(L, g, f, claim_to_ray(f, id));
-    // bounded: at most (max_steps + 1) attempts of T.ns stages plus the launch
-    const long long max_iter = ((long long)f.max_steps + 2) * 6 + 8;
-    bool done = false;
-    for (long long it = 0; it < max_iter && !done; ++it) done = lane_advance<STENCIL, G>(L, g, f, T, q, gmask);
+    bool done = lane_launch<STENCIL, G>(L, g, f, q, gmask);
+    // bounded: every attempt counts against max_steps, so max_steps + 1 attempts end every ray
+    const long long max_att = (long long)f.max_steps + 2;
+    for (long long it = 0; it < max_att && !done; ++it) {
+        lane_attempt<STENCIL, G>(L, g, f, T, q, gmask);
+        done = lane_end_attempt(L, g, f);
+    }
     if (!done) L.status = RT_RAY_MAX_STEPS;
     lane_finish(L, g, f, out, q == 0);
 }
 
 // Persistent kernel: resident blocks; every warp keeps its 32 lanes busy by
 // claiming new rays (one atomicAdd per warp for all idle lanes) as rays end.
+// Claims happen between attempts, where all lanes of the warp meet.
 template <int STENCIL, int G>
 __global__ void __launch_bounds__(128, 3) trace_mixed_persistent_kernel(GridDev g, FanDev f,
                                                                      rt_ray_result *__restrict__ out,
@@ -1175,9 +1203,9 @@ __global__ void __launch_bounds__(128, 3) trace_mixed_persistent_kernel(GridDev 
     bool exhausted = false;  // warp-uniform
     long long iters = 0;
     const long long n = f.n_rays;
-    // bound on the warp's total iterations: every ray needs at most
-    // (max_steps + 2) * 6 + 8 stage iterations, and a warp runs at most all n rays
-    const long long max_iter = (((long long)f.max_steps + 2) * 6 + 8) * (n + 32) + 64;
+    // bound on the warp's loop iterations: every ray ends within max_steps + 1
+    // attempts (+ its launch), and a warp runs at most all n rays
+    const long long max_iter = ((long long)f.max_steps + 4) * (n + 32) + 64;
     for (;;) {
         // the lanes of a group share their ray, so idle lanes come in whole groups
         const unsigned idle = __ballot_sync(FULL, !L.active);
@@ -1193,6 +1221,7 @@ __global__ void __launch_bounds__(128, 3) trace_mixed_persistent_kernel(GridDev 
                 if (c < (unsigned long long)n) {
                     L.active = true;
                     lane_begin_ray(L, g, f, claim_to_ray(f, (long long)c));
+                    if (lane_launch<STENCIL, G>(L, g, f, q, gmask)) lane_finish(L, g, f, out, q == 0);
                 }
             }
         }
@@ -1204,7 +1233,10 @@ __global__ void __launch_bounds__(128, 3) trace_mixed_persistent_kernel(GridDev 
             }
             break;
         }
-        if (L.active && lane_advance<STENCIL, G>(L, g, f, T, q, gmask)) lane_finish(L, g, f, out, q == 0);
+        if (L.active) {
+            lane_attempt<STENCIL, G>(L, g, f, T, q, gmask);
+            if (lane_end_attempt(L, g, f)) lane_finish(L, g, f, out, q == 0);
+        }
     }
 }
 
