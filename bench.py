@@ -397,6 +397,10 @@ def run_ours(args):
             "attempts_per_s": attempts * world / sec,
             "stage_evals_per_s": evals * world / sec,
             "fan_latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
+            "longest_ray": {"index": int(np.argmax(res["n_evals"])), "stage_evals": int(res["n_evals"].max()),
+                            "status": int(res["status"][int(np.argmax(res["n_evals"]))]),
+                            "stage_evals_p50": float(np.median(res["n_evals"])),
+                            "stage_evals_p99": float(np.percentile(res["n_evals"], 99))},
             "accuracy": acc,
             "tighter_rtol": nominal,
             "fp64_gpu_path": {"rays_per_s": n / fp64_s, "seconds": fp64_s},

@@ -86,6 +86,35 @@ __device__ __forceinline__ void gd_half(R s, R &wm1, R &w0, R &dm1, R &d0, int i
     d0 = s * (R(-4.5) + s * (R(1.5) + s * (R(5.0) - s * R(2.5))));
 }
 
+// gd_half with the interpolant fixed at compile time (IP = 0 GD, 1 CR).
+template <typename R, int IP>
+__device__ __forceinline__ void half_weights(R s, R &wm1, R &w0, R &dm1, R &d0) {
+    if (IP == 1) {
+        wm1 = s * (R(-0.5) + s * (R(1) - s * R(0.5)));
+        w0 = R(1) + s * s * (R(-2.5) + s * R(1.5));
+        dm1 = R(-0.5) + s * (R(2) - s * R(1.5));
+        d0 = s * (R(-5) + s * R(4.5));
+    } else {
+        wm1 = s * (R(-0.5) + s * (R(11.0 / 12.0) + s * (R(-1.0 / 6.0) + s * (R(-5.0 / 12.0) + s * R(1.0 / 6.0)))));
+        w0 = R(1) + s * s * (R(-2.25) + s * (R(0.5) + s * (R(1.25) - s * R(0.5))));
+        dm1 = R(-0.5) + s * (R(11.0 / 6.0) + s * (R(-0.5) + s * (R(-5.0 / 3.0) + s * R(5.0 / 6.0))));
+        d0 = s * (R(-4.5) + s * (R(1.5) + s * (R(5.0) - s * R(2.5))));
+    }
+}
+
+// All four weights of one axis, interpolant fixed at compile time: nodes j-1,
+// j from half_weights(t), nodes j+2, j+1 from its mirror half_weights(1 - t).
+template <typename R, int IP>
+__device__ __forceinline__ void axis_weights(R t, R w[4], R d[4]) {
+    R wp2, wp1, dp2, dp1;
+    half_weights<R, IP>(t, w[0], w[1], d[0], d[1]);
+    half_weights<R, IP>(R(1) - t, wp2, wp1, dp2, dp1);
+    w[2] = wp1;
+    w[3] = wp2;
+    d[2] = -dp1;
+    d[3] = -dp2;
+}
+
 // All four weights of one axis (w[a], d[a] for node j-1+a), GD or CR.
 template <typename R>
 __device__ __forceinline__ void interp_weights(R t, R w[4], R d[4], int interp) {
@@ -159,6 +188,11 @@ __device__ __forceinline__ void acc_row(R v, R dv, R wb, R db, R &s, R &sb, R &s
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 __device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
 
+// sqrt: correctly rounded in double; in float x * rsqrt(x) (MUFU.RSQ, a few
+// ulp, no special-case branch), 0 for x <= 0.
+__device__ __forceinline__ double fsqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float fsqrt(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
+
 // Cell index and local coordinate along one axis; false outside [0, n-1].
 template <typename R>
 __device__ __forceinline__ bool cell_coord(R x, int n, int &i, R &t) {
@@ -214,7 +248,7 @@ __device__ __forceinline__ RayPhys<R> make_phys(const GridDev &g, double f_hz, i
 template <typename R>
 __device__ __forceinline__ void appleton_hartree(R X, R L, R T, int mode, R &mu2, R &FX, R &FL, R &FT) {
     const R u = R(1) - X;
-    const R S = sqrt(T * T + R(4) * L * u * u);
+    const R S = fsqrt(T * T + R(4) * L * u * u);
     const R iS = recip(S);
     if (mode > 0) {
         const R W = S + T;
@@ -245,6 +279,51 @@ __device__ __forceinline__ void appleton_hartree(R X, R L, R T, int mode, R &mu2
     }
 }
 
+// Field terms of one stage that do not depend on the electron density: the
+// centred dipole Y = A (-2 m_r, m_th, m_ph) with A = ab0 (R_E / r)^3, |Y|^2,
+// k . Y, and the partials of |Y|^2 and of k . Y along (r, theta, phi).  From
+// dm_r/dth = m_th, dm_th/dth = -m_r, dm_ph/dth = 0, dm_r/dph = sin m_ph,
+// dm_th/dph = cos m_ph, dm_ph/dph = -(sin m_r + cos m_th):
+//   dY/dr = -3 Y / r,  dY/dth = A (-2 m_th, -m_r, 0),
+//   dY/dph = A (-2 sin m_ph, cos m_ph, -(sin m_r + cos m_th)),
+// so d|Y|^2/dx = 2 Y . dY/dx = (-6 |Y|^2 / r, 6 A^2 m_r m_th, 6 A^2 m_r sin m_ph).
+template <typename R>
+struct FieldTerms {
+    R Y[3];     // Y (units of the wave frequency)
+    R YY, kY;   // |Y|^2, k . Y
+    R gYY[3];   // d|Y|^2 / d(r, theta, phi)
+    R gkY[3];   // d(k . Y) / d(r, theta, phi) at fixed k
+    R ir;       // 1 / r
+};
+
+template <typename R>
+__device__ __forceinline__ FieldTerms<R> field_terms(const RayPhys<R> &rp, const StageIn<R> &s) {
+    FieldTerms<R> F;
+    const R kr = s.k[0], kt = s.k[1], kp = s.k[2];
+    const R mx = rp.m[0], my = rp.m[1], mz = rp.m[2];
+    const R mr = mx * s.sth * s.cph + my * s.sth * s.sph + mz * s.cth;
+    const R mt = mx * s.cth * s.cph + my * s.cth * s.sph - mz * s.sth;
+    const R mp = -mx * s.sph + my * s.cph;
+    F.ir = recip(s.r);
+    const R q = rp.R_E * F.ir;
+    const R A = rp.ab0 * q * q * q;
+    F.Y[0] = R(-2) * A * mr;
+    F.Y[1] = A * mt;
+    F.Y[2] = A * mp;
+    const R A2 = A * A;
+    F.YY = A2 * (R(1) + R(3) * mr * mr);  // m is a unit vector
+    F.kY = kr * F.Y[0] + kt * F.Y[1] + kp * F.Y[2];
+    const R smp = s.sth * mp;
+    const R A6mr = R(6) * A2 * mr;
+    F.gYY[0] = R(-6) * F.YY * F.ir;
+    F.gYY[1] = A6mr * mt;
+    F.gYY[2] = A6mr * smp;
+    F.gkY[0] = R(-3) * F.kY * F.ir;
+    F.gkY[1] = A * (R(-2) * kr * mt - kt * mr);
+    F.gkY[2] = A * (R(-2) * kr * smp + kt * s.cth * mp - kp * (s.sth * mr + s.cth * mt));
+    return F;
+}
+
 // Hamiltonian H = (|k|^2 - mu^2)/2 (Eq. 2, k in units of omega/c) and the ray
 // equations (Eq. 1a-1f, with k_phi sin(theta) dphi/dP' in the k_r equation as
 // the canonical momentum p_phi = r sin(theta) k_phi requires).  With G =
@@ -253,9 +332,10 @@ __device__ __forceinline__ void appleton_hartree(R X, R L, R T, int mode, R &mu2
 //   dk_r/dP'   = H_r/G + k_th dtheta + k_ph sin dphi,
 //   dk_th/dP'  = (H_th/G - k_th dr + k_ph r cos dphi) / r,
 //   dk_ph/dP'  = (H_ph/G - k_ph sin dr - k_ph r cos dtheta) / (r sin).
-// mu2_out receives mu^2 at the stage.
+// F holds the field terms of the same stage; mu2_out receives mu^2.
 template <typename R>
-__device__ __forceinline__ void ray_rhs(const RayPhys<R> &rp, const StageIn<R> &s, R dy[6], R *mu2_out) {
+__device__ __forceinline__ void ray_rhs(const RayPhys<R> &rp, const StageIn<R> &s, const FieldTerms<R> &F, R dy[6],
+                                        R *mu2_out) {
     const R kr = s.k[0], kt = s.k[1], kp = s.k[2];
     const R kk = kr * kr + kt * kt + kp * kp;
     R Hr, Ht, Hp, Hk0, Hk1, Hk2, G, mu2;
@@ -270,57 +350,32 @@ __device__ __forceinline__ void ray_rhs(const RayPhys<R> &rp, const StageIn<R> &
         Hk2 = kp;
         G = -kk - s.X;
     } else {
-        // dipole: components of m in the local basis (r, theta, phi)
-        const R mx = rp.m[0], my = rp.m[1], mz = rp.m[2];
-        const R mr = mx * s.sth * s.cph + my * s.sth * s.sph + mz * s.cth;
-        const R mt = mx * s.cth * s.cph + my * s.cth * s.sph - mz * s.sth;
-        const R mp = -mx * s.sph + my * s.cph;
-        const R ir = recip(s.r);
-        const R q = rp.R_E * ir;
-        const R A = rp.ab0 * q * q * q;  // Y = A (-2 m_r, m_th, m_ph)
-        const R Y0 = R(-2) * A * mr, Y1 = A * mt, Y2 = A * mp;
-        const R A2 = A * A;
-        const R YY = A2 * (R(1) + R(3) * mr * mr);  // |Y|^2, m being a unit vector
-        const R kY = kr * Y0 + kt * Y1 + kp * Y2;
         const R ikk = recip(kk);
-        const R L = kY * kY * ikk;
-        R T = YY - L;
+        const R L = F.kY * F.kY * ikk;
+        R T = F.YY - L;
         if (T < R(0)) T = R(0);
-        R F, FX, FL, FT;
-        appleton_hartree<R>(s.X, L, T, rp.mode, F, FX, FL, FT);
-        mu2 = F;
-        // mu^2 = F(X, L, T) with T = Y^2 - L: d/dY^2 = F_T, d/dL|_{Y^2} = F_L - F_T
+        R Fm, FX, FL, FT;
+        appleton_hartree<R>(s.X, L, T, rp.mode, Fm, FX, FL, FT);
+        mu2 = Fm;
+        // mu^2 = F(X, L, T) with T = Y^2 - L: d/dY^2 = F_T, d/dL|_{Y^2} = F_L - F_T;
+        // dL/dx at fixed k = c2 d(k . Y)/dx with c2 = 2 kY / |k|^2
         const R FYL = FL - FT;
-        const R c2 = R(2) * kY * ikk;
-        // Partials of Y along (r, theta, phi), from dm_r/dth = m_th, dm_th/dth = -m_r,
-        // dm_ph/dth = 0, dm_r/dph = sin m_ph, dm_th/dph = cos m_ph,
-        // dm_ph/dph = -(sin m_r + cos m_th):
-        //   dY/dr = -3 Y / r,  dY/dth = A (-2 m_th, -m_r, 0),
-        //   dY/dph = A (-2 sin m_ph, cos m_ph, -(sin m_r + cos m_th)).
-        // Then d|Y|^2/dx = 2 Y . dY/dx = (-6 |Y|^2 / r, 6 A^2 m_r m_th, 6 A^2 m_r sin m_ph)
-        // and dL/dx at fixed k = c2 k . dY/dx.
-        const R smp = s.sth * mp;
-        const R A6mr = R(6) * A2 * mr;
-        const R gY2_0 = R(-6) * YY * ir;
-        const R gY2_1 = A6mr * mt;
-        const R gY2_2 = A6mr * smp;
-        const R gL_0 = R(-3) * c2 * kY * ir;
-        const R gL_1 = c2 * A * (R(-2) * kr * mt - kt * mr);
-        const R gL_2 = c2 * A * (R(-2) * kr * smp + kt * s.cth * mp - kp * (s.sth * mr + s.cth * mt));
-        Hr = R(-0.5) * (FX * s.dX[0] + FT * gY2_0 + FYL * gL_0);
-        Ht = R(-0.5) * (FX * s.dX[1] + FT * gY2_1 + FYL * gL_1);
-        Hp = R(-0.5) * (FX * s.dX[2] + FT * gY2_2 + FYL * gL_2);
+        const R c2 = R(2) * F.kY * ikk;
+        const R cL = FYL * c2;
+        Hr = R(-0.5) * (FX * s.dX[0] + FT * F.gYY[0] + cL * F.gkY[0]);
+        Ht = R(-0.5) * (FX * s.dX[1] + FT * F.gYY[1] + cL * F.gkY[1]);
+        Hp = R(-0.5) * (FX * s.dX[2] + FT * F.gYY[2] + cL * F.gkY[2]);
         // dL/dk_i = (2 kY / |k|^2) (Y_i - (kY / |k|^2) k_i)
-        const R kYn = kY * ikk;
-        const R hf = R(0.5) * FYL * c2;
-        Hk0 = kr - hf * (Y0 - kYn * kr);
-        Hk1 = kt - hf * (Y1 - kYn * kt);
-        Hk2 = kp - hf * (Y2 - kYn * kp);
+        const R kYn = F.kY * ikk;
+        const R hf = R(0.5) * cL;
+        Hk0 = kr - hf * (F.Y[0] - kYn * kr);
+        Hk1 = kt - hf * (F.Y[1] - kYn * kt);
+        Hk2 = kp - hf * (F.Y[2] - kYn * kp);
         // omega dH/domega: X, L and T all scale as omega^-2, |k|^2 as omega^-2
         G = -kk + s.X * FX + L * FL + T * FT;
     }
     const R iG = recip(G);
-    const R ir = recip(s.r);
+    const R ir = F.ir;
     const R irs = ir * recip(s.sth);
     const R dr = -Hk0 * iG;
     const R dt = -Hk1 * iG * ir;

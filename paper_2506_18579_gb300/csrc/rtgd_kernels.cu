@@ -272,7 +272,8 @@ __device__ void rhs64(const GridDev &g, const RayPhys<double> &rp, const double 
         s.dX[1] = -rp.xfac * out[1] * g.inv_dlat * kRad2Deg;
         s.dX[2] = rp.xfac * out[2] * g.inv_dlon * kRad2Deg;
     }
-    ray_rhs<double>(rp, s, dy, mu2);
+    const FieldTerms<double> F = field_terms<double>(rp, s);
+    ray_rhs<double>(rp, s, F, dy, mu2);
 }
 
 __device__ void rk4_step64(const GridDev &g, const RayPhys<double> &rp, const double y[6], const double k1[6],
@@ -629,33 +630,32 @@ __device__ __forceinline__ void two_sum_add(float &hi, float &lo, float d) {
 }
 
 // Stage cell along one axis from base cell i0 and offset coordinate t = t0 +
-// delta * scale; false outside [0, n-1].
+// delta * scale; false outside [0, n-1], and then cell 0 at t = 0, so that the
+// caller can gather from an in-bounds cell without branching.
 __device__ __forceinline__ bool stage_cell(int i0, float t, int n, int &i, float &tt) {
     const float fl = fminf(fmaxf(floorf(t), -1e6f), 1e6f);  // keeps the int sum far from overflow
     int ii = i0 + (int)fl;
     float tr = t - fl;
-    if (!(tr >= 0.0f && tr <= 1.0f)) return false;  // NaN, or an offset beyond the clamp
-    if (ii < 0 || ii > n - 1) return false;
-    if (ii == n - 1) {
-        if (tr != 0.0f) return false;
-        ii = n - 2;
-        tr = 1.0f;
-    }
-    i = ii;
-    tt = tr;
-    return true;
+    const bool last = (ii == n - 1) & (tr == 0.0f);  // the last node: cell n-2 at t = 1
+    // NaN fails the first two tests; an offset beyond the clamp fails them too
+    const bool ok = (tr >= 0.0f) & (tr <= 1.0f) & (ii >= 0) & ((ii < n - 1) | last);
+    ii = last ? n - 2 : ii;
+    tr = last ? 1.0f : tr;
+    i = ok ? ii : 0;
+    tt = ok ? tr : 0.0f;
+    return ok;
 }
 
 // Lat-weights of the rows a = q*4/G .. (q+1)*4/G - 1 handled by lane q of a
 // group of G lanes (G = 1: all four).
-template <int G>
-__device__ __forceinline__ void own_lat_weights(float ta, int q, float wa[4], float da[4], int interp) {
+template <int G, int IP>
+__device__ __forceinline__ void own_lat_weights(float ta, int q, float wa[4], float da[4]) {
     if (G == 1) {
-        interp_weights<float>(ta, wa, da, interp);
+        axis_weights<float, IP>(ta, wa, da);
     } else if (G == 2) {
         const bool hi = q != 0;  // rows 2, 3: nodes j+1, j+2
         float wm1, w0, dm1, d0;
-        gd_half<float>(hi ? 1.0f - ta : ta, wm1, w0, dm1, d0, interp);
+        half_weights<float, IP>(hi ? 1.0f - ta : ta, wm1, w0, dm1, d0);
         wa[0] = hi ? w0 : wm1;
         wa[1] = hi ? wm1 : w0;
         da[0] = hi ? -d0 : dm1;
@@ -663,7 +663,7 @@ __device__ __forceinline__ void own_lat_weights(float ta, int q, float wa[4], fl
     } else {
         const bool hi = q >= 2;
         float wm1, w0, dm1, d0;
-        gd_half<float>(hi ? 1.0f - ta : ta, wm1, w0, dm1, d0, interp);
+        half_weights<float, IP>(hi ? 1.0f - ta : ta, wm1, w0, dm1, d0);
         const bool outer = q == 0 || q == 3;  // nodes j-1, j+2
         wa[0] = outer ? wm1 : w0;
         da[0] = (outer ? dm1 : d0) * (hi ? -1.0f : 1.0f);
@@ -671,10 +671,13 @@ __device__ __forceinline__ void own_lat_weights(float ta, int q, float wa[4], fl
 }
 
 // dy/dP' (float) at base + delta.  STENCIL selects where the 64 samples come
-// from; with G > 1 the G lanes of a group (lane q, shuffle mask gmask) split
-// the 16 sample rows and combine their partial sums with a butterfly, whose
-// every addition is commutative, so all lanes hold bitwise equal results.
-template <int STENCIL, int G>
+// from and IP the interpolant (0 GD, 1 Catmull-Rom); with G > 1 the G lanes
+// of a group (lane q, shuffle mask gmask) split the 16 sample rows and combine
+// their partial sums with a butterfly, whose every addition is commutative,
+// so all lanes hold bitwise equal results.  The body has no branch: the field
+// terms (which do not need Ne) come first and can overlap the sample gathers,
+// and a stage outside the grid gathers from cell 0 and discards the result.
+template <int STENCIL, int G, int IP>
 __device__ __forceinline__ void rhs_mixed(const GridDev &g, const RayPhys<float> &rp, const Base32 &b,
                                           const float d[6], float dy[6], float *mu2, int q, unsigned gmask) {
     StageIn<float> s;
@@ -684,23 +687,27 @@ __device__ __forceinline__ void rhs_mixed(const GridDev &g, const RayPhys<float>
     s.k[0] = b.k[0] + d[3];
     s.k[1] = b.k[1] + d[4];
     s.k[2] = b.k[2] + d[5];
-    s.X = 0.0f;
-    s.dX[0] = s.dX[1] = s.dX[2] = 0.0f;
+    const FieldTerms<float> F = field_terms<float>(rp, s);
     int ia, ib, ic;
     float ta, tb, tc;
-    if (stage_cell(b.ia, b.ta + g.sa * d[1], g.n_lat, ia, ta) && stage_cell(b.ib, b.tb + g.sb * d[2], g.n_lon, ib, tb) &&
-        stage_cell(b.ic, b.tc + g.sc * d[0], g.n_alt, ic, tc)) {
-        float wa[4], da[4], wb[4], db[4], wc[4], dc[4], out[4], ref;
-        constexpr int NA = 4 / G;
-        const int a0 = q * NA;
-        own_lat_weights<G>(ta, q, wa, da, g.interp);
-        interp_weights<float>(tb, wb, db, g.interp);
-        interp_weights<float>(tc, wc, dc, g.interp);
-        if (STENCIL == RT_STENCIL_QUAD) {
-            // quad (pi, pj, k): 4 samples of cell k in padded row (pi, pj); node i-1 -> padded i
-            const long long sj = g.q_alt, si = (long long)(g.n_lon + 2) * g.q_alt;
-            const float4 *qp = g.quad + (long long)ia * si + (long long)ib * sj + ic;
-            ref = __ldg(qp + si + sj).y;  // node (ia, ib, ic)
+    const bool in_a = stage_cell(b.ia, b.ta + g.sa * d[1], g.n_lat, ia, ta);
+    const bool in_b = stage_cell(b.ib, b.tb + g.sb * d[2], g.n_lon, ib, tb);
+    const bool in_c = stage_cell(b.ic, b.tc + g.sc * d[0], g.n_alt, ic, tc);
+    const bool inside = in_a & in_b & in_c;
+    ia = inside ? ia : 0;
+    ib = inside ? ib : 0;
+    ic = inside ? ic : 0;
+    float wa[4], da[4], wb[4], db[4], wc[4], dc[4], out[4], ref;
+    constexpr int NA = 4 / G;
+    const int a0 = q * NA;
+    own_lat_weights<G, IP>(ta, q, wa, da);
+    axis_weights<float, IP>(tb, wb, db);
+    axis_weights<float, IP>(tc, wc, dc);
+    if (STENCIL == RT_STENCIL_QUAD) {
+        // quad (pi, pj, k): 4 samples of cell k in padded row (pi, pj); node i-1 -> padded i
+        const long long sj = g.q_alt, si = (long long)(g.n_lon + 2) * g.q_alt;
+        const float4 *qp = g.quad + (long long)ia * si + (long long)ib * sj + ic;
+        ref = __ldg(qp + si + sj).y;  // node (ia, ib, ic)
 #define RTGD_ROWQ(a, b, u0, u1, u2, u3)                    \
     {                                                      \
         const float4 v_ = __ldg(qp + (a) * si + (b) * sj); \
@@ -709,12 +716,12 @@ __device__ __forceinline__ void rhs_mixed(const GridDev &g, const RayPhys<float>
         u2 = v_.z;                                        \
         u3 = v_.w;                                        \
     }
-            RTGD_CONTRACT(float, RTGD_ROWQ, ref, a0, NA, wa, da, wb, db, wc, dc, out);
+        RTGD_CONTRACT(float, RTGD_ROWQ, ref, a0, NA, wa, da, wb, db, wc, dc, out);
 #undef RTGD_ROWQ
-        } else if (STENCIL == RT_STENCIL_TABLE) {
-            const long long cell = ((long long)ia * (g.n_lon - 1) + ib) * (g.n_alt - 1) + ic;
-            const float4 *qp = g.table + cell * 16;
-            ref = __ldg(qp + 5).y;  // node (ia, ib, ic)
+    } else if (STENCIL == RT_STENCIL_TABLE) {
+        const long long cell = ((long long)ia * (g.n_lon - 1) + ib) * (g.n_alt - 1) + ic;
+        const float4 *qp = g.table + cell * 16;
+        ref = __ldg(qp + 5).y;  // node (ia, ib, ic)
 #define RTGD_ROWT(a, b, u0, u1, u2, u3)              \
     {                                                \
         const float4 v_ = __ldg(qp + (a) * 4 + (b)); \
@@ -723,12 +730,12 @@ __device__ __forceinline__ void rhs_mixed(const GridDev &g, const RayPhys<float>
         u2 = v_.z;                                  \
         u3 = v_.w;                                  \
     }
-            RTGD_CONTRACT(float, RTGD_ROWT, ref, a0, NA, wa, da, wb, db, wc, dc, out);
+        RTGD_CONTRACT(float, RTGD_ROWT, ref, a0, NA, wa, da, wb, db, wc, dc, out);
 #undef RTGD_ROWT
-        } else {
-            const long long sj = g.p_alt, si = (long long)g.p_lon * g.p_alt;
-            const float *p = g.pad32 + (long long)ia * si + (long long)ib * sj + ic;
-            ref = __ldg(p + si + sj + 1);  // node (ia, ib, ic)
+    } else {
+        const long long sj = g.p_alt, si = (long long)g.p_lon * g.p_alt;
+        const float *p = g.pad32 + (long long)ia * si + (long long)ib * sj + ic;
+        ref = __ldg(p + si + sj + 1);  // node (ia, ib, ic)
 #define RTGD_ROWG(a, b, u0, u1, u2, u3)            \
     {                                              \
         const float *p_ = p + (a) * si + (b) * sj; \
@@ -737,23 +744,24 @@ __device__ __forceinline__ void rhs_mixed(const GridDev &g, const RayPhys<float>
         u2 = __ldg(p_ + 2);                        \
         u3 = __ldg(p_ + 3);                        \
     }
-            RTGD_CONTRACT(float, RTGD_ROWG, ref, a0, NA, wa, da, wb, db, wc, dc, out);
+        RTGD_CONTRACT(float, RTGD_ROWG, ref, a0, NA, wa, da, wb, db, wc, dc, out);
 #undef RTGD_ROWG
-        }
-        if (G > 1) {
-#pragma unroll
-            for (int o = 1; o < G; o <<= 1) {
-#pragma unroll
-                for (int i = 0; i < 4; ++i) out[i] += __shfl_xor_sync(gmask, out[i], o);
-            }
-        }
-        out[0] += ref;
-        s.X = rp.xfac * out[0];
-        s.dX[0] = rp.xfac * out[3] * g.sc;
-        s.dX[1] = rp.xfac * out[1] * g.sa;
-        s.dX[2] = rp.xfac * out[2] * g.sb;
     }
-    ray_rhs<float>(rp, s, dy, mu2);
+    if (G > 1) {
+#pragma unroll
+        for (int o = 1; o < G; o <<= 1) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) out[i] += __shfl_xor_sync(gmask, out[i], o);
+        }
+    }
+    out[0] += ref;
+    // Ne = 0 outside the grid box (selects, so that samples gathered there,
+    // whatever they hold, never reach the result)
+    s.X = inside ? rp.xfac * out[0] : 0.0f;
+    s.dX[0] = inside ? rp.xfac * out[3] * g.sc : 0.0f;
+    s.dX[1] = inside ? rp.xfac * out[1] * g.sa : 0.0f;
+    s.dX[2] = inside ? rp.xfac * out[2] * g.sb : 0.0f;
+    ray_rhs<float>(rp, s, F, dy, mu2);
 }
 
 // Butcher tables in "shifted accumulator" form.  After stage s produced k_s,
@@ -958,13 +966,13 @@ __device__ __forceinline__ bool lane_next_attempt(Lane &L, const FanDev &f) {
 
 // The launch evaluation: mu^2 at the transmitter for the launch direction,
 // then |k| = mu.  Returns true when the ray has finished (status set).
-template <int STENCIL, int G>
+template <int STENCIL, int G, int IP>
 __device__ bool lane_launch(Lane &L, const GridDev &g, const FanDev &f, int q, unsigned gmask) {
     const RayPhys<float> rp = lane_phys(g, L);
     float d[6], ks[6], mu2;
 #pragma unroll
     for (int c = 0; c < 6; ++c) d[c] = 0.0f;
-    rhs_mixed<STENCIL, G>(g, rp, L.b, d, ks, &mu2, q, gmask);
+    rhs_mixed<STENCIL, G, IP>(g, rp, L.b, d, ks, &mu2, q, gmask);
     ++L.n_ev;
     L.launch = false;
     if (!(mu2 > 0.0f)) {
@@ -990,7 +998,7 @@ __device__ bool lane_launch(Lane &L, const GridDev &g, const FanDev &f, int q, u
 // and the Butcher coefficients are broadcast reads.  Stage 0 is evaluated
 // only when k1 at the current state is not yet known (after a rejected
 // attempt or during the landing solve it is).
-template <int STENCIL, int G>
+template <int STENCIL, int G, int IP>
 __device__ __forceinline__ void lane_attempt(Lane &L, const GridDev &g, const FanDev &f, const Tableau &T, int q,
                                              unsigned gmask) {
     const RayPhys<float> rp = lane_phys(g, L);
@@ -998,7 +1006,7 @@ __device__ __forceinline__ void lane_attempt(Lane &L, const GridDev &g, const Fa
     if (!L.k1_valid) {
 #pragma unroll
         for (int c = 0; c < 6; ++c) d[c] = 0.0f;
-        rhs_mixed<STENCIL, G>(g, rp, L.b, d, L.k1, nullptr, q, gmask);
+        rhs_mixed<STENCIL, G, IP>(g, rp, L.b, d, L.k1, nullptr, q, gmask);
         ++L.n_ev;
         L.k1_valid = true;
         if (L.have_prev && L.dr_prev > 0.0f && L.k1[0] <= 0.0f) {
@@ -1013,7 +1021,7 @@ __device__ __forceinline__ void lane_attempt(Lane &L, const GridDev &g, const Fa
     for (int s = 1; s < T.ns; ++s) {
 #pragma unroll
         for (int c = 0; c < 6; ++c) d[c] = L.hs * L.acc[0][c];
-        rhs_mixed<STENCIL, G>(g, rp, L.b, d, ks, nullptr, q, gmask);
+        rhs_mixed<STENCIL, G, IP>(g, rp, L.b, d, ks, nullptr, q, gmask);
         ++L.n_ev;
         accumulate_next(L, T, s, ks);
     }
@@ -1163,7 +1171,7 @@ __device__ __forceinline__ unsigned group_mask(int lane) {
 
 // One ray per thread group of G lanes; each group loops attempt by attempt
 // until its ray ends.
-template <int STENCIL, int G>
+template <int STENCIL, int G, int IP>
 __global__ void __launch_bounds__(128, 3) trace_mixed_plain_kernel(GridDev g, FanDev f, rt_ray_result *__restrict__ out) {
     __shared__ Tableau T;
     load_tableau(T, f.integrator);
@@ -1175,11 +1183,11 @@ __global__ void __launch_bounds__(128, 3) trace_mixed_plain_kernel(GridDev g, Fa
     Lane L;
     L.active = true;
     lane_begin_ray(L, g, f, claim_to_ray(f, id));
-    bool done = lane_launch<STENCIL, G>(L, g, f, q, gmask);
+    bool done = lane_launch<STENCIL, G, IP>(L, g, f, q, gmask);
     // bounded: every attempt counts against max_steps, so max_steps + 1 attempts end every ray
     const long long max_att = (long long)f.max_steps + 2;
     for (long long it = 0; it < max_att && !done; ++it) {
-        lane_attempt<STENCIL, G>(L, g, f, T, q, gmask);
+        lane_attempt<STENCIL, G, IP>(L, g, f, T, q, gmask);
         done = lane_end_attempt(L, g, f);
     }
     if (!done) L.status = RT_RAY_MAX_STEPS;
@@ -1189,7 +1197,7 @@ __global__ void __launch_bounds__(128, 3) trace_mixed_plain_kernel(GridDev g, Fa
 // Persistent kernel: resident blocks; every warp keeps its 32 lanes busy by
 // claiming new rays (one atomicAdd per warp for all idle lanes) as rays end.
 // Claims happen between attempts, where all lanes of the warp meet.
-template <int STENCIL, int G>
+template <int STENCIL, int G, int IP>
 __global__ void __launch_bounds__(128, 3) trace_mixed_persistent_kernel(GridDev g, FanDev f,
                                                                      rt_ray_result *__restrict__ out,
                                                                      unsigned long long *__restrict__ counter) {
@@ -1221,7 +1229,7 @@ __global__ void __launch_bounds__(128, 3) trace_mixed_persistent_kernel(GridDev 
                 if (c < (unsigned long long)n) {
                     L.active = true;
                     lane_begin_ray(L, g, f, claim_to_ray(f, (long long)c));
-                    if (lane_launch<STENCIL, G>(L, g, f, q, gmask)) lane_finish(L, g, f, out, q == 0);
+                    if (lane_launch<STENCIL, G, IP>(L, g, f, q, gmask)) lane_finish(L, g, f, out, q == 0);
                 }
             }
         }
@@ -1234,7 +1242,7 @@ __global__ void __launch_bounds__(128, 3) trace_mixed_persistent_kernel(GridDev 
             break;
         }
         if (L.active) {
-            lane_attempt<STENCIL, G>(L, g, f, T, q, gmask);
+            lane_attempt<STENCIL, G, IP>(L, g, f, T, q, gmask);
             if (lane_end_attempt(L, g, f)) lane_finish(L, g, f, out, q == 0);
         }
     }
@@ -1316,9 +1324,15 @@ __global__ void eval_rhs_kernel(GridDev g, const double *__restrict__ ys, double
         Base32 b;
         base_from_state(g, y, b);
         float d[6] = {0, 0, 0, 0, 0, 0}, dyf[6], m2;
-        if (stencil == RT_STENCIL_TABLE) rhs_mixed<RT_STENCIL_TABLE, 1>(g, rp, b, d, dyf, &m2, 0, 0u);
-        else if (stencil == RT_STENCIL_GATHER) rhs_mixed<RT_STENCIL_GATHER, 1>(g, rp, b, d, dyf, &m2, 0, 0u);
-        else rhs_mixed<RT_STENCIL_QUAD, 1>(g, rp, b, d, dyf, &m2, 0, 0u);
+        if (g.interp == 1) {
+            if (stencil == RT_STENCIL_TABLE) rhs_mixed<RT_STENCIL_TABLE, 1, 1>(g, rp, b, d, dyf, &m2, 0, 0u);
+            else if (stencil == RT_STENCIL_GATHER) rhs_mixed<RT_STENCIL_GATHER, 1, 1>(g, rp, b, d, dyf, &m2, 0, 0u);
+            else rhs_mixed<RT_STENCIL_QUAD, 1, 1>(g, rp, b, d, dyf, &m2, 0, 0u);
+        } else {
+            if (stencil == RT_STENCIL_TABLE) rhs_mixed<RT_STENCIL_TABLE, 1, 0>(g, rp, b, d, dyf, &m2, 0, 0u);
+            else if (stencil == RT_STENCIL_GATHER) rhs_mixed<RT_STENCIL_GATHER, 1, 0>(g, rp, b, d, dyf, &m2, 0, 0u);
+            else rhs_mixed<RT_STENCIL_QUAD, 1, 0>(g, rp, b, d, dyf, &m2, 0, 0u);
+        }
 #pragma unroll
         for (int c = 0; c < 6; ++c) dy[c] = dyf[c];
         mu2 = m2;
@@ -1384,16 +1398,23 @@ cudaError_t upload_tableaus() {
     return cudaMemcpyToSymbol(c_pow2q, q, sizeof(q));
 }
 
+template <int STENCIL, int G, int IP>
+static cudaError_t launch_mixed_gi(const GridDev &g, const FanDev &f, rt_ray_result *out,
+                                   unsigned long long *counter, const LaunchPlan &lp, cudaStream_t st) {
+    if (lp.kernel == RT_KERNEL_PERSISTENT) {
+        trace_mixed_persistent_kernel<STENCIL, G, IP><<<lp.blocks, lp.threads, 0, st>>>(g, f, out, counter);
+    } else {
+        const long long blocks = (f.n_rays * G + lp.threads - 1) / lp.threads;
+        trace_mixed_plain_kernel<STENCIL, G, IP><<<(unsigned)blocks, lp.threads, 0, st>>>(g, f, out);
+    }
+    return cudaGetLastError();
+}
+
 template <int STENCIL, int G>
 static cudaError_t launch_mixed_g(const GridDev &g, const FanDev &f, rt_ray_result *out,
                                   unsigned long long *counter, const LaunchPlan &lp, cudaStream_t st) {
-    if (lp.kernel == RT_KERNEL_PERSISTENT) {
-        trace_mixed_persistent_kernel<STENCIL, G><<<lp.blocks, lp.threads, 0, st>>>(g, f, out, counter);
-    } else {
-        const long long blocks = (f.n_rays * G + lp.threads - 1) / lp.threads;
-        trace_mixed_plain_kernel<STENCIL, G><<<(unsigned)blocks, lp.threads, 0, st>>>(g, f, out);
-    }
-    return cudaGetLastError();
+    return g.interp == 1 ? launch_mixed_gi<STENCIL, G, 1>(g, f, out, counter, lp, st)
+                         : launch_mixed_gi<STENCIL, G, 0>(g, f, out, counter, lp, st);
 }
 
 template <int STENCIL>
@@ -1427,13 +1448,13 @@ static cudaError_t occupancy_s(int lanes, int threads, int *blocks_per_sm) {
     switch (lanes) {
         case 2:
             return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                blocks_per_sm, trace_mixed_persistent_kernel<STENCIL, 2>, threads, 0);
+                blocks_per_sm, trace_mixed_persistent_kernel<STENCIL, 2, 0>, threads, 0);
         case 4:
             return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                blocks_per_sm, trace_mixed_persistent_kernel<STENCIL, 4>, threads, 0);
+                blocks_per_sm, trace_mixed_persistent_kernel<STENCIL, 4, 0>, threads, 0);
         default:
             return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                blocks_per_sm, trace_mixed_persistent_kernel<STENCIL, 1>, threads, 0);
+                blocks_per_sm, trace_mixed_persistent_kernel<STENCIL, 1, 0>, threads, 0);
     }
 }
 
