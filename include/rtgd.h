@@ -188,12 +188,13 @@ enum { RT_KERNEL_AUTO = 0, RT_KERNEL_PLAIN = 1, RT_KERNEL_PERSISTENT = 2 };
 enum { RT_STENCIL_AUTO = 0, RT_STENCIL_GATHER = 1, RT_STENCIL_QUAD = 2, RT_STENCIL_TABLE = 3 };
 enum { RT_ORDER_CANONICAL = 0, RT_ORDER_ELEVATION_FASTEST = 1 };
 typedef struct rt_launch_config {
-    int32_t kernel;        /* RT_KERNEL_*: PLAIN = one thread per ray; PERSISTENT = one resident
-                              grid whose lanes claim rays from an atomic counter (mixed only) */
+    int32_t kernel;        /* RT_KERNEL_*: PLAIN = one lane group per ray, one launch-wide grid of
+                              groups (the default); PERSISTENT = one resident grid whose lane
+                              groups claim rays from an atomic counter (mixed only) */
     int32_t stencil;       /* RT_STENCIL_*: where the mixed path reads the 4x4x4 samples:
                               GATHER = padded FP32 grid, QUAD = 4 consecutive altitude samples
                               per float4, TABLE = per-cell table (needs RT_GRID_TABLE) */
-    int32_t block_threads; /* 0 = default; a multiple of 32 in [32, 1024] */
+    int32_t block_threads; /* 0 = default (128); a multiple of 32 in [32, 128] */
     int32_t order;         /* RT_ORDER_*: order in which the persistent kernel claims rays */
     int32_t blocks_per_sm; /* persistent kernel: resident blocks per SM (0 = occupancy limit) */
     int32_t lanes_per_ray; /* mixed path: 1, 2 or 4 lanes share one ray (they split the 16 sample
@@ -237,11 +238,15 @@ rt_err rt_trace_device(const rt_grid *grid, const rt_fan_desc *fan, rt_ray_resul
 rt_err rt_trace_device_noalloc(const rt_grid *grid, const rt_fan_desc *fan, rt_ray_result *out_dev,
                                size_t out_len, const rt_launch_config *cfg, void *stream);
 
-/* Autotuner: times the candidate launch configurations for this grid and fan
- * shape on `stream` (each candidate on a seeded subsample of at most
- * max_rays rays; 0 = 4096) and returns the fastest in *best and its time in
- * *best_ms.  Blocking.  Results are also cached inside the library, keyed by
- * grid and fan shape, and used by later RT_KERNEL_AUTO calls. */
+/* Autotuner: times the candidate launch configurations (kernel x stencil x
+ * claim order x lanes per ray) for this grid and fan shape on `stream`, each
+ * candidate on a strided sub-fan of at most max_rays rays (0 = 65536), and
+ * returns the fastest in *best and its time in *best_ms.  A fan of at least
+ * two waves of resident lanes at one lane per ray is issue-bound: it tries
+ * one lane per ray only, on a sub-fan of at least four such waves (a smaller
+ * sub-fan would reward the latency of its slowest rays instead).  Blocking.  Results are also cached inside the
+ * library, keyed by grid, integrator and fan size, and used by later calls
+ * whose kernel and stencil are both AUTO; rt_grid_destroy drops them. */
 rt_err rt_tune(const rt_grid *grid, const rt_fan_desc *fan, size_t max_rays, void *stream,
                rt_launch_config *best, float *best_ms);
 

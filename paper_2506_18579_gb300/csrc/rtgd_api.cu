@@ -192,7 +192,7 @@ rt_err make_plan(const rt_grid *grid, const rt_fan_desc *fan, size_t n_rays, con
         auto it = g_tuned.find(std::make_tuple(grid, fan->integrator, ray_bucket(n_rays)));
         if (it != g_tuned.end()) c = it->second;
     }
-    if (c.kernel == RT_KERNEL_AUTO) c.kernel = fan->precision == RT_MIXED ? RT_KERNEL_PERSISTENT : RT_KERNEL_PLAIN;
+    if (c.kernel == RT_KERNEL_AUTO) c.kernel = RT_KERNEL_PLAIN;  // measured faster on GB300 for small and large fans
     if (fan->precision == RT_FP64 && c.kernel != RT_KERNEL_PLAIN)
         return fail(RT_EINVAL, "the FP64 path runs the plain one-thread-per-ray kernel only");
     if (c.stencil == RT_STENCIL_AUTO) c.stencil = RT_STENCIL_QUAD;
@@ -494,6 +494,16 @@ rt_err rt_tune(const rt_grid *grid, const rt_fan_desc *fan, size_t max_rays, voi
     if ((r = ensure_device(nullptr)) != RT_OK) return r;
     if (max_rays == 0) max_rays = 65536;
     cudaStream_t st = (cudaStream_t)stream;
+    // A fan of at least two waves of resident lanes at one lane per ray is
+    // bound by issue throughput, where splitting a ray over lanes only
+    // duplicates work, and a sub-fan of about one wave would instead reward
+    // the latency of its slowest rays.  Such fans are timed on a sub-fan of at
+    // least four waves, with one lane per ray.
+    int occ = 0;
+    CUDA_TRY(persistent_occupancy(RT_STENCIL_QUAD, 1, 128, &occ));
+    const long long resident = (long long)props(grid->device).sms * std::max(occ, 1) * 128;
+    const bool throughput = fan->precision == RT_MIXED && (long long)fan_rays(fan) >= 2 * resident;
+    if (throughput) max_rays = std::max(max_rays, (size_t)(4 * resident));
     // strided sub-fan with at most max_rays rays (every k-th elevation, azimuth, frequency)
     std::vector<double> fr(fan->freq_mhz, fan->freq_mhz + fan->n_freq), el(fan->el_deg, fan->el_deg + fan->n_el),
         az(fan->az_deg, fan->az_deg + fan->n_az);
@@ -528,6 +538,7 @@ rt_err rt_tune(const rt_grid *grid, const rt_fan_desc *fan, size_t max_rays, voi
             for (int stencil : {RT_STENCIL_GATHER, RT_STENCIL_QUAD, RT_STENCIL_TABLE})
                 for (int order : {RT_ORDER_CANONICAL, RT_ORDER_ELEVATION_FASTEST})
                     for (int lanes : {1, 2, 4}) {
+                        if (throughput && lanes > 1) continue;
                         if (stencil == RT_STENCIL_TABLE && !grid->table) continue;
                         c.kernel = kernel;
                         c.stencil = stencil;

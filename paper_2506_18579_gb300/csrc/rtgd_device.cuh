@@ -193,6 +193,11 @@ __device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double fsqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float fsqrt(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
 
+// a / b: correctly rounded in double; in float the fast division (MUFU.RCP
+// based, 2 ulp, no special-case branch) for the step-control arithmetic.
+__device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+
 // Cell index and local coordinate along one axis; false outside [0, n-1].
 template <typename R>
 __device__ __forceinline__ bool cell_coord(R x, int n, int &i, R &t) {
@@ -249,13 +254,17 @@ template <typename R>
 __device__ __forceinline__ void appleton_hartree(R X, R L, R T, int mode, R &mu2, R &FX, R &FL, R &FT) {
     const R u = R(1) - X;
     const R S = fsqrt(T * T + R(4) * L * u * u);
-    const R iS = recip(S);
     if (mode > 0) {
+        // one reciprocal gives 1/S, 1/W and 1/(1 + g) = W/V with V = W + 2 L u
         const R W = S + T;
-        const R iW = recip(W);
+        const R V = W + R(2) * L * u;
+        const R SW = S * W;
+        const R m = recip(SW * V);
+        const R iS = W * V * m;
+        const R iW = S * V * m;
         const R g = R(2) * L * u * iW;
         const R opg = R(1) + g;
-        const R iopg = recip(opg);
+        const R iopg = SW * W * m;
         const R gX = R(2) * L * (R(4) * L * u * u * iS - W) * iW * iW;
         const R gL = R(2) * u * iW - R(4) * L * u * u * u * iS * iW * iW;
         const R gT = -g * iS;
@@ -266,11 +275,13 @@ __device__ __forceinline__ void appleton_hartree(R X, R L, R T, int mode, R &mu2
         FT = X * gT * i2;
     } else {
         const R D = R(2) * u - T - S;
+        const R m = recip(S * D);  // 1/S and 1/D from one reciprocal
+        const R iS = D * m;
+        const R iD = S * m;
         const R N = R(2) * X * u;
         const R SX = R(-4) * L * u * iS;
         const R SL = R(2) * u * u * iS;
         const R ST = T * iS;
-        const R iD = recip(D);
         const R iD2 = iD * iD;
         mu2 = R(1) - N * iD;
         FX = (N * (R(-2) - SX) - (R(2) - R(4) * X) * D) * iD2;

@@ -331,7 +331,7 @@ template <typename R>
 __device__ __forceinline__ R rkf45_err(R r, R sth, R kmag, const R e[6], R rtol, R atol) {
     const R pos = fmax(fabs(e[0]), fmax(r * fabs(e[1]), r * sth * fabs(e[2])));
     const R kerr = fmax(fabs(e[3]), fmax(fabs(e[4]), fabs(e[5])));
-    return fmax(pos / (atol + rtol * r), kerr / (rtol * fmax(kmag, R(1e-3))));
+    return fmax(fdiv(pos, atol + rtol * r), fdiv(kerr, rtol * fmax(kmag, R(1e-3))));
 }
 
 // Step-size factor: 0.9 err^(-1/5) limited to [0.2, 5], rounded down to a
@@ -633,8 +633,17 @@ __device__ __forceinline__ void two_sum_add(float &hi, float &lo, float d) {
 // delta * scale; false outside [0, n-1], and then cell 0 at t = 0, so that the
 // caller can gather from an in-bounds cell without branching.
 __device__ __forceinline__ bool stage_cell(int i0, float t, int n, int &i, float &tt) {
-    const float fl = fminf(fmaxf(floorf(t), -1e6f), 1e6f);  // keeps the int sum far from overflow
-    int ii = i0 + (int)fl;
+    // floor of t clamped to +-1e6 (keeps the int sum far from overflow) without
+    // conversion instructions: adding 1.5 * 2^23 rounds to the nearest integer,
+    // which sits in the low mantissa bits; one less if that rounded up.  A NaN
+    // t clamps to -1e6 and then fails the fraction test below.
+    const float magic = 12582912.0f;
+    const float tc = fminf(fmaxf(t, -1e6f), 1e6f);
+    const float big = tc + magic;
+    const float near = big - magic;
+    const bool up = near > tc;
+    const float fl = up ? near - 1.0f : near;
+    int ii = i0 + (__float_as_int(big) - __float_as_int(magic)) - (up ? 1 : 0);
     float tr = t - fl;
     const bool last = (ii == n - 1) & (tr == 0.0f);  // the last node: cell n-2 at t = 1
     // NaN fails the first two tests; an offset beyond the clamp fails them too
@@ -805,12 +814,12 @@ __device__ __forceinline__ float face_axis_f(int i, float t, int n, float v) {
     if (v > 0.0f) {
         int F = i + 1;
         if (F < 0) F = 0;
-        return F <= n - 1 ? ((float)(F - i) - t) / v : INFINITY;
+        return F <= n - 1 ? fdiv((float)(F - i) - t, v) : INFINITY;
     }
     if (v < 0.0f) {
         int F = t > 0.0f ? i : i - 1;
         if (F > n - 1) F = n - 1;
-        return F >= 0 ? ((float)(F - i) - t) / v : INFINITY;
+        return F >= 0 ? fdiv((float)(F - i) - t, v) : INFINITY;
     }
     return INFINITY;
 }
@@ -1080,7 +1089,7 @@ __device__ bool lane_end_attempt(Lane &L, const GridDev &g, const FanDev &f) {
     }
     float h_next = L.h;
     if (f.integrator == RT_RKF45) {
-        const float kmag = sqrtf(L.b.k[0] * L.b.k[0] + L.b.k[1] * L.b.k[1] + L.b.k[2] * L.b.k[2]);
+        const float kmag = fsqrt(L.b.k[0] * L.b.k[0] + L.b.k[1] * L.b.k[1] + L.b.k[2] * L.b.k[2]);
         const float err = rkf45_err<float>(L.b.r, L.b.sth, kmag, ef, f.rtol_f, f.atol_f);
         const float fac = step_factor_f(err);
         // the nominal step changes only by quantised factors of itself

@@ -253,6 +253,25 @@ def test_device_output_and_tuner():
     assert np.array_equal(tuned["status"], host["status"])
 
 
+def test_tuner_keeps_one_lane_per_ray_for_large_fans():
+    """A fan of many waves of resident lanes is issue-bound: the tuner must
+    not split rays over lanes there (it tries one lane per ray only); a fan
+    smaller than the GPU may get more lanes."""
+    w = wl.config1()
+    g = rt.Grid(w.grid, w.ne)
+    big = w.fan.replace(freq_mhz=np.linspace(6.0, 14.0, 16), el_deg=np.linspace(5.0, 50.0, 100),
+                        az_deg=np.linspace(0.0, 351.0, 40), modes=wl.MODE_O | wl.MODE_X, h_km=2.0)
+    fan = rt.Fan(big, rt.RT_MIXED)
+    assert fan.n_rays == 128000
+    best, ms = rt.rt_tune(g, fan, max_rays=16384)
+    assert ms > 0 and best.lanes_per_ray == 1
+    small = rt.Fan(w.fan.replace(h_km=2.0), rt.RT_MIXED)  # 16 rays
+    best_s, _ = rt.rt_tune(g, small)
+    assert best_s.lanes_per_ray in (1, 2, 4)
+    res = rt.rt_trace(g, fan)  # the cached choice traces the whole fan
+    assert np.all(res["status"] != rt.RT_RAY_NOT_RUN)
+
+
 def test_catmull_rom_option_matches_oracle(orc):
     """The comparison interpolant (Eq. 6-9) as a grid option: RHS and whole
     rays against the oracle's Catmull-Rom, FP64 (1e-6 km) and mixed."""
