@@ -63,12 +63,16 @@ def parse_args():
     p.add_argument("--threads", type=int, default=128)
     p.add_argument("--lanes", type=int, default=0, choices=[0, 1, 2, 4],
                    help="lanes per ray with --kernel (0 = the library's choice)")
+    p.add_argument("--workload", choices=["c2", "c4"], default="c2",
+                   help="fan for the --profile and --one-ray modes: c2 = the anisotropic 24,840-ray fan "
+                        "(the benchmark's workload), c4 = the 495,122-ray ionogram-synthesis batch")
     p.add_argument("--one-ray", type=int, default=None,
                    help="latency mode: trace only this canonical ray of the fan (alone) --steps times "
                         "and print its time per stage evaluation")
     p.add_argument("--profile", action="store_true",
                    help="warm-up launches then one launch, nothing else (for ncu captures)")
-    p.add_argument("--cpu-sample", type=int, default=512)
+    p.add_argument("--cpu-sample", type=int, default=0,
+                   help="rays of the fan the CPU oracle baseline traces (0 = the whole fan)")
     p.add_argument("--serve-seconds", type=float, default=4.0,
                    help="seconds of Poisson arrivals per offered load in the serving section (0 = skip)")
     p.add_argument("--no-batch", action="store_true",
@@ -149,20 +153,32 @@ def combine_ranks(mean_ms, n_rays, world):
     return mean_ms, n_rays * world / (mean_ms / 1e3)
 
 
-def cpu_oracle_rate(workload, n_sample, seed=1234):
-    """The FP64 oracle as it stands, on all host cores, over a seeded sample."""
+def cpu_oracle_rate(workload, n_sample, seed=1234, single_core_rays=128):
+    """The FP64 oracle as it stands on the host cores: all cores over a seeded
+    sample of the fan (n_sample <= 0 or >= the fan: the whole fan, about 10 s
+    on 16 Arm cores), and one core over the first rays of that sample."""
     from oracle import oracle
     oracle.build()
     g = oracle.Grid(workload.grid, workload.ne)
-    idx = np.sort(np.random.default_rng(seed).choice(workload.fan.n_rays, n_sample, replace=False))
+    n_all = workload.fan.n_rays
+    if n_sample <= 0 or n_sample >= n_all:
+        idx, what = np.arange(n_all), "the whole %d-ray fan" % n_all
+    else:
+        idx = np.sort(np.random.default_rng(seed).choice(n_all, n_sample, replace=False))
+        what = "%d seeded rays of the %d-ray fan" % (n_sample, n_all)
     cores = os.cpu_count() or 1
     t0 = time.perf_counter()
     res = oracle.trace_fan(g, workload.fan, indices=idx, n_threads=cores)
     dt = time.perf_counter() - t0
-    return dict(value=n_sample / dt, unit="rays/s", cores=cores, kind="oracle",
-                sample="%d seeded rays of the %d-ray fan (FP64 CPU oracle, %d threads)"
-                       % (n_sample, workload.fan.n_rays, cores),
-                ray_steps_per_s=float(res["n_steps"].sum()) / dt, seconds=dt)
+    one = idx[:single_core_rays]
+    t1 = time.perf_counter()
+    res1 = oracle.trace_fan(g, workload.fan, indices=one, n_threads=1)
+    dt1 = time.perf_counter() - t1
+    return dict(value=len(idx) / dt, unit="rays/s", cores=cores, kind="oracle",
+                sample="%s (FP64 CPU oracle, %d threads)" % (what, cores),
+                ray_steps_per_s=float(res["n_steps"].sum()) / dt, seconds=dt,
+                single_core={"value": len(one) / dt1, "unit": "rays/s", "rays": len(one), "seconds": dt1,
+                             "ray_steps_per_s": float(res1["n_steps"].sum()) / dt1})
 
 
 def near_boundary(res, fan):
@@ -228,8 +244,10 @@ def run_ours(args):
     from paper_2506_18579_gb300 import workloads as wl
 
     rtbuild.build()
-    w = wl.config2()
-    spec = w.fan.replace(rtol=args.rtol)
+    if args.workload == "c4" and not (args.profile or args.one_ray is not None):
+        raise SystemExit("--workload c4 is for the --profile and --one-ray modes (the batch section times it)")
+    w = wl.config2() if args.workload == "c2" else wl.config4()
+    spec = w.fan.replace(rtol=args.rtol) if args.workload == "c2" else w.fan
     prec = rt.RT_MIXED if args.precision == "mixed" else rt.RT_FP64
     grid = rt.Grid(w.grid, w.ne, table=(prec == rt.RT_MIXED and
                                         (args.kernel is None or args.stencil == "table")))
