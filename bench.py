@@ -43,9 +43,35 @@ FLOP_PER_EVAL = {"mixed": 1000.0, "fp64": 910.0}
 # Grid samples one stage evaluation reads: 64 samples (16 rows of 4) plus the
 # reference node, FP32 in the mixed path and FP64 in the all-FP64 path.
 GATHER_BYTES = {"mixed": 65 * 4, "fp64": 64 * 8}
+# DRAM bytes (read + write) of one launch of the benchmark's dominant kernel,
+# from the ncu capture summarised in profiles/ (cold caches, as after the
+# L2 flush between timed steps), keyed by workload and launch configuration
+# (kernel, stencil, lanes per ray) and valid only for the kernel sources it
+# was captured from: a changed kernel reports traffic null.
+KERNEL_SOURCES = ("paper_2506_18579_gb300/csrc/rtgd_kernels.cu", "paper_2506_18579_gb300/csrc/rtgd_device.cuh")
+TRAFFIC = {}
 SMS = 152
 FP32_LANES_PER_SM = 128
 FP64_FMA_PER_SM_CLK = 2  # GB300: FP64 issue rate is 1/64 of FP32
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def captured_traffic(workload, cfg):
+    """DRAM bytes per launch from the capture of this exact kernel, or None."""
+    if cfg is None:
+        return None
+    rec = TRAFFIC.get((workload, int(cfg.kernel), int(cfg.stencil), int(cfg.lanes_per_ray)))
+    if rec is None or rec["source_sha256"] != kernel_source_hash():
+        return None
+    return rec["bytes_per_launch"]
 
 
 def parse_args():
@@ -423,7 +449,9 @@ def run_ours(args):
             "tighter_rtol": nominal,
             "fp64_gpu_path": {"rays_per_s": n / fp64_s, "seconds": fp64_s},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None, "peak_basis": bound_note,
+                         "frac": achieved / peak, "traffic": captured_traffic(args.workload, cfg),
+                         "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
+                         "kernel_source_sha256": kernel_source_hash(), "peak_basis": bound_note,
                          "flop_per_stage_eval": FLOP_PER_EVAL[args.precision],
                          "measured_peaks": peaks,
                          "frac_of_measured": achieved / (peaks["fp32_fma_tflops"] if prec == rt.RT_MIXED
