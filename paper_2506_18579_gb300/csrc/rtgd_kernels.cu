@@ -137,11 +137,16 @@ struct RayParams {
     int mode;
 };
 
-__device__ __forceinline__ RayParams ray_params(const FanDev &f, long long id) {
-    const long long a = id % f.n_az;
-    const long long e = (id / f.n_az) % f.n_el;
-    const long long m = (id / ((long long)f.n_az * f.n_el)) % f.n_modes;
-    const long long q = id / ((long long)f.n_az * f.n_el * f.n_modes);
+// Fans hold fewer than 2^31 rays (checked on the host), so 32-bit index
+// arithmetic suffices (64-bit divisions are long instruction sequences).
+__device__ __forceinline__ RayParams ray_params(const FanDev &f, long long id64) {
+    const unsigned id = (unsigned)id64;
+    const unsigned a = id % (unsigned)f.n_az;
+    const unsigned rest = id / (unsigned)f.n_az;
+    const unsigned e = rest % (unsigned)f.n_el;
+    const unsigned rest2 = rest / (unsigned)f.n_el;
+    const unsigned m = rest2 % (unsigned)f.n_modes;
+    const unsigned q = rest2 / (unsigned)f.n_modes;
     RayParams p;
     p.f_hz = f.freq[q] * 1e6;
     p.el = f.el[e] * kDeg2Rad;
@@ -153,12 +158,14 @@ __device__ __forceinline__ RayParams ray_params(const FanDev &f, long long id) {
 // Claim index -> canonical index.  ORDER_ELEVATION_FASTEST hands out
 // neighbouring elevations of one azimuth together (similar paths, so the
 // lanes of a warp gather from nearby cells).
-__device__ __forceinline__ long long claim_to_ray(const FanDev &f, long long c) {
-    if (f.order != RT_ORDER_ELEVATION_FASTEST) return c;
-    const long long e = c % f.n_el;
-    const long long a = (c / f.n_el) % f.n_az;
-    const long long fm = c / ((long long)f.n_el * f.n_az);  // freq * n_modes + mode
-    return (fm * f.n_el + e) * f.n_az + a;
+__device__ __forceinline__ long long claim_to_ray(const FanDev &f, long long c64) {
+    if (f.order != RT_ORDER_ELEVATION_FASTEST) return c64;
+    const unsigned c = (unsigned)c64;
+    const unsigned e = c % (unsigned)f.n_el;
+    const unsigned rest = c / (unsigned)f.n_el;
+    const unsigned a = rest % (unsigned)f.n_az;
+    const unsigned fm = rest / (unsigned)f.n_az;  // freq * n_modes + mode
+    return ((long long)fm * f.n_el + e) * f.n_az + a;
 }
 
 // ================================================================ utilities
@@ -183,13 +190,16 @@ __device__ double hermite_peak(double r0, double r1, double d0, double d1, doubl
 
 // Output quantities of a final state (Sec. II-C: group path, ground distance,
 // azimuth deviation, reflection height): central angle and initial bearing
-// on the sphere from the transmitter (th0, ph0) to (th, ph).
-__device__ void finish_result(const FanDev &f, double az_launch, const double y[6], double P, double apo,
-                              int status, int n_steps, int n_att, int n_evals, double R_E, rt_ray_result *out) {
+// on the sphere from the transmitter (tx_th, tx_ph) to (th, ph).  Out of line
+// (it runs once per ray) with scalar arguments, so that neither the caller's
+// state nor the kernel parameters need an address.
+__device__ __noinline__ void finish_result(double tx_th, double tx_ph, double az_launch, double th, double ph,
+                                           double P, double apo, int status, int n_steps, int n_att, int n_evals,
+                                           double R_E, rt_ray_result *out) {
     double s0, c0, s1, c1, sd, cd;
-    sincos(f.tx_th, &s0, &c0);
-    sincos(y[1], &s1, &c1);
-    sincos(y[2] - f.tx_ph, &sd, &cd);
+    sincos(tx_th, &s0, &c0);
+    sincos(th, &s1, &c1);
+    sincos(ph - tx_ph, &sd, &cd);
     const double east = s1 * sd;                 // components of the final point in the
     const double north = s0 * c1 - c0 * s1 * cd;  // tangent plane at the transmitter
     const double dot = s0 * s1 * cd + c0 * c1;
@@ -199,8 +209,8 @@ __device__ void finish_result(const FanDev &f, double az_launch, const double y[
     r.ground_range_km = R_E * ang;
     r.az_dev_deg = ang > 1e-15 ? wrap180(atan2(east, north) * kRad2Deg - az_launch * kRad2Deg) : 0.0;
     r.apogee_km = apo;
-    r.land_lat_deg = 90.0 - y[1] * kRad2Deg;
-    r.land_lon_deg = wrap180(y[2] * kRad2Deg);
+    r.land_lat_deg = 90.0 - th * kRad2Deg;
+    r.land_lon_deg = wrap180(ph * kRad2Deg);
     r.status = status;
     r.n_steps = n_steps;
     r.n_attempts = n_att;
@@ -345,16 +355,25 @@ __device__ __forceinline__ double step_factor(R err) {
 
 // Launch direction (elevation above the horizontal, azimuth clockwise from
 // north; the theta unit vector points south) and position of a ray.
-__device__ __forceinline__ void launch_dir(const FanDev &f, const RayParams &p, double y[6]) {
+// The direction is computed out of line (once per ray).
+__device__ __noinline__ void launch_k(double el, double az, double *k) {
     double se, ce, sa, ca;
-    sincos(p.el, &se, &ce);
-    sincos(p.az, &sa, &ca);
+    sincos(el, &se, &ce);
+    sincos(az, &sa, &ca);
+    k[0] = se;
+    k[1] = -ce * ca;
+    k[2] = ce * sa;
+}
+
+__device__ __forceinline__ void launch_dir(const FanDev &f, const RayParams &p, double y[6]) {
     y[0] = f.tx_r;
     y[1] = f.tx_th;
     y[2] = f.tx_ph;
-    y[3] = se;
-    y[4] = -ce * ca;
-    y[5] = ce * sa;
+    double k[3];
+    launch_k(p.el, p.az, k);
+    y[3] = k[0];
+    y[4] = k[1];
+    y[5] = k[2];
 }
 
 // Group path to the next cell face the ray reaches, predicted linearly from
@@ -395,7 +414,7 @@ __device__ void trace_ray_fp64(const GridDev &g, const FanDev &f, long long id, 
     launch_dir(f, p, y);
     rhs64(g, rp, y, dummy, &mu2);  // mu^2 at the transmitter for this direction
     if (!(mu2 > 0.0)) {
-        finish_result(f, p.az, y, 0.0, f.tx_r - RE, RT_RAY_NONFINITE, 0, 0, 1, RE, out);
+        finish_result(f.tx_th, f.tx_ph, p.az, y[1], y[2], 0.0, f.tx_r - RE, RT_RAY_NONFINITE, 0, 0, 1, RE, out);
         return;
     }
     const double mu = sqrt(mu2);
@@ -515,7 +534,7 @@ __device__ void trace_ray_fp64(const GridDev &g, const FanDev &f, long long id, 
         }
         h = h_next;
     }
-    finish_result(f, p.az, y, P, apo, status, n_steps, n_att, n_ev, RE, out);
+    finish_result(f.tx_th, f.tx_ph, p.az, y[1], y[2], P, apo, status, n_steps, n_att, n_ev, RE, out);
 }
 
 __global__ void __launch_bounds__(128) trace_fp64_kernel(GridDev g, FanDev f, rt_ray_result *__restrict__ out) {
@@ -558,13 +577,18 @@ __constant__ float c_pow2q[20];
 __device__ __forceinline__ int clamp_cell(double f) { return (int)fmin(fmax(f, -1e6), 1e6); }
 
 // Base of a double state (double arithmetic; used at launch and to resync).
-__device__ void base_from_state(const GridDev &g, const double y[6], Base32 &b) {
-    const double lat = 90.0 - y[1] * kRad2Deg;
-    double lonrel = y[2] * kRad2Deg - g.lon0;
+// Out of line with scalar arguments (it runs at launch and every kResyncSteps
+// accepted steps), returning the base by value.
+__device__ __noinline__ Base32 base_of(double lat0, double lon0, double inv_dlat, double inv_dlon, double R_E,
+                                       double alt0, double inv_dalt, double r, double th, double ph, double k0,
+                                       double k1, double k2) {
+    Base32 b;
+    const double lat = 90.0 - th * kRad2Deg;
+    double lonrel = ph * kRad2Deg - lon0;
     lonrel -= 360.0 * floor(lonrel * (1.0 / 360.0));
-    const double xa = (lat - g.lat0) * g.inv_dlat;
-    const double xb = lonrel * g.inv_dlon;
-    const double xc = (y[0] - g.R_E - g.alt0) * g.inv_dalt;
+    const double xa = (lat - lat0) * inv_dlat;
+    const double xb = lonrel * inv_dlon;
+    const double xc = (r - R_E - alt0) * inv_dalt;
     const double fa = floor(xa), fb = floor(xb), fc = floor(xc);
     // positions far outside the grid are clamped so the integer stays small; they
     // remain outside (and non-finite positions give NaN fractions, also outside)
@@ -574,13 +598,18 @@ __device__ void base_from_state(const GridDev &g, const double y[6], Base32 &b) 
     b.ta = (float)(xa - fa);
     b.tb = (float)(xb - fb);
     b.tc = (float)(xc - fc);
-    b.r = (float)y[0];
-    b.alt = (float)(y[0] - g.R_E);
-    sincosf((float)y[1], &b.sth, &b.cth);
-    sincosf((float)y[2], &b.sph, &b.cph);
-    b.k[0] = (float)y[3];
-    b.k[1] = (float)y[4];
-    b.k[2] = (float)y[5];
+    b.r = (float)r;
+    b.alt = (float)(r - R_E);
+    sincosf((float)th, &b.sth, &b.cth);
+    sincosf((float)ph, &b.sph, &b.cph);
+    b.k[0] = (float)k0;
+    b.k[1] = (float)k1;
+    b.k[2] = (float)k2;
+    return b;
+}
+
+__device__ __forceinline__ void base_from_state(const GridDev &g, const double y[6], Base32 &b) {
+    b = base_of(g.lat0, g.lon0, g.inv_dlat, g.inv_dlon, g.R_E, g.alt0, g.inv_dalt, y[0], y[1], y[2], y[3], y[4], y[5]);
 }
 
 __device__ __forceinline__ void shift_axis(int &i, float &t, float dt) {
@@ -796,7 +825,7 @@ __device__ __forceinline__ float step_factor_f(float err) {
 
 // Peak rise of the cubic Hermite fit over one step, relative to its start:
 // p(s) = m0 s + B s^2 + A s^3 with p(1) = dr, p'(0) = m0 > 0 >= p'(1) = m1.
-__device__ __forceinline__ float hermite_rise_f(float dr, float m0, float m1) {
+__device__ __noinline__ float hermite_rise_f(float dr, float m0, float m1) {  // once per ray: out of line
     const float A = m0 + m1 - 2.0f * dr, B = 3.0f * dr - 2.0f * m0 - m1;
     float lo = 0.0f, hi = 1.0f;
     for (int it = 0; it < 24; ++it) {
@@ -937,12 +966,9 @@ __device__ __forceinline__ void lane_finish(Lane &L, const GridDev &g, const Fan
                                             bool writer = true) {
     L.active = false;
     if (!writer) return;
-    rt_ray_result r;
     const double az = f.az[L.out_id % f.n_az] * kDeg2Rad;
-    double y[6];
-    lane_state(L, y);
-    finish_result(f, az, y, L.P, (double)L.apo, L.status, L.n_steps, L.n_att, L.n_ev, g.R_E, &r);
-    out[L.out_id] = r;
+    finish_result(f.tx_th, f.tx_ph, az, L.y[1], L.y[2], L.P, (double)L.apo, L.status, L.n_steps, L.n_att, L.n_ev,
+                  g.R_E, out + L.out_id);
 }
 
 // Once k1 is known: end an adaptive step just past the next cell face, and
@@ -1002,21 +1028,11 @@ __device__ bool lane_launch(Lane &L, const GridDev &g, const FanDev &f, int q, u
     return !lane_next_attempt(L, f);
 }
 
-// The stages of one step attempt.  Every lane of a warp runs its attempt in
-// the same loop, so the stage index is warp-uniform: the lanes stay converged
-// and the Butcher coefficients are broadcast reads.  Stage 0 is evaluated
-// only when k1 at the current state is not yet known (after a rejected
-// attempt or during the landing solve it is).
-template <int STENCIL, int G, int IP>
-__device__ __forceinline__ void lane_attempt(Lane &L, const GridDev &g, const FanDev &f, const Tableau &T, int q,
-                                             unsigned gmask) {
-    const RayPhys<float> rp = lane_phys(g, L);
-    float d[6], ks[6];
-    if (!L.k1_valid) {
-#pragma unroll
-        for (int c = 0; c < 6; ++c) d[c] = 0.0f;
-        rhs_mixed<STENCIL, G, IP>(g, rp, L.b, d, L.k1, nullptr, q, gmask);
-        ++L.n_ev;
+// Stage 0 bookkeeping once k1 is known: apogee check, face-limited step,
+// accumulators.
+__device__ __forceinline__ void lane_stage0_done(Lane &L, const GridDev &g, const FanDev &f, const Tableau &T,
+                                                 bool fresh) {
+    if (fresh) {
         L.k1_valid = true;
         if (L.have_prev && L.dr_prev > 0.0f && L.k1[0] <= 0.0f) {
             const float rise = hermite_rise_f(L.b.r - L.r_prev, L.h_prev * L.dr_prev, L.h_prev * L.k1[0]);
@@ -1026,14 +1042,87 @@ __device__ __forceinline__ void lane_attempt(Lane &L, const GridDev &g, const Fa
     }
     lane_limit_step(L, g, f);
     accumulate_first(L, T, L.k1);
+}
+
+// The stages of one step attempt.  Every lane of a warp runs its attempt in
+// the same loop, so the stage index is warp-uniform: the lanes stay converged
+// and the Butcher coefficients are broadcast reads.  Stage 0 is evaluated
+// only when k1 at the current state is not yet known (after a rejected
+// attempt or during the landing solve it is): such lanes sit out that one
+// evaluation.  With one lane per ray (throughput-bound fans) one copy of the
+// stage evaluation serves all stages, which keeps the loop inside the
+// instruction cache; with 2 or 4 lanes per ray (latency-bound fans) stage 0
+// is a separate copy, which schedules better.
+template <int STENCIL, int G, int IP>
+__device__ __forceinline__ void lane_attempt(Lane &L, const GridDev &g, const FanDev &f, const Tableau &T, int q,
+                                             unsigned gmask) {
+    const RayPhys<float> rp = lane_phys(g, L);
+    float d[6], ks[6];
+    if (G == 1) {
 #pragma unroll 1
-    for (int s = 1; s < T.ns; ++s) {
+        for (int s = 0; s < T.ns; ++s) {
+            const bool fresh = s == 0 && !L.k1_valid;
+            if (s > 0 || fresh) {
 #pragma unroll
-        for (int c = 0; c < 6; ++c) d[c] = L.hs * L.acc[0][c];
-        rhs_mixed<STENCIL, G, IP>(g, rp, L.b, d, ks, nullptr, q, gmask);
-        ++L.n_ev;
-        accumulate_next(L, T, s, ks);
+                for (int c = 0; c < 6; ++c) d[c] = s == 0 ? 0.0f : L.hs * L.acc[0][c];
+                rhs_mixed<STENCIL, G, IP>(g, rp, L.b, d, ks, nullptr, q, gmask);
+                ++L.n_ev;
+            }
+            if (s == 0) {
+                if (fresh) {
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) L.k1[c] = ks[c];
+                }
+                lane_stage0_done(L, g, f, T, fresh);
+            } else {
+                accumulate_next(L, T, s, ks);
+            }
+        }
+    } else {
+        const bool fresh = !L.k1_valid;
+        if (fresh) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) d[c] = 0.0f;
+            rhs_mixed<STENCIL, G, IP>(g, rp, L.b, d, L.k1, nullptr, q, gmask);
+            ++L.n_ev;
+        }
+        lane_stage0_done(L, g, f, T, fresh);
+#pragma unroll 1
+        for (int s = 1; s < T.ns; ++s) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) d[c] = L.hs * L.acc[0][c];
+            rhs_mixed<STENCIL, G, IP>(g, rp, L.b, d, ks, nullptr, q, gmask);
+            ++L.n_ev;
+            accumulate_next(L, T, s, ks);
+        }
     }
+}
+
+// Bracket of the landing / exit solve (Illinois regula falsi on the step size).
+struct Bracket {
+    double la, lfa, lb, lfb;
+    int side;
+};
+
+// One regula falsi update with the new point (c, fc); returns the next step
+// size.  Out of line: it runs only on the last step of a ray.
+__device__ __noinline__ double bracket_update(Bracket &B, double c, double fc) {
+    if (fc < 0.0) {
+        B.lb = c;
+        B.lfb = fc;
+        if (B.side == -1) B.lfa *= 0.5;
+        B.side = -1;
+    } else {
+        B.la = c;
+        B.lfa = fc;
+        if (B.side == 1) B.lfb *= 0.5;
+        B.side = 1;
+    }
+    return B.lb - B.lfb * (B.lb - B.la) / (B.lfb - B.lfa);
+}
+
+__device__ __noinline__ double bracket_first(double lb, double lfa, double lfb) {
+    return lb - lfb * lb / (lfb - lfa);  // la = 0
 }
 
 // Bookkeeping after an attempt: landing/exit solve, accept or reject, state
@@ -1058,18 +1147,13 @@ __device__ bool lane_end_attempt(Lane &L, const GridDev &g, const FanDev &f) {
         const double c = (double)L.hs;
         const bool done = fabs(fc) < f.land_tol || L.land_it >= 60 || fabs(L.lb - L.la) < 1e-9 || !fin;
         if (!done) {
-            if (fc < 0.0) {
-                L.lb = c;
-                L.lfb = fc;
-                if (L.side == -1) L.lfa *= 0.5;
-                L.side = -1;
-            } else {
-                L.la = c;
-                L.lfa = fc;
-                if (L.side == 1) L.lfb *= 0.5;
-                L.side = 1;
-            }
-            L.hs = (float)(L.lb - L.lfb * (L.lb - L.la) / (L.lfb - L.lfa));
+            Bracket B{L.la, L.lfa, L.lb, L.lfb, L.side};
+            L.hs = (float)bracket_update(B, c, fc);
+            L.la = B.la;
+            L.lfa = B.lfa;
+            L.lb = B.lb;
+            L.lfb = B.lfb;
+            L.side = B.side;
             return !lane_next_attempt(L, f);
         }
         if (!fin) {
@@ -1122,7 +1206,7 @@ __device__ bool lane_end_attempt(Lane &L, const GridDev &g, const FanDev &f) {
         L.lfb = sg * (r_new - L.r_target);
         L.side = 0;
         L.land_it = 0;
-        L.hs = (float)(L.lb - L.lfb * (L.lb - L.la) / (L.lfb - L.lfa));
+        L.hs = (float)bracket_first(L.lb, L.lfa, L.lfb);
         return !lane_next_attempt(L, f);
     }
     L.r_prev = L.b.r;
