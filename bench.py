@@ -49,7 +49,12 @@ GATHER_BYTES = {"mixed": 65 * 4, "fp64": 64 * 8}
 # (kernel, stencil, lanes per ray) and valid only for the kernel sources it
 # was captured from: a changed kernel reports traffic null.
 KERNEL_SOURCES = ("paper_2506_18579_gb300/csrc/rtgd_kernels.cu", "paper_2506_18579_gb300/csrc/rtgd_device.cuh")
-TRAFFIC = {}
+TRAFFIC = {
+    # profiles/trace_mixed_c2_fan.md: 25.93 MB read + 0.07 MB written
+    ("c2", 1, 3, 4): {"bytes_per_launch": 26000896, "source_sha256": "39888b84aae29584"},
+    # profiles/trace_mixed_c4_batch.md: 4.23 MB read + 0.27 MB written
+    ("c4", 1, 2, 1): {"bytes_per_launch": 4498432, "source_sha256": "39888b84aae29584"},
+}
 SMS = 152
 FP32_LANES_PER_SM = 128
 FP64_FMA_PER_SM_CLK = 2  # GB300: FP64 issue rate is 1/64 of FP32
@@ -553,7 +558,11 @@ def run_batch(rt, wl, torch, flush, steps=3):
              "launch": {"kernel": cfg.kernel, "stencil": cfg.stencil, "block_threads": cfg.block_threads,
                         "order": cfg.order, "lanes_per_ray": cfg.lanes_per_ray},
              "graph": "one plan execute (counter reset + launch) captured, replayed per batch",
-             "tune_ms": tune_ms, "l2": "flushed before every replay"}
+             "tune_ms": tune_ms, "l2": "flushed before every replay",
+             "roofline": {"bound": "alu", "achieved": float(res["n_evals"].sum()) * FLOP_PER_EVAL["mixed"] / sec / 1e12,
+                          "peak": SMS * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12, "unit": "TFLOP/s",
+                          "traffic": captured_traffic("c4", cfg)}}
+    out_d["roofline"]["frac"] = out_d["roofline"]["achieved"] / out_d["roofline"]["peak"]
     del graph
     plan.close()
     grid.close()
