@@ -253,7 +253,9 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": w.name, "rays_per_step": per_step, "sample_of": w.fan.n_rays},
+        "config": {"workload": w.name, "rays": w.fan.n_rays, "precision": "fp64 (CPU oracle)",
+                   "rtol": w.fan.rtol, "rays_per_step": per_step,
+                   "l2": "not applicable (host cores)", "parallelism": "host threads"},
         "ray_steps_per_s": steps / total,
         "cpu_baseline": {"value": value, "unit": "rays/s", "cores": cores, "kind": "oracle",
                          "sample": "%d seeded rays per step of the %d-ray fan" % (per_step, w.fan.n_rays)},
