@@ -863,58 +863,25 @@ __device__ __forceinline__ float face_distance_f(const GridDev &g, const Base32 
     return best;
 }
 
-// Per-lane state of the mixed tracer.  The state a stage evaluation reads
-// stays in registers; the state touched once per attempt (FP64 position and
-// group path, the wave vector's compensated pair, the landing bracket, the
-// counters and the apogee bookkeeping) lives in this thread's slot of a
-// per-block shared-memory structure, which keeps the one-lane-per-ray kernels
-// within 128 registers (four resident blocks per SM instead of three).
-constexpr int kColdSlots = 128;  // threads per block at most
-
-struct LaneCold {
-    double y[3][kColdSlots];  // r (km), theta, phi (rad): the FP64 position
-    double P[kColdSlots];     // group path (km)
-    double la[kColdSlots], lfa[kColdSlots], lb[kColdSlots], lfb[kColdSlots];  // crossing bracket
-    double r_target[kColdSlots];  // R_E (ground) or R_E + top (exit through the grid top)
-    float k_hi[3][kColdSlots], k_lo[3][kColdSlots];  // wave vector as a compensated float pair
-    float r_prev[kColdSlots];  // radius at the start of the last accepted step
-    float h_prev[kColdSlots], dr_prev[kColdSlots];  // last accepted step and its dr/dP' at the start
-    float apo[kColdSlots];     // reflection height so far (km)
-    int out_id[kColdSlots], n_steps[kColdSlots], n_att[kColdSlots], status[kColdSlots];
-    int side[kColdSlots], land_it[kColdSlots], since_sync[kColdSlots];
-};
-
+// Per-lane state of the mixed tracer.
 struct Lane {
+    double y[3];              // r (km), theta, phi (rad): the FP64 position
+    double P;                 // group path (km)
+    float k_hi[3], k_lo[3];   // wave vector as a compensated float pair
+    float r_prev;             // radius at the start of the last accepted step
+    double la, lfa, lb, lfb;  // crossing bracket (step size, signed r - target)
+    double r_target;          // R_E (ground) or R_E + top (exit through the grid top)
     float h, hs;              // next step / step of the current attempt (km)
+    float h_prev, dr_prev;    // last accepted step and its dr/dP' at the start
+    float apo;                // reflection height so far (km)
     float acc[5][6];
     float y4[6], e[6];
     float k1[6];
     float xfac, ab0;
     Base32 b;
-    int mode, n_ev;
+    int out_id, mode;
+    int n_steps, n_att, n_ev, status, side, land_it, since_sync;
     bool active, launch, landing, exiting, have_prev, k1_valid, at_face;
-    LaneCold *c;  // the block's cold-state slots
-    int t;        // this thread's slot
-    __device__ __forceinline__ double &y(int i) const { return c->y[i][t]; }
-    __device__ __forceinline__ double &P() const { return c->P[t]; }
-    __device__ __forceinline__ double &la() const { return c->la[t]; }
-    __device__ __forceinline__ double &lfa() const { return c->lfa[t]; }
-    __device__ __forceinline__ double &lb() const { return c->lb[t]; }
-    __device__ __forceinline__ double &lfb() const { return c->lfb[t]; }
-    __device__ __forceinline__ double &r_target() const { return c->r_target[t]; }
-    __device__ __forceinline__ float &k_hi(int i) const { return c->k_hi[i][t]; }
-    __device__ __forceinline__ float &k_lo(int i) const { return c->k_lo[i][t]; }
-    __device__ __forceinline__ float &r_prev() const { return c->r_prev[t]; }
-    __device__ __forceinline__ float &h_prev() const { return c->h_prev[t]; }
-    __device__ __forceinline__ float &dr_prev() const { return c->dr_prev[t]; }
-    __device__ __forceinline__ float &apo() const { return c->apo[t]; }
-    __device__ __forceinline__ int &out_id() const { return c->out_id[t]; }
-    __device__ __forceinline__ int &n_steps() const { return c->n_steps[t]; }
-    __device__ __forceinline__ int &n_att() const { return c->n_att[t]; }
-    __device__ __forceinline__ int &status() const { return c->status[t]; }
-    __device__ __forceinline__ int &side() const { return c->side[t]; }
-    __device__ __forceinline__ int &land_it() const { return c->land_it[t]; }
-    __device__ __forceinline__ int &since_sync() const { return c->since_sync[t]; }
 };
 
 __device__ __forceinline__ RayPhys<float> lane_phys(const GridDev &g, const Lane &L) {
@@ -963,7 +930,7 @@ __device__ __forceinline__ void accumulate_next(Lane &L, const Tableau &T, int s
 
 __device__ void lane_begin_ray(Lane &L, const GridDev &g, const FanDev &f, long long id) {
     const RayParams p = ray_params(f, id);
-    L.out_id() = (int)id;
+    L.out_id = (int)id;
     L.xfac = (float)(kPlasmaHz2PerM3 / (p.f_hz * p.f_hz));
     L.ab0 = (float)(kGyroHzPerTesla / p.f_hz * g.b0);
     L.mode = p.mode;
@@ -971,16 +938,16 @@ __device__ void lane_begin_ray(Lane &L, const GridDev &g, const FanDev &f, long 
     launch_dir(f, p, y);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        L.y(i) = y[i];
-        L.k_hi(i) = (float)y[3 + i];
-        L.k_lo(i) = 0.0f;
+        L.y[i] = y[i];
+        L.k_hi[i] = (float)y[3 + i];
+        L.k_lo[i] = 0.0f;
     }
-    L.P() = 0.0;
+    L.P = 0.0;
     L.h = f.h0_f;
-    L.apo() = (float)(f.tx_r - g.R_E);
-    L.n_steps() = L.n_att() = L.n_ev = 0;
-    L.since_sync() = 0;
-    L.status() = RT_RAY_NOT_RUN;
+    L.apo = (float)(f.tx_r - g.R_E);
+    L.n_steps = L.n_att = L.n_ev = 0;
+    L.since_sync = 0;
+    L.status = RT_RAY_NOT_RUN;
     L.have_prev = L.k1_valid = L.landing = L.exiting = false;
     L.launch = true;
     base_from_state(g, y, L.b);
@@ -990,8 +957,8 @@ __device__ void lane_begin_ray(Lane &L, const GridDev &g, const FanDev &f, long 
 __device__ __forceinline__ void lane_state(const Lane &L, double y[6]) {
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        y[i] = L.y(i);
-        y[3 + i] = (double)L.k_hi(i) + (double)L.k_lo(i);
+        y[i] = L.y[i];
+        y[3 + i] = (double)L.k_hi[i] + (double)L.k_lo[i];
     }
 }
 
@@ -999,9 +966,9 @@ __device__ __forceinline__ void lane_finish(Lane &L, const GridDev &g, const Fan
                                             bool writer = true) {
     L.active = false;
     if (!writer) return;
-    const double az = f.az[L.out_id() % f.n_az] * kDeg2Rad;
-    finish_result(f.tx_th, f.tx_ph, az, L.y(1), L.y(2), L.P(), (double)L.apo(), L.status(), L.n_steps(), L.n_att(), L.n_ev,
-                  g.R_E, out + L.out_id());
+    const double az = f.az[L.out_id % f.n_az] * kDeg2Rad;
+    finish_result(f.tx_th, f.tx_ph, az, L.y[1], L.y[2], L.P, (double)L.apo, L.status, L.n_steps, L.n_att, L.n_ev,
+                  g.R_E, out + L.out_id);
 }
 
 // Once k1 is known: end an adaptive step just past the next cell face, and
@@ -1015,14 +982,14 @@ __device__ __forceinline__ void lane_limit_step(Lane &L, const GridDev &g, const
             L.at_face = true;
         }
     }
-    if (f.has_max_path && L.P() + (double)L.hs > f.max_path) L.hs = (float)(f.max_path - L.P());
+    if (f.has_max_path && L.P + (double)L.hs > f.max_path) L.hs = (float)(f.max_path - L.P);
 }
 
 // Sets up the next step attempt from the current state; returns false when
 // the ray stops (step budget).
 __device__ __forceinline__ bool lane_next_attempt(Lane &L, const FanDev &f) {
-    if (L.n_att() >= f.max_steps) {
-        L.status() = RT_RAY_MAX_STEPS;
+    if (L.n_att >= f.max_steps) {
+        L.status = RT_RAY_MAX_STEPS;
         return false;
     }
     if (!L.landing) {
@@ -1044,7 +1011,7 @@ __device__ bool lane_launch(Lane &L, const GridDev &g, const FanDev &f, int q, u
     ++L.n_ev;
     L.launch = false;
     if (!(mu2 > 0.0f)) {
-        L.status() = RT_RAY_NONFINITE;
+        L.status = RT_RAY_NONFINITE;
         return true;
     }
     // |k| = mu: rescale the launch direction (double), split into hi + lo
@@ -1054,9 +1021,9 @@ __device__ bool lane_launch(Lane &L, const GridDev &g, const FanDev &f, int q, u
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         const double k = y[3 + i] * mu;
-        L.k_hi(i) = (float)k;
-        L.k_lo(i) = (float)(k - (double)L.k_hi(i));
-        L.b.k[i] = L.k_hi(i);
+        L.k_hi[i] = (float)k;
+        L.k_lo[i] = (float)(k - (double)L.k_hi[i]);
+        L.b.k[i] = L.k_hi[i];
     }
     return !lane_next_attempt(L, f);
 }
@@ -1067,9 +1034,9 @@ __device__ __forceinline__ void lane_stage0_done(Lane &L, const GridDev &g, cons
                                                  bool fresh) {
     if (fresh) {
         L.k1_valid = true;
-        if (L.have_prev && L.dr_prev() > 0.0f && L.k1[0] <= 0.0f) {
-            const float rise = hermite_rise_f(L.b.r - L.r_prev(), L.h_prev() * L.dr_prev(), L.h_prev() * L.k1[0]);
-            L.apo() = fmaxf(L.apo(), L.b.alt - (L.b.r - L.r_prev()) + rise);
+        if (L.have_prev && L.dr_prev > 0.0f && L.k1[0] <= 0.0f) {
+            const float rise = hermite_rise_f(L.b.r - L.r_prev, L.h_prev * L.dr_prev, L.h_prev * L.k1[0]);
+            L.apo = fmaxf(L.apo, L.b.alt - (L.b.r - L.r_prev) + rise);
         }
         L.have_prev = false;
     }
@@ -1163,7 +1130,7 @@ __device__ __noinline__ double bracket_first(double lb, double lfa, double lfb) 
 __device__ bool lane_end_attempt(Lane &L, const GridDev &g, const FanDev &f) {
     const double RE = g.R_E;
     const float hf = L.hs;
-    ++L.n_att();
+    ++L.n_att;
     float dy4[6], ef[6];
     bool fin = true;
 #pragma unroll
@@ -1175,33 +1142,33 @@ __device__ bool lane_end_attempt(Lane &L, const GridDev &g, const FanDev &f) {
     if (L.landing) {
         // Illinois regula falsi on the step size: f(h*) = +-(r(step(h*)) - target)
         const double sg = L.exiting ? -1.0 : 1.0;
-        const double fc = sg * ((L.y(0) - L.r_target()) + (double)dy4[0]);
-        ++L.land_it();
+        const double fc = sg * ((L.y[0] - L.r_target) + (double)dy4[0]);
+        ++L.land_it;
         const double c = (double)L.hs;
-        const bool done = fabs(fc) < f.land_tol || L.land_it() >= 60 || fabs(L.lb() - L.la()) < 1e-9 || !fin;
+        const bool done = fabs(fc) < f.land_tol || L.land_it >= 60 || fabs(L.lb - L.la) < 1e-9 || !fin;
         if (!done) {
-            Bracket B{L.la(), L.lfa(), L.lb(), L.lfb(), L.side()};
+            Bracket B{L.la, L.lfa, L.lb, L.lfb, L.side};
             L.hs = (float)bracket_update(B, c, fc);
-            L.la() = B.la;
-            L.lfa() = B.lfa;
-            L.lb() = B.lb;
-            L.lfb() = B.lfb;
-            L.side() = B.side;
+            L.la = B.la;
+            L.lfa = B.lfa;
+            L.lb = B.lb;
+            L.lfb = B.lfb;
+            L.side = B.side;
             return !lane_next_attempt(L, f);
         }
         if (!fin) {
-            L.status() = RT_RAY_NONFINITE;
+            L.status = RT_RAY_NONFINITE;
             return true;
         }
-        L.P() += c;
-        ++L.n_steps();
+        L.P += c;
+        ++L.n_steps;
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-            L.y(i) += (double)dy4[i];
-            two_sum_add(L.k_hi(i), L.k_lo(i), dy4[3 + i]);
+            L.y[i] += (double)dy4[i];
+            two_sum_add(L.k_hi[i], L.k_lo[i], dy4[3 + i]);
         }
-        if (L.exiting) L.apo() = fmaxf(L.apo(), (float)(L.y(0) - RE));
-        L.status() = L.exiting ? RT_RAY_ESCAPED : RT_RAY_LANDED;
+        if (L.exiting) L.apo = fmaxf(L.apo, (float)(L.y[0] - RE));
+        L.status = L.exiting ? RT_RAY_ESCAPED : RT_RAY_LANDED;
         return true;
     }
     float h_next = L.h;
@@ -1213,7 +1180,7 @@ __device__ bool lane_end_attempt(Lane &L, const GridDev &g, const FanDev &f) {
         if (!(err <= 1.0f)) {
             L.h = L.h * fac;
             if (L.h < f.hmin_f) {
-                L.status() = RT_RAY_STEP_UNDERFLOW;
+                L.status = RT_RAY_STEP_UNDERFLOW;
                 return true;
             }
             return !lane_next_attempt(L, f);
@@ -1221,59 +1188,58 @@ __device__ bool lane_end_attempt(Lane &L, const GridDev &g, const FanDev &f) {
         h_next = fminf(fmaxf(L.h * (L.at_face ? fminf(1.0f, fac) : fac), f.hmin_f), f.hmax_f);
     }
     if (!fin) {
-        L.status() = RT_RAY_NONFINITE;
+        L.status = RT_RAY_NONFINITE;
         return true;
     }
     const float alt_new = L.b.alt + dy4[0];
     const bool lands = alt_new < 0.0f;
     if (lands || alt_new > g.top_f) {
         // ground return or exit through the grid top inside this step
-        const double r_new = L.y(0) + (double)dy4[0];
+        const double r_new = L.y[0] + (double)dy4[0];
         L.landing = true;
         L.exiting = !lands;
-        L.r_target() = lands ? RE : RE + g.top;
+        L.r_target = lands ? RE : RE + g.top;
         const double sg = lands ? 1.0 : -1.0;
-        L.la() = 0.0;
-        L.lfa() = sg * (L.y(0) - L.r_target());
-        L.lb() = (double)L.hs;
-        L.lfb() = sg * (r_new - L.r_target());
-        L.side() = 0;
-        L.land_it() = 0;
-        L.hs = (float)bracket_first(L.lb(), L.lfa(), L.lfb());
+        L.la = 0.0;
+        L.lfa = sg * (L.y[0] - L.r_target);
+        L.lb = (double)L.hs;
+        L.lfb = sg * (r_new - L.r_target);
+        L.side = 0;
+        L.land_it = 0;
+        L.hs = (float)bracket_first(L.lb, L.lfa, L.lfb);
         return !lane_next_attempt(L, f);
     }
-    L.r_prev() = L.b.r;
+    L.r_prev = L.b.r;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        L.y(i) += (double)dy4[i];
-        two_sum_add(L.k_hi(i), L.k_lo(i), dy4[3 + i]);
+        L.y[i] += (double)dy4[i];
+        two_sum_add(L.k_hi[i], L.k_lo[i], dy4[3 + i]);
     }
-    L.P() += (double)L.hs;
-    ++L.n_steps();
-    L.apo() = fmaxf(L.apo(), alt_new);
+    L.P += (double)L.hs;
+    ++L.n_steps;
+    L.apo = fmaxf(L.apo, alt_new);
     L.have_prev = true;
-    L.dr_prev() = L.k1[0];
-    L.h_prev() = L.hs;
+    L.dr_prev = L.k1[0];
+    L.h_prev = L.hs;
     L.k1_valid = false;
-    if (++L.since_sync() >= kResyncSteps) {
-        L.since_sync() = 0;
+    if (++L.since_sync >= kResyncSteps) {
+        L.since_sync = 0;
         double y[6];
         lane_state(L, y);
         base_from_state(g, y, L.b);
     } else {
-        const float kh[3] = {L.k_hi(0), L.k_hi(1), L.k_hi(2)};
-        advance_base(g, L.b, dy4, kh);
+        advance_base(g, L.b, dy4, L.k_hi);
     }
     if (L.b.alt >= (float)g.alt0) {
         const bool in_lat = L.b.ia >= 0 && (L.b.ia < g.n_lat - 1 || (L.b.ia == g.n_lat - 1 && L.b.ta == 0.0f));
         const bool in_lon = L.b.ib >= 0 && (L.b.ib < g.n_lon - 1 || (L.b.ib == g.n_lon - 1 && L.b.tb == 0.0f));
         if (!(in_lat && in_lon)) {
-            L.status() = RT_RAY_LEFT_GRID;
+            L.status = RT_RAY_LEFT_GRID;
             return true;
         }
     }
-    if (f.has_max_path && L.P() >= f.max_path - 1e-6) {
-        L.status() = RT_RAY_MAX_PATH;
+    if (f.has_max_path && L.P >= f.max_path - 1e-6) {
+        L.status = RT_RAY_MAX_PATH;
         return true;
     }
     L.h = h_next;
@@ -1299,7 +1265,7 @@ __device__ __forceinline__ unsigned group_mask(int lane) {
 // One ray per thread group of G lanes; each group loops attempt by attempt
 // until its ray ends.
 template <int STENCIL, int G, int IP>
-__global__ void __launch_bounds__(128, G == 1 ? 4 : 3) trace_mixed_plain_kernel(GridDev g, FanDev f, rt_ray_result *__restrict__ out) {
+__global__ void __launch_bounds__(128, 3) trace_mixed_plain_kernel(GridDev g, FanDev f, rt_ray_result *__restrict__ out) {
     __shared__ Tableau T;
     load_tableau(T, f.integrator);
     const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -1307,10 +1273,7 @@ __global__ void __launch_bounds__(128, G == 1 ? 4 : 3) trace_mixed_plain_kernel(
     if (id >= f.n_rays) return;  // whole groups leave together
     const int lane = threadIdx.x & 31, q = lane % G;
     const unsigned gmask = group_mask<G>(lane);
-    __shared__ LaneCold cold;
     Lane L;
-    L.c = &cold;
-    L.t = threadIdx.x;
     L.active = true;
     lane_begin_ray(L, g, f, claim_to_ray(f, id));
     bool done = lane_launch<STENCIL, G, IP>(L, g, f, q, gmask);
@@ -1320,7 +1283,7 @@ __global__ void __launch_bounds__(128, G == 1 ? 4 : 3) trace_mixed_plain_kernel(
         lane_attempt<STENCIL, G, IP>(L, g, f, T, q, gmask);
         done = lane_end_attempt(L, g, f);
     }
-    if (!done) L.status() = RT_RAY_MAX_STEPS;
+    if (!done) L.status = RT_RAY_MAX_STEPS;
     lane_finish(L, g, f, out, q == 0);
 }
 
@@ -1328,7 +1291,7 @@ __global__ void __launch_bounds__(128, G == 1 ? 4 : 3) trace_mixed_plain_kernel(
 // claiming new rays (one atomicAdd per warp for all idle lanes) as rays end.
 // Claims happen between attempts, where all lanes of the warp meet.
 template <int STENCIL, int G, int IP>
-__global__ void __launch_bounds__(128, G == 1 ? 4 : 3) trace_mixed_persistent_kernel(GridDev g, FanDev f,
+__global__ void __launch_bounds__(128, 3) trace_mixed_persistent_kernel(GridDev g, FanDev f,
                                                                      rt_ray_result *__restrict__ out,
                                                                      unsigned long long *__restrict__ counter) {
     __shared__ Tableau T;
@@ -1336,10 +1299,7 @@ __global__ void __launch_bounds__(128, G == 1 ? 4 : 3) trace_mixed_persistent_ke
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, q = lane % G;
     const unsigned gmask = group_mask<G>(lane);
-    __shared__ LaneCold cold;
     Lane L;
-    L.c = &cold;
-    L.t = threadIdx.x;
     L.active = false;
     bool exhausted = false;  // warp-uniform
     long long iters = 0;
@@ -1369,7 +1329,7 @@ __global__ void __launch_bounds__(128, G == 1 ? 4 : 3) trace_mixed_persistent_ke
         if (!__any_sync(FULL, L.active)) break;
         if (++iters > max_iter) {  // defensive bound; never reached for valid inputs
             if (L.active) {
-                L.status() = RT_RAY_MAX_STEPS;
+                L.status = RT_RAY_MAX_STEPS;
                 lane_finish(L, g, f, out, q == 0);
             }
             break;
