@@ -259,10 +259,11 @@ def test_tuner_keeps_one_lane_per_ray_for_large_fans():
     smaller than the GPU may get more lanes."""
     w = wl.config1()
     g = rt.Grid(w.grid, w.ne)
-    big = w.fan.replace(freq_mhz=np.linspace(6.0, 14.0, 16), el_deg=np.linspace(5.0, 50.0, 100),
+    # 256,000 rays: above two waves of resident lanes (152 SMs x 3 or 4 blocks x 128)
+    big = w.fan.replace(freq_mhz=np.linspace(6.0, 14.0, 16), el_deg=np.linspace(5.0, 50.0, 200),
                         az_deg=np.linspace(0.0, 351.0, 40), modes=wl.MODE_O | wl.MODE_X, h_km=2.0)
     fan = rt.Fan(big, rt.RT_MIXED)
-    assert fan.n_rays == 128000
+    assert fan.n_rays == 256000
     best, ms = rt.rt_tune(g, fan, max_rays=16384)
     assert ms > 0 and best.lanes_per_ray == 1
     small = rt.Fan(w.fan.replace(h_km=2.0), rt.RT_MIXED)  # 16 rays
