@@ -557,18 +557,24 @@ rt_err rt_tune(const rt_grid *grid, const rt_fan_desc *fan, size_t max_rays, voi
     rt_launch_config best_c = cands[0];
     for (const auto &cc : cands) {
         if ((r = queue_trace(grid, &sub, out, n, &cc, st)) != RT_OK) break;  // warm-up
-        float t_min = 1e30f;
-        for (int rep = 0; rep < 2 && r == RT_OK; ++rep) {
+        // median of five timed launches: a launch whose slowest ray happened to
+        // share its SM with little other work must not decide the choice
+        float ts[5];
+        int nt = 0;
+        for (int rep = 0; rep < 5 && r == RT_OK; ++rep) {
             cudaEventRecord(e0, st);
             r = queue_trace(grid, &sub, out, n, &cc, st);
             cudaEventRecord(e1, st);
             if (r == RT_OK) r = sync_with_timeout(st);
             float ms = 0.0f;
-            if (r == RT_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) t_min = std::min(t_min, ms);
+            if (r == RT_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) ts[nt++] = ms;
         }
         if (r != RT_OK) break;
-        if (t_min < best_t) {
-            best_t = t_min;
+        if (nt == 0) continue;
+        std::sort(ts, ts + nt);
+        const float t_med = ts[nt / 2];
+        if (t_med < best_t) {
+            best_t = t_med;
             best_c = cc;
         }
     }
