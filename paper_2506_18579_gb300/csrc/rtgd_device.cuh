@@ -86,51 +86,9 @@ __device__ __forceinline__ void gd_half(R s, R &wm1, R &w0, R &dm1, R &d0, int i
     d0 = s * (R(-4.5) + s * (R(1.5) + s * (R(5.0) - s * R(2.5))));
 }
 
-// half_weights in float with packed FP32 arithmetic: (w_{-1}, w_0) and
-// (w'_{-1}, w'_0) as two Horner chains of paired fused multiply-adds, each pair
-// one instruction (each half rounds as a scalar FMA would).  Coefficients from
-// the highest power down: GD p = 3, w_{-1} = (0, -1/2, 11/12, -1/6, -5/12, 1/6),
-// w_0 = (1, 0, -9/4, 1/2, 5/4, -1/2); Catmull-Rom (Eq. 7), w_{-1} = (0, -1/2, 1,
-// -1/2), w_0 = (1, 0, -5/2, 3/2); the derivatives are their term-by-term
-// derivatives.
-template <int IP>
-__device__ __forceinline__ void half_weights_f2(float s, float &wm1, float &w0, float &dm1, float &d0) {
-    const float2 s2 = make_float2(s, s);
-    float2 w, d;
-    if (IP == 1) {
-        w = make_float2(-0.5f, 1.5f);
-        w = __ffma2_rn(w, s2, make_float2(1.0f, -2.5f));
-        w = __ffma2_rn(w, s2, make_float2(-0.5f, 0.0f));
-        w = __ffma2_rn(w, s2, make_float2(0.0f, 1.0f));
-        d = make_float2(-1.5f, 4.5f);
-        d = __ffma2_rn(d, s2, make_float2(2.0f, -5.0f));
-        d = __ffma2_rn(d, s2, make_float2(-0.5f, 0.0f));
-    } else {
-        w = make_float2(1.0f / 6.0f, -0.5f);
-        w = __ffma2_rn(w, s2, make_float2(-5.0f / 12.0f, 1.25f));
-        w = __ffma2_rn(w, s2, make_float2(-1.0f / 6.0f, 0.5f));
-        w = __ffma2_rn(w, s2, make_float2(11.0f / 12.0f, -2.25f));
-        w = __ffma2_rn(w, s2, make_float2(-0.5f, 0.0f));
-        w = __ffma2_rn(w, s2, make_float2(0.0f, 1.0f));
-        d = make_float2(5.0f / 6.0f, -2.5f);
-        d = __ffma2_rn(d, s2, make_float2(-5.0f / 3.0f, 5.0f));
-        d = __ffma2_rn(d, s2, make_float2(-0.5f, 1.5f));
-        d = __ffma2_rn(d, s2, make_float2(11.0f / 6.0f, -4.5f));
-        d = __ffma2_rn(d, s2, make_float2(-0.5f, 0.0f));
-    }
-    wm1 = w.x;
-    w0 = w.y;
-    dm1 = d.x;
-    d0 = d.y;
-}
-
 // gd_half with the interpolant fixed at compile time (IP = 0 GD, 1 CR).
 template <typename R, int IP>
 __device__ __forceinline__ void half_weights(R s, R &wm1, R &w0, R &dm1, R &d0) {
-    if constexpr (sizeof(R) == sizeof(float)) {
-        half_weights_f2<IP>(s, wm1, w0, dm1, d0);
-        return;
-    }
     if (IP == 1) {
         wm1 = s * (R(-0.5) + s * (R(1) - s * R(0.5)));
         w0 = R(1) + s * s * (R(-2.5) + s * R(1.5));
