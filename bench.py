@@ -419,6 +419,11 @@ def run_ours(args):
             peak = SMS * FP64_FMA_PER_SM_CLK * 2 * 2070e6 / 1e12
             bound_note = "FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz"
         achieved = flop / sec / 1e12
+        # the fan's critical path: its longest ray traced alone, same launch configuration
+        i_long = int(np.argmax(res["n_evals"]))
+        alone_ms, _ = time_one_ray(rt, torch, grid, one_ray_spec(wl, spec, i_long), prec, cfg, 3, 2)
+        critical = {"longest_ray_alone_ms": alone_ms, "fan_ms": mean_ms, "fan_over_alone": mean_ms / alone_ms,
+                    "ns_per_stage_eval_alone": alone_ms * 1e6 / max(int(res["n_evals"][i_long]), 1)}
         cpu = cpu_oracle_rate(w, args.cpu_sample) if world == 1 else None
         batch = None
         if world == 1 and not args.no_batch and prec == rt.RT_MIXED:
@@ -448,6 +453,7 @@ def run_ours(args):
             "attempts_per_s": attempts * world / sec,
             "stage_evals_per_s": evals * world / sec,
             "fan_latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
+            "critical_path": critical,
             "longest_ray": {"index": int(np.argmax(res["n_evals"])), "stage_evals": int(res["n_evals"].max()),
                             "status": int(res["status"][int(np.argmax(res["n_evals"]))]),
                             "stage_evals_p50": float(np.median(res["n_evals"])),
@@ -483,34 +489,44 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
-def run_one_ray(args, rt, wl, torch, grid, spec, prec, cfg):
-    """Latency of one ray traced alone (a one-ray fan): the fan's critical path
-    when its longest ray dominates.  Prints the time per stage evaluation."""
+def one_ray_spec(wl, spec, index):
+    """The fan of spec reduced to its canonical ray `index` (a one-ray fan)."""
     freq, el, az = np.atleast_1d(spec.freq_mhz), np.atleast_1d(spec.el_deg), np.atleast_1d(spec.az_deg)
     modes = [m for m in (wl.MODE_O, wl.MODE_X) if spec.modes & m]
-    i = args.one_ray
+    i = index
     ia, i = i % len(az), i // len(az)
     ie, i = i % len(el), i // len(el)
     im, fi = i % len(modes), i // len(modes)
-    one = spec.replace(freq_mhz=np.array([freq[fi]]), modes=modes[im], el_deg=np.array([el[ie]]),
-                       az_deg=np.array([az[ia]]))
+    return spec.replace(freq_mhz=np.array([freq[fi]]), modes=modes[im], el_deg=np.array([el[ie]]),
+                        az_deg=np.array([az[ia]]))
+
+
+def time_one_ray(rt, torch, grid, one, prec, cfg, steps, warmup):
+    """Median CUDA-event time (ms) of tracing a one-ray fan alone, and its record."""
     fan = rt.Fan(one, prec)
     st = torch.cuda.current_stream()
     buf = torch.empty(64, dtype=torch.uint8, device="cuda")
-    for _ in range(max(args.warmup, 1)):
+    for _ in range(max(warmup, 1)):
         rt.rt_trace_device(grid, fan, buf.data_ptr(), 1, cfg=cfg, stream=st.cuda_stream)
     ts = []
-    for _ in range(args.steps):
+    for _ in range(steps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(st)
         rt.rt_trace_device(grid, fan, buf.data_ptr(), 1, cfg=cfg, stream=st.cuda_stream)
         b.record(st)
         torch.cuda.synchronize()
         ts.append(a.elapsed_time(b))
-    r = rt.results_view(buf.cpu().numpy(), 1)
-    ms = float(np.median(ts))
-    print(json.dumps({"one_ray": args.one_ray, "freq_mhz": float(freq[fi]), "mode": "O" if modes[im] == wl.MODE_O else "X",
-                      "el_deg": float(el[ie]), "az_deg": float(az[ia]), "status": int(r["status"][0]),
+    return float(np.median(ts)), rt.results_view(buf.cpu().numpy(), 1).copy()
+
+
+def run_one_ray(args, rt, wl, torch, grid, spec, prec, cfg):
+    """Latency of one ray traced alone (a one-ray fan): the fan's critical path
+    when its longest ray dominates.  Prints the time per stage evaluation."""
+    one = one_ray_spec(wl, spec, args.one_ray)
+    ms, r = time_one_ray(rt, torch, grid, one, prec, cfg, args.steps, args.warmup)
+    print(json.dumps({"one_ray": args.one_ray, "freq_mhz": float(one.freq_mhz[0]),
+                      "mode": "O" if one.modes == wl.MODE_O else "X",
+                      "el_deg": float(one.el_deg[0]), "az_deg": float(one.az_deg[0]), "status": int(r["status"][0]),
                       "stage_evals": int(r["n_evals"][0]), "ms": ms,
                       "ns_per_stage_eval": ms * 1e6 / max(int(r["n_evals"][0]), 1),
                       "launch": None if cfg is None else {"kernel": cfg.kernel, "stencil": cfg.stencil,

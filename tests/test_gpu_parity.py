@@ -234,6 +234,28 @@ def test_invalid_calls_are_errors():
         rt.Grid(wl.GridSpec(**{**spec.__dict__, "n_alt": 3}), w.ne[:, :, :3])
 
 
+def test_fans_of_two_to_the_31_rays_are_refused():
+    """The largest fan is 2^31 - 1 rays (32-bit ray indices on the device): a
+    2^32-ray descriptor is refused before anything is queued, on every entry
+    point that takes a fan (the output buffer here is deliberately tiny; the
+    size check comes before any use of it)."""
+    torch = pytest.importorskip("torch")
+    w = wl.config1()
+    g = rt.Grid(w.grid, w.ne)
+    huge = rt.Fan(w.fan.replace(freq_mhz=np.full(65536, 10.0), el_deg=np.linspace(5.0, 50.0, 32768),
+                                az_deg=[0.0], modes=wl.MODE_O | wl.MODE_X), rt.RT_MIXED)
+    assert huge.n_rays == 1 << 32
+    out = torch.empty(64, dtype=torch.uint8, device="cuda")
+    for fn in (rt.rt_trace_device, rt.rt_trace_device_noalloc):
+        with pytest.raises(rt.RtError) as ei:
+            fn(g, huge, out.data_ptr(), huge.n_rays)
+        assert ei.value.code == rt.RT_EINVAL
+    with pytest.raises(rt.RtError) as ei:
+        rt.Plan(g, huge)
+    assert ei.value.code == rt.RT_EINVAL
+    torch.cuda.synchronize()
+
+
 def test_device_output_and_tuner():
     torch = pytest.importorskip("torch")
     w = _c2_small()
