@@ -550,6 +550,16 @@ rt_err rt_tune(const rt_grid *grid, const rt_fan_desc *fan, size_t max_rays, voi
     }
     rt_ray_result *out = nullptr;
     CUDA_TRY(cudaMallocAsync((void **)&out, n * sizeof(rt_ray_result), st));
+    // Each timed launch starts from a cold L2 (a 256 MiB fill evicts the
+    // ~126 MB L2), as a fan does when its grid was not just traced: with a warm
+    // L2 the kernels rank differently.
+    const size_t flush_bytes = (size_t)256 << 20;
+    void *flush = nullptr;
+    if (cudaMallocAsync(&flush, flush_bytes, st) != cudaSuccess) {
+        cudaFreeAsync(out, st);
+    cudaFreeAsync(flush, st);
+        return fail(RT_ENOMEM, "rt_tune: no device memory for the L2 flush buffer");
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -562,6 +572,7 @@ rt_err rt_tune(const rt_grid *grid, const rt_fan_desc *fan, size_t max_rays, voi
         float ts[5];
         int nt = 0;
         for (int rep = 0; rep < 5 && r == RT_OK; ++rep) {
+            cudaMemsetAsync(flush, rep, flush_bytes, st);
             cudaEventRecord(e0, st);
             r = queue_trace(grid, &sub, out, n, &cc, st);
             cudaEventRecord(e1, st);
