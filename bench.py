@@ -92,6 +92,8 @@ def parse_args():
     p.add_argument("--stencil", choices=["gather", "quad", "table"], default="quad")
     p.add_argument("--order", choices=["canonical", "elevation"], default="elevation")
     p.add_argument("--threads", type=int, default=128)
+    p.add_argument("--blocks-per-sm", type=int, default=0,
+                   help="persistent kernel with --kernel: resident blocks per SM (0 = occupancy limit)")
     p.add_argument("--lanes", type=int, default=0, choices=[0, 1, 2, 4],
                    help="lanes per ray with --kernel (0 = the library's choice)")
     p.add_argument("--workload", choices=["c2", "c4"], default="c2",
@@ -297,7 +299,7 @@ def run_ours(args):
                      "table": rt.RT_STENCIL_TABLE}[args.stencil],
             block_threads=args.threads,
             order=rt.RT_ORDER_CANONICAL if args.order == "canonical" else rt.RT_ORDER_ELEVATION_FASTEST,
-            lanes_per_ray=args.lanes)
+            blocks_per_sm=args.blocks_per_sm, lanes_per_ray=args.lanes)
     elif prec == rt.RT_MIXED and not args.no_tune:
         cfg, tune_ms = rt.rt_tune(grid, fan, max_rays=8192, stream=sptr)
     if args.one_ray is not None:
