@@ -207,11 +207,12 @@ def cpu_oracle_rate(workload, n_sample, seed=1234, single_core_rays=128):
     t1 = time.perf_counter()
     res1 = oracle.trace_fan(g, workload.fan, indices=one, n_threads=1)
     dt1 = time.perf_counter() - t1
-    return dict(value=len(idx) / dt, unit="rays/s", cores=cores, kind="oracle",
+    info = dict(value=len(idx) / dt, unit="rays/s", cores=cores, kind="oracle",
                 sample="%s (FP64 CPU oracle, %d threads)" % (what, cores),
                 ray_steps_per_s=float(res["n_steps"].sum()) / dt, seconds=dt,
                 single_core={"value": len(one) / dt1, "unit": "rays/s", "rays": len(one), "seconds": dt1,
                              "ray_steps_per_s": float(res1["n_steps"].sum()) / dt1})
+    return info, idx, res
 
 
 def near_boundary(res, fan):
@@ -388,6 +389,16 @@ def run_ours(args):
             e["status_mismatch"] = int((ref["status"] != r["status"]).sum())
             return e
 
+        def errs_idx(r, oref, idx):
+            # records r (the whole fan) against oracle records for rays idx; same
+            # well-conditioned set as above, all rays for the status count
+            m = ok[idx] & (oref["status"] == r["status"][idx])
+            e = {f: float(np.abs(r[f][idx] - oref[f])[m].max()) if m.any() else None for f in
+                 ("group_path_km", "ground_range_km", "az_dev_deg", "apogee_km")}
+            e["rays_compared"] = int(m.sum())
+            e["status_mismatch"] = int((oref["status"] != r["status"][idx]).sum())
+            return e
+
         acc = {"vs_fp64_same_rtol": errs(res, ref64), "vs_converged_fp64": errs(res, conv),
                "fp64_same_rtol_vs_converged": errs(ref64, conv), "converged": "FP64 GPU path, rtol 1e-11"}
         # ten times tighter tolerance: throughput and error of the same path
@@ -426,7 +437,13 @@ def run_ours(args):
         alone_ms, _ = time_one_ray(rt, torch, grid, one_ray_spec(wl, spec, i_long), prec, cfg, 3, 2)
         critical = {"longest_ray_alone_ms": alone_ms, "fan_ms": mean_ms, "fan_over_alone": mean_ms / alone_ms,
                     "ns_per_stage_eval_alone": alone_ms * 1e6 / max(int(res["n_evals"][i_long]), 1)}
-        cpu = cpu_oracle_rate(w, args.cpu_sample) if world == 1 else None
+        cpu = None
+        if world == 1:
+            # the CPU baseline leg traces the fan through the oracle; its records
+            # also give the full-size parity of both GPU paths
+            cpu, o_idx, o_res = cpu_oracle_rate(w, args.cpu_sample)
+            acc["vs_cpu_oracle"] = errs_idx(res, o_res, o_idx)
+            acc["fp64_gpu_vs_cpu_oracle"] = errs_idx(ref64, o_res, o_idx)
         batch = None
         if world == 1 and not args.no_batch and prec == rt.RT_MIXED:
             try:
