@@ -596,10 +596,22 @@ def run_batch(rt, wl, torch, flush, steps=3):
                         "order": cfg.order, "lanes_per_ray": cfg.lanes_per_ray},
              "graph": "one plan execute (counter reset + launch) captured, replayed per batch",
              "tune_ms": tune_ms, "l2": "flushed before every replay",
+             "cpu_baseline": None, "vs_cpu_oracle": None,
              "roofline": {"bound": "alu", "achieved": float(res["n_evals"].sum()) * FLOP_PER_EVAL["mixed"] / sec / 1e12,
                           "peak": SMS * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12, "unit": "TFLOP/s",
                           "traffic": captured_traffic("c4", cfg)}}
     out_d["roofline"]["frac"] = out_d["roofline"]["achieved"] / out_d["roofline"]["peak"]
+    # CPU baseline leg of the batch: the FP64 oracle on a seeded 5,000-ray
+    # sample (its rays/s stands for the whole batch), and the batch's mixed
+    # records against the oracle's on that sample, rays next to a skip or
+    # Pedersen boundary left out
+    info, idx, o_res = cpu_oracle_rate(w, 5000)
+    ok = ~near_boundary(res, w.fan)[idx] & (o_res["status"] == res["status"][idx])
+    out_d["cpu_baseline"] = info
+    out_d["vs_cpu_oracle"] = {f: float(np.abs(res[f][idx] - o_res[f])[ok].max()) if ok.any() else None
+                              for f in ("group_path_km", "ground_range_km", "az_dev_deg", "apogee_km")}
+    out_d["vs_cpu_oracle"]["rays_compared"] = int(ok.sum())
+    out_d["vs_cpu_oracle"]["status_mismatch"] = int((o_res["status"] != res["status"][idx]).sum())
     del graph
     plan.close()
     grid.close()
