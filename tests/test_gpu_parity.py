@@ -434,3 +434,19 @@ def test_config4_batched_fan_in_captured_graph(orc):
     ok = ~near_boundary(fp64, w.fan)[idx] & (mixed["status"][idx] == ref["status"])
     _close64(mixed[idx][ok], ref[ok], km=MIX_KM, deg=MIX_DEG)
     plan.close()
+
+
+def test_config4_inputs_at_the_precision_forms_tolerance(orc):
+    """The batch's inputs (181x361x301 grid, day/night gradient) traced at
+    rtol 1e-8, the tolerance of the precision form: the mixed path meets its
+    bar (0.05 km, 1e-4 deg) against the oracle on sampled rays away from skip
+    and Pedersen boundaries.  (At the batch's own rtol 1e-7 the two differ by
+    the integrator's truncation error instead.)"""
+    w = wl.config4(rtol=1e-8)
+    g = rt.Grid(w.grid, w.ne)
+    mixed = rt.rt_trace(g, rt.Fan(w.fan, rt.RT_MIXED))
+    idx = wl.sample_indices(w.fan.n_rays, 300, seed=48)
+    ref = orc.trace_fan(orc.Grid(w.grid, w.ne), w.fan, indices=idx)
+    ok = ~near_boundary(mixed, w.fan)[idx] & (mixed["status"][idx] == ref["status"])
+    assert ok.sum() > 250
+    _close64(mixed[idx][ok], ref[ok], km=MIX_KM, deg=MIX_DEG)
