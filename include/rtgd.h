@@ -106,8 +106,9 @@ enum { RT_MODE_O = 1u, RT_MODE_X = 2u };
 enum { RT_RK4 = 0, RT_RKF45 = 1 };
 enum {
     RT_FP64 = 0,  /* every step of the path in double precision */
-    RT_MIXED = 1  /* interpolation, Appleton-Hartree and derivatives in FP32; ray state,
-                     its RK accumulation, path sums and the landing solve in FP64 */
+    RT_MIXED = 1  /* interpolation, Appleton-Hartree and derivatives in FP32; the ray's
+                     position and its RK accumulation, the group path and the landing /
+                     exit solve in FP64; the wave vector as a compensated pair of floats */
 };
 
 /* A fan of rays (Sec. II-C main module): every combination of frequency,
@@ -151,7 +152,8 @@ typedef struct rt_fan_desc {
 /* Per-ray status. */
 enum {
     RT_RAY_NOT_RUN = 0,
-    RT_RAY_LANDED = 1,         /* returned to r = R_E (landing point solved to 1e-9 km in FP64) */
+    RT_RAY_LANDED = 1,         /* returned to r = R_E (landing point solved to |r - R_E| < 1e-9 km
+                                  on the FP64 path, 1e-5 km on the mixed path) */
     RT_RAY_ESCAPED = 2,        /* left through the top of the grid (exit point solved like landing) */
     RT_RAY_LEFT_GRID = 3,      /* left the grid sideways inside its altitude span */
     RT_RAY_MAX_STEPS = 4,      /* max_steps attempts used */
@@ -195,7 +197,9 @@ typedef struct rt_launch_config {
                               GATHER = padded FP32 grid, QUAD = 4 consecutive altitude samples
                               per float4, TABLE = per-cell table (needs RT_GRID_TABLE) */
     int32_t block_threads; /* 0 = default (128); a multiple of 32 in [32, 128] */
-    int32_t order;         /* RT_ORDER_*: order in which the persistent kernel claims rays */
+    int32_t order;         /* RT_ORDER_*: order in which rays are handed to lane groups (both
+                              kernels); ELEVATION_FASTEST keeps neighbouring elevations of one
+                              azimuth in one warp (similar paths, nearby cells) */
     int32_t blocks_per_sm; /* persistent kernel: resident blocks per SM (0 = occupancy limit) */
     int32_t lanes_per_ray; /* mixed path: 1, 2 or 4 lanes share one ray (they split the 16 sample
                               rows of every stage; 32 / lanes rays per warp); 0 = chosen from the
@@ -243,13 +247,14 @@ rt_err rt_trace_device_noalloc(const rt_grid *grid, const rt_fan_desc *fan, rt_r
  * candidate on a strided sub-fan of at most max_rays rays (0 = 65536; one
  * warm-up and five timed launches each, every timed launch after a 256 MiB
  * fill that evicts L2), and returns the candidate with the lowest median time
- * in *best and that time in *best_ms.  Uses stream-ordered scratch: the
- * records of the sub-fan and the 256 MiB fill buffer (RT_ENOMEM without it).  A fan of at least
- * two waves of resident lanes at one lane per ray is issue-bound: it tries
- * one lane per ray only, on a sub-fan of at least four such waves (a smaller
- * sub-fan would reward the latency of its slowest rays instead).  Blocking.  Results are also cached inside the
- * library, keyed by grid, integrator and fan size, and used by later calls
- * whose kernel and stencil are both AUTO; rt_grid_destroy drops them. */
+ * in *best and that time in *best_ms.  A fan of at least two waves of
+ * resident lanes at one lane per ray is issue-bound: it tries one lane per
+ * ray only, on a sub-fan of at least four such waves (a smaller sub-fan would
+ * reward the latency of its slowest rays instead).  Blocking.  Uses
+ * stream-ordered scratch: the sub-fan's records and the fill buffer
+ * (RT_ENOMEM without them).  Results are also cached inside the library,
+ * keyed by grid, integrator and fan size, and used by later calls whose
+ * kernel and stencil are both AUTO; rt_grid_destroy drops them. */
 rt_err rt_tune(const rt_grid *grid, const rt_fan_desc *fan, size_t max_rays, void *stream,
                rt_launch_config *best, float *best_ms);
 
