@@ -450,6 +450,12 @@ def run_ours(args):
                 batch = run_batch(rt, wl, torch, flush)
             except Exception as exc:
                 batch = {"error": repr(exc)}
+        interpolants = None
+        if world == 1 and not args.no_batch:
+            try:
+                interpolants = run_interpolants(rt, wl)
+            except Exception as exc:
+                interpolants = {"error": repr(exc)}
         serving = None
         if world == 1 and args.serve_seconds > 0 and prec == rt.RT_MIXED:
             try:
@@ -499,6 +505,7 @@ def run_ours(args):
             "wall_s_timed": t_wall,
             "tune_ms": tune_ms,
             "batch": batch,
+            "interpolants": interpolants,
             "serving": serving,
         }
     grid.close()
@@ -601,6 +608,26 @@ def run_batch(rt, wl, torch, flush, steps=3):
                           "peak": SMS * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12, "unit": "TFLOP/s",
                           "traffic": captured_traffic("c4", cfg)}}
     out_d["roofline"]["frac"] = out_d["roofline"]["achieved"] / out_d["roofline"]["peak"]
+    # cost of the interpolant (Sec. IV: GD against Catmull-Rom): the same batch,
+    # the same launch configuration, on a Catmull-Rom copy of the grid; time
+    # per stage evaluation (the two fields differ slightly, so do the paths)
+    grid_cr = rt.Grid(w.grid, w.ne, interp="cr")
+    t_cr = []
+    for i in range(steps + 1):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(cur)
+        rt.rt_trace_device(grid_cr, fan, out.data_ptr(), n, cfg=cfg, stream=cur.cuda_stream)
+        b.record(cur)
+        torch.cuda.synchronize()
+        if i > 0:
+            t_cr.append(a.elapsed_time(b))
+    res_cr = rt.results_view(out.cpu().numpy(), n)
+    ns_gd = sec * 1e9 / float(res["n_evals"].sum())
+    ns_cr = float(np.mean(t_cr)) * 1e6 / float(res_cr["n_evals"].sum())
+    out_d["interpolant_cost"] = {"gd_ns_per_stage_eval": ns_gd, "cr_ns_per_stage_eval": ns_cr,
+                                 "gd_over_cr": ns_gd / ns_cr, "cr_ms_per_batch": float(np.mean(t_cr))}
+    grid_cr.close()
     # CPU baseline leg of the batch: the FP64 oracle on a seeded 5,000-ray
     # sample (its rays/s stands for the whole batch), and the batch's mixed
     # records against the oracle's on that sample, rays next to a skip or
@@ -616,6 +643,34 @@ def run_batch(rt, wl, torch, flush, steps=3):
     plan.close()
     grid.close()
     return out_d
+
+
+def run_interpolants(rt, wl):
+    """Accuracy of GD against Catmull-Rom (Sec. IV): one analytic ionosphere
+    sampled on a coarse grid (1 deg, 1 deg, 5 km) and on a 4x finer grid that
+    stands in for the analytic field; 672 rays traced on the FP64 path at rtol
+    1e-9 on the coarse grid with each interpolant and on the fine grid with GD
+    (the reference).  Errors over rays with the same status on all three and
+    not next to a skip/Pedersen boundary."""
+    c, nc, f, nf, spec = wl.interp_comparison()
+    fan = rt.Fan(spec, rt.RT_FP64)
+    grids = {"gd": rt.Grid(c, nc.astype(np.float64)), "cr": rt.Grid(c, nc.astype(np.float64), interp="cr"),
+             "reference": rt.Grid(f, nf.astype(np.float64))}
+    res = {k: rt.rt_trace(gr, fan) for k, gr in grids.items()}
+    ref = res["reference"]
+    ok = ~near_boundary(ref, spec) & (res["gd"]["status"] == ref["status"]) & (res["cr"]["status"] == ref["status"])
+    out = {"grids": {"coarse": list(c.shape), "reference": list(f.shape)}, "rays": spec.n_rays,
+           "rays_compared": int(ok.sum())}
+    for k in ("gd", "cr"):
+        e = {}
+        for fld in ("group_path_km", "ground_range_km", "apogee_km"):
+            d = np.abs(res[k][fld] - ref[fld])[ok]
+            e[fld] = {"max": float(d.max()), "median": float(np.median(d)), "rms": float(np.sqrt(np.mean(d ** 2)))}
+        e["status_differs"] = int((res[k]["status"] != ref["status"]).sum())
+        out[k] = e
+    for gr in grids.values():
+        gr.close()
+    return out
 
 
 def run_serving(rt, wl, seconds, seed=9):

@@ -308,3 +308,41 @@ def serving_requests(n, seed, grid_specs, max_rays=SERVING_MAX_RAYS):
                       atol_km=1e-6, h_min_km=1e-6, h_max_km=20.0, max_steps=200000, precision=MIXED)
         out.append((gi, fan))
     return out
+
+
+def interp_comparison(seed=10, refine=4):
+    """Inputs for the GD-versus-Catmull-Rom comparison (Sec. IV): one analytic
+    ionosphere (E layer + F2 with a 6-10 MHz latitude gradient, a 5 % TID of
+    600 km wavelength, the anisotropic fan case's dipole) sampled on a coarse
+    grid (1 deg, 1 deg, 5 km; 31x31x121 over +-15 deg, 60-660 km) and on a
+    grid `refine` times finer along every axis over the same box, which stands
+    in for the analytic field.  Fan: 8 and 12 MHz x O/X x elevations 5-55 deg
+    step 2.5 x azimuths 0-315 step 45 (672 rays), RKF45 rtol 1e-9.
+    Returns (coarse GridSpec, coarse Ne, fine GridSpec, fine Ne, FanSpec)."""
+    rng = np.random.default_rng(seed)
+    tid_params = dict(lat_c=TX[0] + rng.uniform(-5.0, 5.0), lon_c=TX[1] + rng.uniform(-5.0, 5.0),
+                      direction=rng.uniform(0.0, 2.0 * np.pi), phase=rng.uniform(0.0, 2.0 * np.pi))
+    field = dipole_field(TX[1])
+    lat_lo, lat_hi = TX[0] - 15.0, TX[0] + 15.0
+
+    def sample(g):
+        lat, lon, alt = g.axes()
+        LAT, LON, ALT = np.meshgrid(lat, lon, alt, indexing="ij")
+        fof2 = 6.0 + 4.0 * (LAT - lat_lo) / (lat_hi - lat_lo)
+        ne = chapman(ALT, nm_from_fo(3.0), 110.0, 10.0) + chapman(ALT, nm_from_fo(fof2), 300.0, 50.0)
+        la, lo = LAT[:, :, 0], LON[:, :, 0]
+        rho = _great_circle_km(tid_params["lat_c"], tid_params["lon_c"], la, lo)
+        dn = np.radians(la - tid_params["lat_c"]) * EARTH_RADIUS_KM
+        de = np.radians(lo - tid_params["lon_c"]) * EARTH_RADIUS_KM * np.cos(np.radians(tid_params["lat_c"]))
+        s = dn * np.cos(tid_params["direction"]) + de * np.sin(tid_params["direction"])
+        tid = 1.0 + 0.05 * np.exp(-(rho ** 2) / (2.0 * 600.0 ** 2)) * np.cos(2.0 * np.pi * s / 600.0 +
+                                                                           tid_params["phase"])
+        return ne * tid[:, :, None]
+
+    coarse = centred_grid(TX[0], TX[1], 31, 31, 121, 1.0, 1.0, 5.0, **field)
+    fine = centred_grid(TX[0], TX[1], 30 * refine + 1, 30 * refine + 1, 120 * refine + 1,
+                        1.0 / refine, 1.0 / refine, 5.0 / refine, **field)
+    fan = FanSpec(*TX, freq_mhz=np.array([8.0, 12.0]), el_deg=np.arange(5.0, 55.0 + 1e-9, 2.5),
+                  az_deg=np.arange(0.0, 360.0 - 1e-9, 45.0), modes=MODE_O | MODE_X, integrator=RKF45,
+                  h_km=1.0, rtol=1e-9, atol_km=1e-6, h_min_km=1e-6, h_max_km=20.0, max_steps=200000)
+    return coarse, sample(coarse), fine, sample(fine), fan
