@@ -648,7 +648,7 @@ def run_batch(rt, wl, torch, flush, steps=3):
 def run_interpolants(rt, wl):
     """Accuracy of GD against Catmull-Rom (Sec. IV): one analytic ionosphere
     sampled on a coarse grid (1 deg, 1 deg, 5 km) and on a 4x finer grid that
-    stands in for the analytic field; 672 rays traced on the FP64 path at rtol
+    stands in for the analytic field; 3,232 rays traced on the FP64 path at rtol
     1e-9 on the coarse grid with each interpolant and on the fine grid with GD
     (the reference).  Errors over rays with the same status on all three and
     not next to a skip/Pedersen boundary."""

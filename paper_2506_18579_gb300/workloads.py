@@ -317,7 +317,7 @@ def interp_comparison(seed=10, refine=4):
     grid (1 deg, 1 deg, 5 km; 31x31x121 over +-15 deg, 60-660 km) and on a
     grid `refine` times finer along every axis over the same box, which stands
     in for the analytic field.  Fan: 8 and 12 MHz x O/X x elevations 5-55 deg
-    step 2.5 x azimuths 0-315 step 45 (672 rays), RKF45 rtol 1e-9.
+    step 0.5 x azimuths 0-315 step 45 (3,232 rays), RKF45 rtol 1e-9.
     Returns (coarse GridSpec, coarse Ne, fine GridSpec, fine Ne, FanSpec)."""
     rng = np.random.default_rng(seed)
     tid_params = dict(lat_c=TX[0] + rng.uniform(-5.0, 5.0), lon_c=TX[1] + rng.uniform(-5.0, 5.0),
@@ -342,7 +342,7 @@ def interp_comparison(seed=10, refine=4):
     coarse = centred_grid(TX[0], TX[1], 31, 31, 121, 1.0, 1.0, 5.0, **field)
     fine = centred_grid(TX[0], TX[1], 30 * refine + 1, 30 * refine + 1, 120 * refine + 1,
                         1.0 / refine, 1.0 / refine, 5.0 / refine, **field)
-    fan = FanSpec(*TX, freq_mhz=np.array([8.0, 12.0]), el_deg=np.arange(5.0, 55.0 + 1e-9, 2.5),
+    fan = FanSpec(*TX, freq_mhz=np.array([8.0, 12.0]), el_deg=np.arange(5.0, 55.0 + 1e-9, 0.5),
                   az_deg=np.arange(0.0, 360.0 - 1e-9, 45.0), modes=MODE_O | MODE_X, integrator=RKF45,
                   h_km=1.0, rtol=1e-9, atol_km=1e-6, h_min_km=1e-6, h_max_km=20.0, max_steps=200000)
     return coarse, sample(coarse), fine, sample(fine), fan
