@@ -608,6 +608,33 @@ def run_batch(rt, wl, torch, flush, steps=3):
                           "peak": SMS * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12, "unit": "TFLOP/s",
                           "traffic": captured_traffic("c4", cfg)}}
     out_d["roofline"]["frac"] = out_d["roofline"]["achieved"] / out_d["roofline"]["peak"]
+    # the same batch as one persistent launch (lane groups claim rays from an
+    # atomic counter), captured and replayed like the tuned plan
+    cfg_p = rt.launch_config(kernel=rt.RT_KERNEL_PERSISTENT, stencil=cfg.stencil, block_threads=cfg.block_threads,
+                             order=cfg.order, lanes_per_ray=cfg.lanes_per_ray)
+    pplan = rt.Plan(grid, fan, cfg=cfg_p)
+    pgraph = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(pgraph, stream=side):
+            pplan.execute(out.data_ptr(), n, stream=side.cuda_stream)
+    torch.cuda.synchronize()
+    pgraph.replay()
+    t_p = []
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(cur)
+        pgraph.replay()
+        b.record(cur)
+        torch.cuda.synchronize()
+        t_p.append(a.elapsed_time(b))
+    out_d["persistent_graph"] = {"ms_per_batch": float(np.mean(t_p)), "rays_per_s": n / (float(np.mean(t_p)) / 1e3),
+                                 "launch": {"kernel": cfg_p.kernel, "stencil": cfg_p.stencil,
+                                            "block_threads": cfg_p.block_threads, "order": cfg_p.order,
+                                            "lanes_per_ray": cfg_p.lanes_per_ray}}
+    del pgraph
+    pplan.close()
     # cost of the interpolant (Sec. IV: GD against Catmull-Rom): the same batch,
     # the same launch configuration, on a Catmull-Rom copy of the grid; time
     # per stage evaluation (the two fields differ slightly, so do the paths)

@@ -243,11 +243,11 @@ rt_err rt_trace_device_noalloc(const rt_grid *grid, const rt_fan_desc *fan, rt_r
                                size_t out_len, const rt_launch_config *cfg, void *stream);
 
 /* Autotuner: times the candidate launch configurations (kernel x stencil x
- * claim order x lanes per ray) for this grid and fan shape on `stream`, each
- * candidate on a strided sub-fan of at most max_rays rays (0 = 65536; one
- * warm-up and five timed launches each, every timed launch after a 256 MiB
- * fill that evicts L2), and returns the candidate with the lowest median time
- * in *best and that time in *best_ms.  A fan of at least two waves of
+ * claim order x lanes per ray x 64 or 128 threads per block) for this grid
+ * and fan shape on `stream`, each candidate on a strided sub-fan of at most
+ * max_rays rays (0 = 65536; one warm-up and three timed launches each,
+ * every timed launch after a 256 MiB fill that evicts L2), and returns the
+ * candidate with the lowest median time in *best and that time in *best_ms.  A fan of at least two waves of
  * resident lanes at one lane per ray is issue-bound: it tries one lane per
  * ray only, on a sub-fan of at least four such waves (a smaller sub-fan would
  * reward the latency of its slowest rays instead).  Blocking.  Uses

@@ -537,13 +537,14 @@ rt_err rt_tune(const rt_grid *grid, const rt_fan_desc *fan, size_t max_rays, voi
         for (int kernel : {RT_KERNEL_PLAIN, RT_KERNEL_PERSISTENT})
             for (int stencil : {RT_STENCIL_GATHER, RT_STENCIL_QUAD, RT_STENCIL_TABLE})
                 for (int order : {RT_ORDER_CANONICAL, RT_ORDER_ELEVATION_FASTEST})
-                    for (int lanes : {1, 2, 4}) {
+                    for (int lanes : {1, 2, 4})
+                        for (int threads : {64, 128}) {
                         if (throughput && lanes > 1) continue;
                         if (stencil == RT_STENCIL_TABLE && !grid->table) continue;
                         c.kernel = kernel;
                         c.stencil = stencil;
                         c.order = order;
-                        c.block_threads = 128;
+                        c.block_threads = threads;
                         c.lanes_per_ray = lanes;
                         cands.push_back(c);
                     }
@@ -567,11 +568,11 @@ rt_err rt_tune(const rt_grid *grid, const rt_fan_desc *fan, size_t max_rays, voi
     rt_launch_config best_c = cands[0];
     for (const auto &cc : cands) {
         if ((r = queue_trace(grid, &sub, out, n, &cc, st)) != RT_OK) break;  // warm-up
-        // median of five timed launches: a launch whose slowest ray happened to
+        // median of three timed launches: a launch whose slowest ray happened to
         // share its SM with little other work must not decide the choice
-        float ts[5];
+        float ts[3];
         int nt = 0;
-        for (int rep = 0; rep < 5 && r == RT_OK; ++rep) {
+        for (int rep = 0; rep < 3 && r == RT_OK; ++rep) {
             cudaMemsetAsync(flush, rep, flush_bytes, st);
             cudaEventRecord(e0, st);
             r = queue_trace(grid, &sub, out, n, &cc, st);

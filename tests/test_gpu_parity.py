@@ -405,8 +405,8 @@ def test_ionogram_matches_oracle(orc, prec):
 def test_config4_batched_fan_in_captured_graph(orc):
     """The ionogram-synthesis batch at full size: 181x361x301 grid, 281
     frequencies x 881 elevations x O/X = 495,122 rays of 50-5000 steps, run as
-    one plan captured in a CUDA graph (mixed) and by the FP64 kernel; sampled
-    rays against the oracle."""
+    one plan captured in a CUDA graph (mixed; plain and persistent kernel) and
+    by the FP64 kernel; sampled rays against the oracle."""
     torch = pytest.importorskip("torch")
     w = wl.config4()
     assert w.fan.n_rays == 495122
@@ -434,6 +434,28 @@ def test_config4_batched_fan_in_captured_graph(orc):
     ok = ~near_boundary(fp64, w.fan)[idx] & (mixed["status"][idx] == ref["status"])
     _close64(mixed[idx][ok], ref[ok], km=MIX_KM, deg=MIX_DEG)
     plan.close()
+    # the same batch as one persistent launch (lane groups claim rays from an
+    # atomic counter), also captured in a graph and replayed twice
+    cfg = rt.launch_config(kernel=rt.RT_KERNEL_PERSISTENT, stencil=rt.RT_STENCIL_QUAD, lanes_per_ray=1,
+                           order=rt.RT_ORDER_ELEVATION_FASTEST)
+    pplan = rt.Plan(g, rt.Fan(w.fan, rt.RT_MIXED), cfg=cfg)
+    outp = torch.zeros(n * 64, dtype=torch.uint8, device="cuda")
+    pgraph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(pgraph, stream=side):
+            pplan.execute(outp.data_ptr(), n, stream=side.cuda_stream)
+    pgraph.replay()
+    torch.cuda.synchronize()
+    first = outp.cpu().numpy().copy()
+    pgraph.replay()
+    torch.cuda.synchronize()
+    pers = rt.results_view(outp.cpu().numpy(), n).copy()
+    assert pers.tobytes() == first.tobytes()  # replays are deterministic
+    assert np.all(pers["status"] != rt.RT_RAY_NOT_RUN)
+    well = ~near_boundary(mixed, w.fan) & (pers["status"] == mixed["status"])
+    assert well.sum() > 0.9 * n and (pers["status"] != mixed["status"]).sum() < 0.001 * n
+    _close64(pers[well], mixed[well], km=MIX_KM, deg=MIX_DEG)
+    pplan.close()
 
 
 def test_config4_inputs_at_the_precision_forms_tolerance(orc):
