@@ -608,6 +608,27 @@ def run_batch(rt, wl, torch, flush, steps=3):
                           "peak": SMS * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12, "unit": "TFLOP/s",
                           "traffic": captured_traffic("c4", cfg)}}
     out_d["roofline"]["frac"] = out_d["roofline"]["achieved"] / out_d["roofline"]["peak"]
+    # oblique-ionogram synthesis on the batch's grid and scan (Sec. IV-B-4):
+    # transmitter to a receiver 1,500 km away along azimuth 45 deg; one blocking
+    # rt_ionogram call (trace, point extraction on the GPU, host sort)
+    lat1, lon1, brg, dd = np.radians(w.fan.tx_lat_deg), np.radians(w.fan.tx_lon_deg), np.radians(45.0), 1500.0 / 6371.0
+    lat2 = np.arcsin(np.sin(lat1) * np.cos(dd) + np.cos(lat1) * np.sin(dd) * np.cos(brg))
+    lon2 = lon1 + np.arctan2(np.sin(brg) * np.sin(dd) * np.cos(lat1), np.cos(dd) - np.sin(lat1) * np.sin(lat2))
+    rx = (float(np.degrees(lat2)), float(np.degrees(lon2)))
+    iono_kw = dict(modes=w.fan.modes, integrator=w.fan.integrator, precision=rt.RT_MIXED, rtol=w.fan.rtol,
+                   atol_km=w.fan.atol_km, h_km=w.fan.h_km, h_max_km=w.fan.h_max_km, cfg=cfg)
+    tx = (w.fan.tx_lat_deg, w.fan.tx_lon_deg, w.fan.tx_alt_km)
+    rt.rt_ionogram(grid, tx, rx, w.fan.freq_mhz, w.fan.el_deg, **iono_kw)  # warm-up
+    t_io = []
+    for _ in range(steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pts, n_pts = rt.rt_ionogram(grid, tx, rx, w.fan.freq_mhz, w.fan.el_deg, **iono_kw)
+        t_io.append(time.perf_counter() - t0)
+    out_d["ionogram"] = {"receiver_km": 1500.0, "rays": n, "points": int(n_pts),
+                         "ms_per_ionogram": float(np.mean(t_io)) * 1e3,
+                         "traces_with_points": int(len({(float(p["freq_mhz"]), int(p["mode"])) for p in pts}))}
     # the same batch as one persistent launch (lane groups claim rays from an
     # atomic counter), captured and replayed like the tuned plan
     cfg_p = rt.launch_config(kernel=rt.RT_KERNEL_PERSISTENT, stencil=cfg.stencil, block_threads=cfg.block_threads,
