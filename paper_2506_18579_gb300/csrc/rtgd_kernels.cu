@@ -1265,7 +1265,7 @@ __device__ __forceinline__ unsigned group_mask(int lane) {
 // One ray per thread group of G lanes; each group loops attempt by attempt
 // until its ray ends.
 template <int STENCIL, int G, int IP>
-__global__ void __launch_bounds__(128, 3) trace_mixed_plain_kernel(GridDev g, FanDev f, rt_ray_result *__restrict__ out) {
+__global__ void __launch_bounds__(128, G == 4 ? 2 : 3) trace_mixed_plain_kernel(GridDev g, FanDev f, rt_ray_result *__restrict__ out) {
     __shared__ Tableau T;
     load_tableau(T, f.integrator);
     const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
