@@ -1263,9 +1263,13 @@ __device__ __forceinline__ unsigned group_mask(int lane) {
 }
 
 // One ray per thread group of G lanes; each group loops attempt by attempt
-// until its ray ends.
+// until its ray ends.  Launch bounds: one lane per ray is throughput-bound
+// (three blocks of 128 per SM, <= 168 registers); 2 or 4 lanes per ray serve
+// fans whose time is the latency of their slowest ray, and there the
+// compiler's own register choice (~200, two blocks per SM) schedules a lone
+// warp's stage evaluation faster.
 template <int STENCIL, int G, int IP>
-__global__ void __launch_bounds__(128, G == 4 ? 2 : 3) trace_mixed_plain_kernel(GridDev g, FanDev f, rt_ray_result *__restrict__ out) {
+__global__ void __launch_bounds__(128, G == 1 ? 3 : 2) trace_mixed_plain_kernel(GridDev g, FanDev f, rt_ray_result *__restrict__ out) {
     __shared__ Tableau T;
     load_tableau(T, f.integrator);
     const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -1291,7 +1295,7 @@ __global__ void __launch_bounds__(128, G == 4 ? 2 : 3) trace_mixed_plain_kernel(
 // claiming new rays (one atomicAdd per warp for all idle lanes) as rays end.
 // Claims happen between attempts, where all lanes of the warp meet.
 template <int STENCIL, int G, int IP>
-__global__ void __launch_bounds__(128, 3) trace_mixed_persistent_kernel(GridDev g, FanDev f,
+__global__ void __launch_bounds__(128, G == 1 ? 3 : 2) trace_mixed_persistent_kernel(GridDev g, FanDev f,
                                                                      rt_ray_result *__restrict__ out,
                                                                      unsigned long long *__restrict__ counter) {
     __shared__ Tableau T;
