@@ -87,7 +87,10 @@ __global__ void quad_kernel(const float *__restrict__ pad32, float4 *__restrict_
 }
 
 // table[cell * 16 + a * 4 + b] = the 4 altitude samples of row (a, b) of the
-// 4x4x4 stencil of cell (i, j, k); cells are ordered [i][j][k].
+// 4x4x4 stencil of cell (i, j, k), each minus the cell's reference node
+// (i, j, k) (padded (i+1, j+1, k+1)); cells are ordered [i][j][k].  The stage
+// evaluation contracts samples relative to that node, so storing them that
+// way saves the subtraction (the same float operation, done once per grid).
 __global__ void table_kernel(const float4 *__restrict__ quad, float4 *__restrict__ table, int n_lat, int n_lon,
                              int n_alt) {
     const long long C_lon = n_lon - 1, C_alt = n_alt - 1, P_lon = n_lon + 2;
@@ -100,7 +103,9 @@ __global__ void table_kernel(const float4 *__restrict__ quad, float4 *__restrict
         const long long j = (cell / C_alt) % C_lon;
         const long long i = cell / (C_alt * C_lon);
         const int a = ab >> 2, b = ab & 3;
-        table[e] = quad[((i + a) * P_lon + (j + b)) * C_alt + k];
+        const float4 u = quad[((i + a) * P_lon + (j + b)) * C_alt + k];
+        const float ref = quad[((i + 1) * P_lon + (j + 1)) * C_alt + k].y;
+        table[e] = make_float4(u.x - ref, u.y - ref, u.z - ref, u.w - ref);
     }
 }
 
@@ -758,8 +763,8 @@ __device__ __forceinline__ void rhs_mixed(const GridDev &g, const RayPhys<float>
 #undef RTGD_ROWQ
     } else if (STENCIL == RT_STENCIL_TABLE) {
         const long long cell = ((long long)ia * (g.n_lon - 1) + ib) * (g.n_alt - 1) + ic;
-        const float4 *qp = g.table + cell * 16;
-        ref = __ldg(qp + 5).y;  // node (ia, ib, ic)
+        const float4 *qp = g.table + cell * 16;  // samples minus the node (ia, ib, ic)
+        ref = __ldg(g.pad32 + (long long)(ia + 1) * g.p_lon * g.p_alt + (long long)(ib + 1) * g.p_alt + ic + 1);
 #define RTGD_ROWT(a, b, u0, u1, u2, u3)              \
     {                                                \
         const float4 v_ = __ldg(qp + (a) * 4 + (b)); \
@@ -768,7 +773,7 @@ __device__ __forceinline__ void rhs_mixed(const GridDev &g, const RayPhys<float>
         u2 = v_.z;                                  \
         u3 = v_.w;                                  \
     }
-        RTGD_CONTRACT(float, RTGD_ROWT, ref, a0, NA, wa, da, wb, db, wc, dc, out);
+        RTGD_CONTRACT(float, RTGD_ROWT, 0.0f, a0, NA, wa, da, wb, db, wc, dc, out);
 #undef RTGD_ROWT
     } else {
         const long long sj = g.p_alt, si = (long long)g.p_lon * g.p_alt;
