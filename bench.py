@@ -564,7 +564,7 @@ def run_batch(rt, wl, torch, flush, steps=3):
     frequencies x 881 elevations x O/X = 495,122 rays of 50-5000 steps) as one
     autotuned plan captured in a CUDA graph; L2 flushed before each replay."""
     w = wl.config4()
-    grid = rt.Grid(w.grid, w.ne)
+    grid = rt.Grid(w.grid, w.ne, table=True)  # 5 GB per-cell table: a tuner candidate
     fan = rt.Fan(w.fan, rt.RT_MIXED)
     n = fan.n_rays
     side = torch.cuda.Stream()
@@ -659,7 +659,7 @@ def run_batch(rt, wl, torch, flush, steps=3):
     # cost of the interpolant (Sec. IV: GD against Catmull-Rom): the same batch,
     # the same launch configuration, on a Catmull-Rom copy of the grid; time
     # per stage evaluation (the two fields differ slightly, so do the paths)
-    grid_cr = rt.Grid(w.grid, w.ne, interp="cr")
+    grid_cr = rt.Grid(w.grid, w.ne, interp="cr", table=(cfg.stencil == rt.RT_STENCIL_TABLE))
     t_cr = []
     for i in range(steps + 1):
         flush.zero_()
