@@ -61,11 +61,17 @@ FP64_FMA_PER_SM_CLK = 2  # GB300: FP64 issue rate is 1/64 of FP32
 
 
 def kernel_source_hash():
+    """Hash of the kernel code (comments and whitespace removed, so that a
+    comment edit does not invalidate a capture)."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for rel in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, rel), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, rel), encoding="utf-8") as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)  # block comments
+        src = re.sub(r"//[^\n]*", " ", src)  # line comments (no URLs or // in strings here)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -5,13 +5,14 @@
 //                       optional per-cell 64-sample table (Sec. II-C: the
 //                       interpolation data are prepared once per grid cell).
 //   trace_fp64        : all-FP64 tracer, one thread per ray.
-//   trace_mixed_*     : mixed-precision tracer.  A lane advances its ray one
-//                       stage (one right-hand-side evaluation) per loop
-//                       iteration, so lanes at different stages, steps or
-//                       rays never diverge in the heavy part.  The plain
-//                       kernel gives each lane one ray; the persistent kernel
-//                       keeps a resident grid whose idle lanes claim new rays
-//                       from an atomic counter (warp-aggregated).
+//   trace_mixed_*     : mixed-precision tracer.  A group of 1, 2 or 4 lanes
+//                       carries one ray; every loop iteration runs one whole
+//                       RK attempt for all lanes of a warp (the stage index
+//                       is warp-uniform), so the lanes stay converged.  The
+//                       plain kernel gives each group one ray; the persistent
+//                       kernel keeps a resident grid whose idle groups claim
+//                       new rays from an atomic counter (warp-aggregated)
+//                       between attempts.
 //   eval_rhs          : diagnostic evaluation of dy/dP' at given states.
 #include <cuda_runtime.h>
 #include <math.h>
@@ -1251,8 +1252,8 @@ __device__ bool lane_end_attempt(Lane &L, const GridDev &g, const FanDev &f) {
     return !lane_next_attempt(L, f);
 }
 
-// Loads the Butcher table of the fan's integrator into shared memory (lanes
-// at different stages then read it without constant-cache serialisation).
+// Loads the Butcher table of the fan's integrator into shared memory; the
+// stage loop reads it at a warp-uniform stage index (broadcast reads).
 __device__ __forceinline__ void load_tableau(Tableau &T, int integrator) {
     const Tableau &src = c_tab[integrator == RT_RKF45 ? 1 : 0];
     const float *s = (const float *)&src;
