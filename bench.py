@@ -50,10 +50,10 @@ GATHER_BYTES = {"mixed": 65 * 4, "fp64": 64 * 8}
 # was captured from: a changed kernel reports traffic null.
 KERNEL_SOURCES = ("paper_2506_18579_gb300/csrc/rtgd_kernels.cu", "paper_2506_18579_gb300/csrc/rtgd_device.cuh")
 TRAFFIC = {
-    # profiles/trace_mixed_c2_fan.md: 26.26 MB read + 0.05 MB written
-    ("c2", 1, 3, 4): {"bytes_per_launch": 26307584, "source_sha256": "398962c00cc8a520"},
-    # profiles/trace_mixed_c4_batch.md: 4.24 MB read + 0.25 MB written
-    ("c4", 1, 2, 1): {"bytes_per_launch": 4497664, "source_sha256": "398962c00cc8a520"},
+    # profiles/trace_mixed_c2_fan.md: 26.68 MB read + 0.08 MB written
+    ("c2", 1, 3, 4): {"bytes_per_launch": 26760704, "source_sha256": "939725055bdcf6c5"},
+    # profiles/trace_mixed_c4_batch.md: 20.23 MB read + 1.26 MB written
+    ("c4", 1, 3, 1): {"bytes_per_launch": 21499392, "source_sha256": "939725055bdcf6c5"},
 }
 SMS = 152
 FP32_LANES_PER_SM = 128
