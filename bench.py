@@ -739,7 +739,7 @@ def run_serving(rt, wl, seconds, seed=9):
     handles = [rt.Grid(g, ne) for g, ne in grids]
     specs = [g for g, _ in grids]
     srv = rt.Server(max_inflight=8, mem_reserve_bytes=1 << 30)
-    stream_reqs = iter(wl.serving_requests(16 + 96 + 3 * 2000, seed, specs))
+    stream_reqs = iter(wl.serving_requests(16 + 96 + 16 + 96 + 3 * 2000, seed, specs))
 
     def run(reqs, arrivals):
         fans = [rt.Fan(f) for _, f in reqs]
@@ -767,9 +767,13 @@ def run_serving(rt, wl, seconds, seed=9):
         lat = np.array([d.total_s for d in done])
         ends = np.array(t_sub) + lat
         rays = sum(f.n_rays for f in fans)
+        evals = sum(int(t[1]["n_evals"].sum()) for t in tickets)
         bad = sum(int(d.status != rt.RT_OK) for d in done)
         span = float(ends.max())  # first submit at t = 0
+        fp32_peak = SMS * FP32_LANES_PER_SM * 2 * 2070e6
         return {"requests": len(reqs), "rays": rays, "rays_per_s": rays / span,
+                "stage_evals_per_s": evals / span,
+                "fp32_roofline_frac": evals * FLOP_PER_EVAL["mixed"] / span / fp32_peak,
                 "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3)},
                 "queue_ms_p50": float(np.percentile([d.queue_s for d in done], 50) * 1e3),
                 "failed": bad}
@@ -780,8 +784,17 @@ def run_serving(rt, wl, seconds, seed=9):
     run(take(16), np.zeros(16))  # warm-up: every grid and kernel variant touched
     sat = run(take(96), np.zeros(96))
     peak = sat["rays_per_s"]
+    # the same saturated mix with every request on the persistent kernel
+    srv.close()
+    srv = rt.Server(max_inflight=8, mem_reserve_bytes=1 << 30,
+                    cfg=rt.launch_config(kernel=rt.RT_KERNEL_PERSISTENT))
+    run(take(16), np.zeros(16))
+    sat_p = run(take(96), np.zeros(96))
+    srv.close()
+    srv = rt.Server(max_inflight=8, mem_reserve_bytes=1 << 30)
     mean_rays = wl.serving_mean_rays()
-    out = {"grids": [list(g.shape) for g in specs], "max_inflight": 8, "saturated": sat, "loads": {}}
+    out = {"grids": [list(g.shape) for g in specs], "max_inflight": 8, "saturated": sat,
+           "saturated_persistent_kernel": sat_p, "loads": {}}
     rng = np.random.default_rng(seed + 1)
     for frac in (0.1, 0.5, 0.9):
         rate = frac * peak / mean_rays  # requests per second
