@@ -112,6 +112,8 @@ def parse_args():
                    help="warm-up launches then one launch, nothing else (for ncu captures)")
     p.add_argument("--cpu-sample", type=int, default=0,
                    help="rays of the fan the CPU oracle baseline traces (0 = the whole fan)")
+    p.add_argument("--serve-slots", type=int, default=8,
+                   help="request server stream slots (requests in flight at once)")
     p.add_argument("--serve-seconds", type=float, default=4.0,
                    help="seconds of Poisson arrivals per offered load in the serving section (0 = skip)")
     p.add_argument("--no-batch", action="store_true",
@@ -465,7 +467,7 @@ def run_ours(args):
         serving = None
         if world == 1 and args.serve_seconds > 0 and prec == rt.RT_MIXED:
             try:
-                serving = run_serving(rt, wl, args.serve_seconds)
+                serving = run_serving(rt, wl, args.serve_seconds, slots=args.serve_slots)
             except Exception as exc:  # the serving section must not cost the main line
                 serving = {"error": repr(exc)}
         line = {
@@ -727,7 +729,7 @@ def run_interpolants(rt, wl):
     return out
 
 
-def run_serving(rt, wl, seconds, seed=9):
+def run_serving(rt, wl, seconds, seed=9, slots=8):
     """Serving form: a Poisson stream of uneven fan requests (1..100k rays,
     ionogram-synthesis and OTHR-registration shapes) over four resident grids
     (21x21x61 .. 181x361x301), through the continuous-batching server.  The
@@ -738,7 +740,7 @@ def run_serving(rt, wl, seconds, seed=9):
     grids = wl.serving_grids()
     handles = [rt.Grid(g, ne) for g, ne in grids]
     specs = [g for g, _ in grids]
-    srv = rt.Server(max_inflight=8, mem_reserve_bytes=1 << 30)
+    srv = rt.Server(max_inflight=slots, mem_reserve_bytes=1 << 30)
     stream_reqs = iter(wl.serving_requests(16 + 96 + 16 + 96 + 3 * 2000, seed, specs))
 
     def run(reqs, arrivals):
@@ -786,14 +788,14 @@ def run_serving(rt, wl, seconds, seed=9):
     peak = sat["rays_per_s"]
     # the same saturated mix with every request on the persistent kernel
     srv.close()
-    srv = rt.Server(max_inflight=8, mem_reserve_bytes=1 << 30,
+    srv = rt.Server(max_inflight=slots, mem_reserve_bytes=1 << 30,
                     cfg=rt.launch_config(kernel=rt.RT_KERNEL_PERSISTENT))
     run(take(16), np.zeros(16))
     sat_p = run(take(96), np.zeros(96))
     srv.close()
-    srv = rt.Server(max_inflight=8, mem_reserve_bytes=1 << 30)
+    srv = rt.Server(max_inflight=slots, mem_reserve_bytes=1 << 30)
     mean_rays = wl.serving_mean_rays()
-    out = {"grids": [list(g.shape) for g in specs], "max_inflight": 8, "saturated": sat,
+    out = {"grids": [list(g.shape) for g in specs], "max_inflight": slots, "saturated": sat,
            "saturated_persistent_kernel": sat_p, "loads": {}}
     rng = np.random.default_rng(seed + 1)
     for frac in (0.1, 0.5, 0.9):
