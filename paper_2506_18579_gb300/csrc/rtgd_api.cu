@@ -558,7 +558,6 @@ rt_err rt_tune(const rt_grid *grid, const rt_fan_desc *fan, size_t max_rays, voi
     void *flush = nullptr;
     if (cudaMallocAsync(&flush, flush_bytes, st) != cudaSuccess) {
         cudaFreeAsync(out, st);
-    cudaFreeAsync(flush, st);
         return fail(RT_ENOMEM, "rt_tune: no device memory for the L2 flush buffer");
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -593,6 +592,7 @@ rt_err rt_tune(const rt_grid *grid, const rt_fan_desc *fan, size_t max_rays, voi
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFreeAsync(out, st);
+    cudaFreeAsync(flush, st);
     if (r != RT_OK) return r;
     if (fan->precision == RT_MIXED) {
         std::lock_guard<std::mutex> lk(g_tune_mu);

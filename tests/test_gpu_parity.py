@@ -273,6 +273,14 @@ def test_device_output_and_tuner():
     assert ms > 0 and best.kernel in (rt.RT_KERNEL_PLAIN, rt.RT_KERNEL_PERSISTENT)
     tuned = rt.rt_trace(g, fan)  # picks the cached configuration
     assert np.array_equal(tuned["status"], host["status"])
+    # the tuner releases its scratch (results and the 256 MiB L2-flush buffer):
+    # repeated calls leave the device's free memory where it was
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        rt.rt_tune(g, fan, max_rays=512)
+    torch.cuda.synchronize()
+    assert free0 - torch.cuda.mem_get_info()[0] < (128 << 20)
 
 
 def test_tuner_keeps_one_lane_per_ray_for_large_fans():
