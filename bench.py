@@ -112,6 +112,8 @@ def parse_args():
                    help="warm-up launches then one launch, nothing else (for ncu captures)")
     p.add_argument("--cpu-sample", type=int, default=0,
                    help="rays of the fan the CPU oracle baseline traces (0 = the whole fan)")
+    p.add_argument("--serve-fuse", type=int, default=32768,
+                   help="fuse_max_rays of the serving section's fused runs")
     p.add_argument("--serve-slots", type=int, default=8,
                    help="request server stream slots (requests in flight at once)")
     p.add_argument("--serve-seconds", type=float, default=4.0,
@@ -467,7 +469,7 @@ def run_ours(args):
         serving = None
         if world == 1 and args.serve_seconds > 0 and prec == rt.RT_MIXED:
             try:
-                serving = run_serving(rt, wl, args.serve_seconds, slots=args.serve_slots)
+                serving = run_serving(rt, wl, args.serve_seconds, slots=args.serve_slots, fuse=args.serve_fuse)
             except Exception as exc:  # the serving section must not cost the main line
                 serving = {"error": repr(exc)}
         line = {
@@ -729,21 +731,26 @@ def run_interpolants(rt, wl):
     return out
 
 
-def run_serving(rt, wl, seconds, seed=9, slots=8):
+def run_serving(rt, wl, seconds, seed=9, slots=8, fuse=32768):
     """Serving form: a Poisson stream of uneven fan requests (1..100k rays,
     ionogram-synthesis and OTHR-registration shapes) over four resident grids
     (21x21x61 .. 181x361x301), through the continuous-batching server.  The
     saturated throughput of the same request mix is measured first (all
-    requests submitted at once); offered loads of 10 %, 50 % and 90 % of it
-    follow, each for `seconds` of arrivals.  Latency = submit -> records in the
+    requests submitted at once), one 96-request list served three ways: one
+    launch per request, the persistent kernel, and fusion of requests of at
+    most `fuse` rays; offered loads of 10 %, 50 % and 90 % of the first
+    follow, each for `seconds` of arrivals, served without and with fusion
+    (same requests, same arrival times).  Latency = submit -> records in the
     caller's host buffer."""
     grids = wl.serving_grids()
     handles = [rt.Grid(g, ne) for g, ne in grids]
     specs = [g for g, _ in grids]
-    srv = rt.Server(max_inflight=slots, mem_reserve_bytes=1 << 30)
-    stream_reqs = iter(wl.serving_requests(16 + 96 + 16 + 96 + 3 * 2000, seed, specs))
+    stream_reqs = iter(wl.serving_requests(3 * 16 + 96 + 3 * 2000, seed, specs))
 
-    def run(reqs, arrivals):
+    def server(**kw):
+        return rt.Server(max_inflight=slots, mem_reserve_bytes=1 << 30, **kw)
+
+    def run(srv, reqs, arrivals):
         fans = [rt.Fan(f) for _, f in reqs]
         done = [None] * len(reqs)
         tickets = [None] * len(reqs)
@@ -778,34 +785,37 @@ def run_serving(rt, wl, seconds, seed=9, slots=8):
                 "fp32_roofline_frac": evals * FLOP_PER_EVAL["mixed"] / span / fp32_peak,
                 "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3)},
                 "queue_ms_p50": float(np.percentile([d.queue_s for d in done], 50) * 1e3),
+                "requests_per_launch_mean": float(np.mean([d.batch_size for d in done])),
                 "failed": bad}
 
     def take(k):
         return [next(stream_reqs) for _ in range(k)]
 
-    run(take(16), np.zeros(16))  # warm-up: every grid and kernel variant touched
-    sat = run(take(96), np.zeros(96))
+    plain, persistent, fused = server(), server(cfg=rt.launch_config(kernel=rt.RT_KERNEL_PERSISTENT)), \
+        server(fuse_max_rays=fuse)
+    for srv in (plain, persistent, fused):
+        run(srv, take(16), np.zeros(16))  # warm-up: every grid and kernel variant touched
+    sat_reqs = take(96)
+    sat = run(plain, sat_reqs, np.zeros(96))
+    sat_p = run(persistent, sat_reqs, np.zeros(96))
+    sat_f = run(fused, sat_reqs, np.zeros(96))
+    persistent.close()
     peak = sat["rays_per_s"]
-    # the same saturated mix with every request on the persistent kernel
-    srv.close()
-    srv = rt.Server(max_inflight=slots, mem_reserve_bytes=1 << 30,
-                    cfg=rt.launch_config(kernel=rt.RT_KERNEL_PERSISTENT))
-    run(take(16), np.zeros(16))
-    sat_p = run(take(96), np.zeros(96))
-    srv.close()
-    srv = rt.Server(max_inflight=slots, mem_reserve_bytes=1 << 30)
     mean_rays = wl.serving_mean_rays()
-    out = {"grids": [list(g.shape) for g in specs], "max_inflight": slots, "saturated": sat,
-           "saturated_persistent_kernel": sat_p, "loads": {}}
+    out = {"grids": [list(g.shape) for g in specs], "max_inflight": slots, "fuse_max_rays": fuse,
+           "saturated": sat, "saturated_persistent_kernel": sat_p, "saturated_fused": sat_f,
+           "loads": {}, "loads_fused": {}}
     rng = np.random.default_rng(seed + 1)
     for frac in (0.1, 0.5, 0.9):
         rate = frac * peak / mean_rays  # requests per second
         k = int(np.clip(rate * seconds, 40, 2000))
         arrivals = np.cumsum(rng.exponential(1.0 / rate, k))
-        res = run(take(k), arrivals)
-        res["offered_rays_per_s"] = frac * peak
-        out["loads"]["%d%%" % round(frac * 100)] = res
-    srv.close()
+        reqs = take(k)
+        key = "%d%%" % round(frac * 100)
+        out["loads"][key] = dict(run(plain, reqs, arrivals), offered_rays_per_s=frac * peak)
+        out["loads_fused"][key] = dict(run(fused, reqs, arrivals), offered_rays_per_s=frac * peak)
+    plain.close()
+    fused.close()
     for h in handles:
         h.close()
     return out

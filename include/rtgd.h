@@ -318,13 +318,28 @@ rt_err rt_ionogram(const rt_grid *grid, const rt_ionogram_desc *desc, rt_ionogra
  * completion thread copies each result to the caller's host buffer (through
  * pinned staging) and wakes rt_server_wait.  Every request uses the launch
  * configuration given at creation, so its records equal those of rt_trace
- * with that configuration whatever else is in flight.  The paper has no
+ * with that configuration whatever else is in flight.  Optionally, small
+ * requests queued at the same time are fused into one launch (fuse_max_rays)
+ * so that they fill the GPU together.  The paper has no
  * counterpart (it traces one scan at a time on a CPU). */
 typedef struct rt_server rt_server;
 
 typedef struct rt_server_config {
     int32_t max_inflight;        /* stream slots, 1..64 (0 = 8) */
-    int32_t reserved;            /* must be 0 */
+    int32_t fuse_max_rays;       /* 0 = one launch per request.  > 0: mixed requests of at most
+                                    fuse_max_rays rays are small and are fused.  The dispatcher admits
+                                    a small head request together with the queued small requests on the
+                                    same grid with the same integrator, in queue order, up to
+                                    fuse_max_rays rays in total and 256 requests, and traces them as one
+                                    launch in one slot.  Every small request, alone or not, runs the
+                                    fused kernel: four lanes per ray, the stencil, block size and ray
+                                    order of `launch` (whose kernel must be AUTO or PLAIN and
+                                    lanes_per_ray 0 or 4).  Its records therefore do not depend on what
+                                    shares its launch; they equal those of rt_trace on the plain kernel
+                                    at four lanes per ray up to float rounding (the two kernels are
+                                    compiled apart).  Other requests run as without fusion.  A useful
+                                    value is about one wave of resident four-lane groups (152 SMs x 2
+                                    blocks x 128 threads / 4 = 9,728 rays). */
     size_t mem_reserve_bytes;    /* device memory kept free by admission */
     rt_launch_config launch;     /* kernel choice for every request (zero = library defaults) */
 } rt_server_config;
@@ -335,7 +350,7 @@ typedef struct rt_request_stats {
     double total_s;              /* submit -> result in the caller's buffer */
     int64_t n_rays;
     int32_t status;              /* rt_err of the request */
-    int32_t reserved;
+    int32_t batch_size;          /* requests traced by the launch that traced this one (1 = alone) */
 } rt_request_stats;
 
 /* Creates a server on the current device (threads start immediately). */

@@ -340,6 +340,66 @@ rt_err rtgd_queue_trace(const rt_grid *grid, const rt_fan_desc *fan, rt_ray_resu
     return queue_trace(grid, fan, out_dev, out_len, cfg, st);
 }
 
+rt_err rtgd_queue_trace_fans(const rt_grid *grid, const rt_fan_desc *const *fans, int n_fans, rt_ray_result *out_dev,
+                             size_t out_len, const rt_launch_config *cfg, cudaStream_t st) {
+    if (!grid || !fans || n_fans < 1 || !out_dev) return fail(RT_EINVAL, "fused trace: NULL argument or no fans");
+    int dev = 0;
+    rt_err r = ensure_device(&dev);
+    if (r != RT_OK) return r;
+    if (dev != grid->device) return fail(RT_EINVAL, "grid lives on device %d, current device is %d", grid->device, dev);
+    size_t n_total = 0, n_tab = 0;
+    for (int k = 0; k < n_fans; ++k) {
+        if ((r = validate_fan(fans[k])) != RT_OK) return r;
+        if (fans[k]->precision != RT_MIXED) return fail(RT_EINVAL, "fused trace: mixed-precision fans only");
+        if (fans[k]->integrator != fans[0]->integrator) return fail(RT_EINVAL, "fused trace: fans differ in integrator");
+        n_total += fan_rays(fans[k]);
+        n_tab += (size_t)fans[k]->n_freq + fans[k]->n_el + fans[k]->n_az;
+    }
+    if (out_len < n_total) return fail(RT_EINVAL, "out_len %zu < %zu rays", out_len, n_total);
+    if (n_total >= ((size_t)1 << 31)) return fail(RT_EINVAL, "fused trace too large (at most 2^31 - 1 rays)");
+    rt_launch_config c;
+    std::memset(&c, 0, sizeof(c));
+    if (cfg) c = *cfg;
+    c.kernel = RT_KERNEL_PLAIN;
+    c.lanes_per_ray = 4;
+    LaunchPlan lp;
+    int order = 0;
+    if ((r = make_plan(grid, fans[0], n_total, &c, &lp, &order)) != RT_OK) return r;
+    // scratch: the fans' device views, the n_fans + 1 ray offsets, the fan tables
+    const size_t off_first = (size_t)n_fans * sizeof(FanDev);
+    const size_t off_tab = off_first + (size_t)(n_fans + 1) * sizeof(long long);
+    const size_t bytes = off_tab + n_tab * sizeof(double);
+    std::vector<char> blob(bytes);
+    char *ws = nullptr;
+    CUDA_TRY(cudaMallocAsync((void **)&ws, bytes, st));
+    FanDev *fd = (FanDev *)blob.data();
+    long long *first = (long long *)(blob.data() + off_first);
+    double *tab_h = (double *)(blob.data() + off_tab);
+    const double *tab_d = (const double *)(ws + off_tab);
+    size_t t = 0;
+    long long acc = 0;
+    for (int k = 0; k < n_fans; ++k) {
+        const rt_fan_desc *fk = fans[k];
+        const size_t nk = fan_rays(fk);
+        std::memcpy(tab_h + t, fk->freq_mhz, fk->n_freq * sizeof(double));
+        std::memcpy(tab_h + t + fk->n_freq, fk->el_deg, fk->n_el * sizeof(double));
+        std::memcpy(tab_h + t + fk->n_freq + fk->n_el, fk->az_deg, fk->n_az * sizeof(double));
+        fd[k] = fill_fandev(grid, fk, nk, order, tab_d + t);
+        first[k] = acc;
+        acc += (long long)nk;
+        t += (size_t)fk->n_freq + fk->n_el + fk->n_az;
+    }
+    first[n_fans] = acc;
+    cudaError_t e = cudaMemcpyAsync(ws, blob.data(), bytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = launch_trace_fans(grid->g, (const FanDev *)ws, (const long long *)(ws + off_first), n_fans, acc,
+                              fans[0]->integrator, out_dev, lp, st);
+    const cudaError_t e2 = cudaFreeAsync(ws, st);
+    if (e != cudaSuccess) return cuda_fail(e, "fused trace launch");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync");
+    return RT_OK;
+}
+
 rt_err rtgd_set_error(rt_err code, const char *msg) { return fail(code, "%s", msg); }
 
 extern "C" {

@@ -42,12 +42,24 @@ cudaError_t upload_tableaus();
 cudaError_t launch_trace(const GridDev &g, const FanDev &f, rt_ray_result *out, unsigned long long *counter,
                          const LaunchPlan &lp, cudaStream_t st);
 cudaError_t persistent_occupancy(int stencil, int lanes, int threads, int *blocks_per_sm);
+// Mixed path, four lanes per ray: n_fans fans (device array fans) in one
+// launch; first (device, n_fans + 1 entries) holds each fan's first ray in
+// the launch and the total; out receives the records fan after fan.
+cudaError_t launch_trace_fans(const GridDev &g, const FanDev *fans, const long long *first, int n_fans,
+                              long long n_total, int integrator, rt_ray_result *out, const LaunchPlan &lp,
+                              cudaStream_t st);
 }  // namespace rtgd
 
 // Entry points shared between the translation units of the host library
 // (defined in rtgd_api.cu).
 rt_err rtgd_queue_trace(const rt_grid *grid, const rt_fan_desc *fan, rt_ray_result *out_dev, size_t out_len,
                         const rt_launch_config *cfg, cudaStream_t st);
+// Queues n_fans mixed-precision fans with one integrator on one grid as one
+// launch (four lanes per ray; stencil, block size and ray order from cfg);
+// out_dev receives the records fan after fan.  A fan's records do not
+// depend on the other fans of the launch.
+rt_err rtgd_queue_trace_fans(const rt_grid *grid, const rt_fan_desc *const *fans, int n_fans, rt_ray_result *out_dev,
+                             size_t out_len, const rt_launch_config *cfg, cudaStream_t st);
 rt_err rtgd_set_error(rt_err code, const char *msg);
 
 namespace rtgd {

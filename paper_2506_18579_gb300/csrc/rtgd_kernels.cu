@@ -1351,6 +1351,45 @@ __global__ void __launch_bounds__(128, G == 1 ? 3 : 2) trace_mixed_persistent_ke
     }
 }
 
+// ================================================================ fused fans
+// Several small fans on one grid in one launch (the request server's fused
+// batches).  Ray i of the launch belongs to fan k with first[k] <= i <
+// first[k + 1] (binary search over the n_fans + 1 offsets); its record goes
+// to out + first[k] + its index within fan k.  The fans share one integrator
+// (the block's Butcher table).  Four lanes per ray, as for any fan too small
+// to fill the GPU: the per-ray code is that of the four-lane plain kernel,
+// with the fan read from global memory.
+template <int STENCIL, int IP>
+__global__ void __launch_bounds__(128, 2) trace_mixed_fans_kernel(GridDev g, const FanDev *__restrict__ fans,
+                                                                  const long long *__restrict__ first, int n_fans,
+                                                                  int integrator, rt_ray_result *__restrict__ out) {
+    constexpr int G = 4;
+    __shared__ Tableau T;
+    load_tableau(T, integrator);
+    const long long i = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / G;
+    if (i >= first[n_fans]) return;  // whole groups leave together
+    int lo = 0, hi = n_fans - 1;
+    while (lo < hi) {  // largest k with first[k] <= i
+        const int mid = (lo + hi + 1) >> 1;
+        if (first[mid] <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    const FanDev &f = fans[lo];
+    const int lane = threadIdx.x & 31, q = lane % G;
+    const unsigned gmask = group_mask<G>(lane);
+    Lane L;
+    L.active = true;
+    lane_begin_ray(L, g, f, claim_to_ray(f, i - first[lo]));
+    bool done = lane_launch<STENCIL, G, IP>(L, g, f, q, gmask);
+    const long long max_att = (long long)f.max_steps + 2;
+    for (long long it = 0; it < max_att && !done; ++it) {
+        lane_attempt<STENCIL, G, IP>(L, g, f, T, q, gmask);
+        done = lane_end_attempt(L, g, f);
+    }
+    if (!done) L.status = RT_RAY_MAX_STEPS;
+    lane_finish(L, g, f, out + first[lo], q == 0);
+}
+
 // ================================================================ ionogram
 // One warp per (frequency, mode) trace: lanes scan neighbouring elevation
 // pairs; the pairs whose landed rays bracket the receiver distance d_rx emit
@@ -1543,6 +1582,31 @@ cudaError_t launch_trace(const GridDev &g, const FanDev &f, rt_ray_result *out, 
         case RT_STENCIL_GATHER: return launch_mixed<RT_STENCIL_GATHER>(g, f, out, counter, lp, st);
         case RT_STENCIL_TABLE: return launch_mixed<RT_STENCIL_TABLE>(g, f, out, counter, lp, st);
         default: return launch_mixed<RT_STENCIL_QUAD>(g, f, out, counter, lp, st);
+    }
+}
+
+template <int STENCIL>
+static cudaError_t launch_fans_s(const GridDev &g, const FanDev *fans, const long long *first, int n_fans,
+                                 long long n_total, int integrator, rt_ray_result *out, int threads, cudaStream_t st) {
+    const unsigned blocks = (unsigned)((n_total * 4 + threads - 1) / threads);  // four lanes per ray
+    if (g.interp == 1)
+        trace_mixed_fans_kernel<STENCIL, 1><<<blocks, threads, 0, st>>>(g, fans, first, n_fans, integrator, out);
+    else
+        trace_mixed_fans_kernel<STENCIL, 0><<<blocks, threads, 0, st>>>(g, fans, first, n_fans, integrator, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trace_fans(const GridDev &g, const FanDev *fans, const long long *first, int n_fans,
+                              long long n_total, int integrator, rt_ray_result *out, const LaunchPlan &lp,
+                              cudaStream_t st) {
+    if (n_total == 0) return cudaSuccess;
+    switch (lp.stencil) {
+        case RT_STENCIL_GATHER:
+            return launch_fans_s<RT_STENCIL_GATHER>(g, fans, first, n_fans, n_total, integrator, out, lp.threads, st);
+        case RT_STENCIL_TABLE:
+            return launch_fans_s<RT_STENCIL_TABLE>(g, fans, first, n_fans, n_total, integrator, out, lp.threads, st);
+        default:
+            return launch_fans_s<RT_STENCIL_QUAD>(g, fans, first, n_fans, n_total, integrator, out, lp.threads, st);
     }
 }
 

@@ -7,8 +7,15 @@
 // slot's stream and records an event.  The completion thread polls the
 // in-flight events, copies finished records to the caller's buffer and wakes
 // the waiters.  Requests therefore join the GPU while others are running.
+// With fusion on, mixed-precision requests of at most fuse_max_rays rays are
+// small: the dispatcher admits a small head request together with the queued
+// small requests that can share its launch (same grid, same integrator) up
+// to fuse_max_rays rays in total, and traces them as one four-lane launch (a
+// fused batch occupies one slot).  A GPU that one small fan leaves mostly
+// idle is filled by several.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -37,18 +44,22 @@ struct Request {
     Clock::time_point t_submit, t_admit, t_done;
     rt_err status = RT_OK;
     std::string msg;                   // rt_last_error text of a failed request
+    int batch_size = 1;                // requests in the launch that traced this one
     bool done = false;
 };
 
 struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t event = nullptr;
-    rt_ray_result *dev = nullptr;   // device records (cudaMallocAsync per request)
+    rt_ray_result *dev = nullptr;   // device records (cudaMallocAsync per admission)
     rt_ray_result *pinned = nullptr;
     size_t pinned_cap = 0;
-    std::shared_ptr<Request> req;   // null when free
-    bool armed = false;             // the request's work and event are queued: the completer may poll
+    std::vector<std::shared_ptr<Request>> reqs;  // the admitted batch (records back to back); empty when free
+    bool armed = false;             // the batch's work and event are queued: the completer may poll
 };
+
+// At most this many requests share one fused launch.
+constexpr int kMaxFused = 256;
 
 }  // namespace
 
@@ -70,29 +81,46 @@ namespace {
 
 double seconds(Clock::time_point a, Clock::time_point b) { return std::chrono::duration<double>(b - a).count(); }
 
+size_t batch_rays(const std::vector<std::shared_ptr<Request>> &b) {
+    size_t n = 0;
+    for (const auto &r : b) n += r->n;
+    return n;
+}
+
 void finish_locked(rt_server *s, Slot &slot, rt_err status) {
-    auto &r = *slot.req;
-    r.status = status;
-    if (status != RT_OK) r.msg = rt_last_error();  // the message is thread-local: keep it for the waiter
-    r.t_done = Clock::now();
-    r.done = true;
-    slot.req.reset();
+    const std::string msg = status != RT_OK ? rt_last_error() : "";  // thread-local: keep it for the waiters
+    const auto now = Clock::now();
+    for (auto &rp : slot.reqs) {
+        rp->status = status;
+        rp->msg = msg;
+        rp->t_done = now;
+        rp->done = true;
+    }
+    slot.reqs.clear();
     slot.armed = false;
     --s->inflight;
     s->cv_done.notify_all();
     s->cv_dispatch.notify_all();
 }
 
-// Starts request r on slot sl (called by the dispatcher with the lock released).
-rt_err start(rt_server *s, Slot &sl, Request &r) {
+// Small requests of a fusing server (always traced by the fused kernel).
+bool is_small(const rt_server *s, const Request &r) {
+    return s->cfg.fuse_max_rays > 0 && r.fan.precision == RT_MIXED && r.n <= (size_t)s->cfg.fuse_max_rays;
+}
+
+// Starts the batch of slot sl (called by the dispatcher with the lock released).
+rt_err start(rt_server *s, Slot &sl) {
     cudaSetDevice(s->device);
-    r.fan.freq_mhz = r.freq.data();
-    r.fan.el_deg = r.el.data();
-    r.fan.az_deg = r.az.data();
-    if (sl.pinned_cap < r.n) {
+    const size_t n = batch_rays(sl.reqs);
+    for (auto &rp : sl.reqs) {
+        rp->fan.freq_mhz = rp->freq.data();
+        rp->fan.el_deg = rp->el.data();
+        rp->fan.az_deg = rp->az.data();
+    }
+    if (sl.pinned_cap < n) {
         // grow by powers of two: freeing pinned memory synchronises the device
         size_t cap = 1024;
-        while (cap < r.n) cap *= 2;
+        while (cap < n) cap *= 2;
         if (sl.pinned) cudaFreeHost(sl.pinned);
         sl.pinned = nullptr;
         sl.pinned_cap = 0;
@@ -100,11 +128,20 @@ rt_err start(rt_server *s, Slot &sl, Request &r) {
             return rtgd_set_error(RT_ENOMEM, "server: pinned staging allocation failed");
         sl.pinned_cap = cap;
     }
-    if (cudaMallocAsync((void **)&sl.dev, r.n * sizeof(rt_ray_result), sl.stream) != cudaSuccess)
+    if (cudaMallocAsync((void **)&sl.dev, n * sizeof(rt_ray_result), sl.stream) != cudaSuccess)
         return rtgd_set_error(RT_ENOMEM, "server: device allocation failed");
-    const rt_launch_config *lc = &s->cfg.launch;
-    rt_err e = rtgd_queue_trace(r.grid, &r.fan, sl.dev, r.n, lc, sl.stream);
-    if (e == RT_OK && cudaMemcpyAsync(sl.pinned, sl.dev, r.n * sizeof(rt_ray_result), cudaMemcpyDeviceToHost,
+    const rt_launch_config &lc = s->cfg.launch;
+    rt_err e;
+    // a small request runs the fused kernel, alone or not, so its records do
+    // not depend on what shares its launch
+    if (!is_small(s, *sl.reqs[0])) {
+        e = rtgd_queue_trace(sl.reqs[0]->grid, &sl.reqs[0]->fan, sl.dev, n, &lc, sl.stream);
+    } else {
+        std::vector<const rt_fan_desc *> fans;
+        for (const auto &rp : sl.reqs) fans.push_back(&rp->fan);
+        e = rtgd_queue_trace_fans(sl.reqs[0]->grid, fans.data(), (int)fans.size(), sl.dev, n, &lc, sl.stream);
+    }
+    if (e == RT_OK && cudaMemcpyAsync(sl.pinned, sl.dev, n * sizeof(rt_ray_result), cudaMemcpyDeviceToHost,
                                       sl.stream) != cudaSuccess)
         e = rtgd_set_error(RT_ECUDA, "server: result copy failed");
     cudaFreeAsync(sl.dev, sl.stream);
@@ -122,10 +159,23 @@ void dispatch_loop(rt_server *s) {
             return (s->stopping && s->queue.empty()) || (!s->queue.empty() && s->inflight < (int)s->slots.size());
         });
         if (s->queue.empty()) return;  // stopping, nothing left to admit
-        // admission by device memory: the request's records + tables must fit above the reserve
+        // the batch: the head request, and with fusion the queued requests
+        // that can share its launch, in queue order, up to fuse_max_rays rays
+        std::vector<size_t> pick{0};
+        const Request &head = *s->queue.front();
+        size_t n_batch = head.n;
+        if (is_small(s, head)) {
+            for (size_t i = 1; i < s->queue.size() && pick.size() < (size_t)kMaxFused; ++i) {
+                const Request &q = *s->queue[i];
+                if (!is_small(s, q) || q.grid != head.grid || q.fan.integrator != head.fan.integrator) continue;
+                if (n_batch + q.n > (size_t)s->cfg.fuse_max_rays) continue;
+                pick.push_back(i);
+                n_batch += q.n;
+            }
+        }
+        // admission by device memory: the batch's records + tables must fit above the reserve
         size_t free_b = 0, total_b = 0;
-        auto req = s->queue.front();
-        const size_t need = req->n * sizeof(rt_ray_result) * 2 + 4096;
+        const size_t need = n_batch * sizeof(rt_ray_result) * 2 + 4096 * pick.size();
         lk.unlock();
         cudaMemGetInfo(&free_b, &total_b);
         lk.lock();
@@ -134,19 +184,30 @@ void dispatch_loop(rt_server *s) {
             s->cv_dispatch.wait_for(lk, std::chrono::milliseconds(2));
             continue;
         }
-        s->queue.pop_front();
+        // the queue only grows at its back while the lock was released, so
+        // the picked positions are still valid
+        std::vector<std::shared_ptr<Request>> batch;
+        for (size_t k = pick.size(); k-- > 0;) {
+            batch.push_back(s->queue[pick[k]]);
+            s->queue.erase(s->queue.begin() + (std::ptrdiff_t)pick[k]);
+        }
+        std::reverse(batch.begin(), batch.end());
         int idx = -1;
         for (size_t i = 0; i < s->slots.size(); ++i)
-            if (!s->slots[i].req) {
+            if (s->slots[i].reqs.empty()) {
                 idx = (int)i;
                 break;
             }
         Slot &sl = s->slots[idx];
-        sl.req = req;
+        sl.reqs = std::move(batch);
         ++s->inflight;
-        req->t_admit = Clock::now();
+        const auto now = Clock::now();
+        for (auto &rp : sl.reqs) {
+            rp->t_admit = now;
+            rp->batch_size = (int)sl.reqs.size();
+        }
         lk.unlock();
-        const rt_err e = start(s, sl, *req);
+        const rt_err e = start(s, sl);
         lk.lock();
         // until start() has recorded the slot's event, a query of that event
         // reports the previous request (or success, if never recorded)
@@ -162,14 +223,21 @@ void complete_loop(rt_server *s) {
         if (s->stopping && s->inflight == 0 && s->queue.empty()) return;
         bool any = false;
         for (auto &sl : s->slots) {
-            if (!sl.req) continue;
+            if (sl.reqs.empty()) continue;
             any = true;
             if (!sl.armed) continue;  // still being started by the dispatcher
             const cudaError_t q = cudaEventQuery(sl.event);
             if (q == cudaErrorNotReady) continue;
             rt_err st = RT_OK;
-            if (q == cudaSuccess) std::memcpy(sl.req->out_host, sl.pinned, sl.req->n * sizeof(rt_ray_result));
-            else st = rtgd_set_error(RT_ECUDA, cudaGetErrorString(q));
+            if (q == cudaSuccess) {
+                size_t off = 0;
+                for (auto &rp : sl.reqs) {
+                    std::memcpy(rp->out_host, sl.pinned + off, rp->n * sizeof(rt_ray_result));
+                    off += rp->n;
+                }
+            } else {
+                st = rtgd_set_error(RT_ECUDA, cudaGetErrorString(q));
+            }
             finish_locked(s, sl, st);
         }
         lk.unlock();
@@ -190,7 +258,10 @@ rt_err rt_server_create(const rt_server_config *cfg, rt_server **out) {
     if (cfg) c = *cfg;
     if (c.max_inflight == 0) c.max_inflight = 8;
     if (c.max_inflight < 1 || c.max_inflight > 64) return rtgd_set_error(RT_EINVAL, "max_inflight must be in 1..64");
-    if (c.reserved != 0) return rtgd_set_error(RT_EINVAL, "reserved field must be 0");
+    if (c.fuse_max_rays < 0) return rtgd_set_error(RT_EINVAL, "fuse_max_rays must be >= 0");
+    if (c.fuse_max_rays > 0 && (c.launch.kernel == RT_KERNEL_PERSISTENT ||
+                                (c.launch.lanes_per_ray != 0 && c.launch.lanes_per_ray != 4)))
+        return rtgd_set_error(RT_EINVAL, "fusion runs a plain kernel at four lanes per ray");
     int n = 0;
     if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) return rtgd_set_error(RT_EUNSUPPORTED, "no CUDA device available");
     auto *s = new rt_server();
@@ -260,7 +331,7 @@ rt_err rt_server_wait(rt_server *s, uint64_t ticket, double timeout_s, rt_reques
         stats->total_s = seconds(r->t_submit, r->t_done);
         stats->n_rays = (int64_t)r->n;
         stats->status = r->status;
-        stats->reserved = 0;
+        stats->batch_size = r->batch_size;
     }
     if (r->status != RT_OK) return rtgd_set_error(r->status, r->msg.c_str());
     return r->status;

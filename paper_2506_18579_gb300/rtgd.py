@@ -89,13 +89,13 @@ class rt_ionogram_desc(ctypes.Structure):
 
 
 class rt_server_config(ctypes.Structure):
-    _fields_ = [("max_inflight", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    _fields_ = [("max_inflight", ctypes.c_int32), ("fuse_max_rays", ctypes.c_int32),
                 ("mem_reserve_bytes", ctypes.c_size_t), ("launch", rt_launch_config)]
 
 
 class rt_request_stats(ctypes.Structure):
     _fields_ = [("queue_s", ctypes.c_double), ("run_s", ctypes.c_double), ("total_s", ctypes.c_double),
-                ("n_rays", ctypes.c_int64), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("n_rays", ctypes.c_int64), ("status", ctypes.c_int32), ("batch_size", ctypes.c_int32)]
 
 
 class rt_peaks(ctypes.Structure):
@@ -350,8 +350,9 @@ def rt_trace_device_noalloc(grid, fan, out_ptr, out_len, cfg=None, stream=None):
 class Server:
     """rt_server: continuous-batching request server on the current device."""
 
-    def __init__(self, max_inflight=8, mem_reserve_bytes=0, cfg=None):
-        c = rt_server_config(max_inflight, 0, mem_reserve_bytes, cfg if cfg is not None else rt_launch_config())
+    def __init__(self, max_inflight=8, mem_reserve_bytes=0, cfg=None, fuse_max_rays=0):
+        c = rt_server_config(max_inflight, fuse_max_rays, mem_reserve_bytes,
+                             cfg if cfg is not None else rt_launch_config())
         h = ctypes.c_void_p()
         _check(load().rt_server_create(ctypes.byref(c), ctypes.byref(h)))
         self.handle = h
