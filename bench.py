@@ -50,10 +50,10 @@ GATHER_BYTES = {"mixed": 65 * 4, "fp64": 64 * 8}
 # was captured from: a changed kernel reports traffic null.
 KERNEL_SOURCES = ("paper_2506_18579_gb300/csrc/rtgd_kernels.cu", "paper_2506_18579_gb300/csrc/rtgd_device.cuh")
 TRAFFIC = {
-    # profiles/trace_mixed_c2_fan.md: 26.68 MB read + 0.08 MB written
-    ("c2", 1, 3, 4): {"bytes_per_launch": 26760704, "source_sha256": "939725055bdcf6c5"},
-    # profiles/trace_mixed_c4_batch.md: 20.23 MB read + 1.26 MB written
-    ("c4", 1, 3, 1): {"bytes_per_launch": 21499392, "source_sha256": "939725055bdcf6c5"},
+    # profiles/trace_mixed_c2_fan.md: 26.70 MB read + 0.03 MB written
+    ("c2", 1, 3, 4): {"bytes_per_launch": 26728192, "source_sha256": "91c55e6b7720bda6"},
+    # profiles/trace_mixed_c4_batch.md: 20.28 MB read + 1.04 MB written
+    ("c4", 1, 3, 1): {"bytes_per_launch": 21322240, "source_sha256": "91c55e6b7720bda6"},
 }
 SMS = 152
 FP32_LANES_PER_SM = 128
@@ -112,7 +112,7 @@ def parse_args():
                    help="warm-up launches then one launch, nothing else (for ncu captures)")
     p.add_argument("--cpu-sample", type=int, default=0,
                    help="rays of the fan the CPU oracle baseline traces (0 = the whole fan)")
-    p.add_argument("--serve-fuse", type=int, default=32768,
+    p.add_argument("--serve-fuse", type=int, default=16384,
                    help="fuse_max_rays of the serving section's fused runs")
     p.add_argument("--serve-slots", type=int, default=8,
                    help="request server stream slots (requests in flight at once)")
@@ -731,7 +731,7 @@ def run_interpolants(rt, wl):
     return out
 
 
-def run_serving(rt, wl, seconds, seed=9, slots=8, fuse=32768):
+def run_serving(rt, wl, seconds, seed=9, slots=8, fuse=16384):
     """Serving form: a Poisson stream of uneven fan requests (1..100k rays,
     ionogram-synthesis and OTHR-registration shapes) over four resident grids
     (21x21x61 .. 181x361x301), through the continuous-batching server.  The

@@ -326,20 +326,21 @@ typedef struct rt_server rt_server;
 
 typedef struct rt_server_config {
     int32_t max_inflight;        /* stream slots, 1..64 (0 = 8) */
-    int32_t fuse_max_rays;       /* 0 = one launch per request.  > 0: mixed requests of at most
-                                    fuse_max_rays rays are small and are fused.  The dispatcher admits
-                                    a small head request together with the queued small requests on the
-                                    same grid with the same integrator, in queue order, up to
-                                    fuse_max_rays rays in total and 256 requests, and traces them as one
-                                    launch in one slot.  Every small request, alone or not, runs the
-                                    fused kernel: four lanes per ray, the stencil, block size and ray
-                                    order of `launch` (whose kernel must be AUTO or PLAIN and
-                                    lanes_per_ray 0 or 4).  Its records therefore do not depend on what
-                                    shares its launch; they equal those of rt_trace on the plain kernel
-                                    at four lanes per ray up to float rounding (the two kernels are
-                                    compiled apart).  Other requests run as without fusion.  A useful
-                                    value is about one wave of resident four-lane groups (152 SMs x 2
-                                    blocks x 128 threads / 4 = 9,728 rays). */
+    int32_t fuse_max_rays;       /* 0 = one launch per request.  > 0: fusion.  Small requests are the
+                                    mixed ones that the automatic lane choice would trace at four lanes
+                                    per ray on their own (at most a quarter of the resident lanes:
+                                    14,592 rays on 152 SMs with the default block) and of at most
+                                    fuse_max_rays rays.  The dispatcher admits a small head request
+                                    together with the queued small requests on the same grid with the
+                                    same integrator, in queue order, up to fuse_max_rays rays in total
+                                    and 256 requests, and traces them as one launch in one slot.  Every
+                                    small request, alone or not, runs the fused kernel: four lanes per
+                                    ray, the stencil, block size and ray order of `launch` (whose kernel
+                                    must be AUTO or PLAIN and lanes_per_ray 0 or 4).  Its records
+                                    therefore do not depend on what shares its launch; they equal those
+                                    of rt_trace on the plain kernel at four lanes per ray up to float
+                                    rounding (the two kernels are compiled apart).  Other requests run
+                                    as without fusion. */
     size_t mem_reserve_bytes;    /* device memory kept free by admission */
     rt_launch_config launch;     /* kernel choice for every request (zero = library defaults) */
 } rt_server_config;

@@ -400,6 +400,16 @@ rt_err rtgd_queue_trace_fans(const rt_grid *grid, const rt_fan_desc *const *fans
     return RT_OK;
 }
 
+rt_err rtgd_four_lane_limit(int device, const rt_launch_config *cfg, size_t *limit) {
+    const int stencil = cfg && cfg->stencil != RT_STENCIL_AUTO ? cfg->stencil : RT_STENCIL_QUAD;
+    const int threads = cfg && cfg->block_threads ? cfg->block_threads : 128;
+    int occ = 0;
+    CUDA_TRY(persistent_occupancy(stencil, 1, threads, &occ));
+    // the automatic lane choice gives four lanes to fans of at most a quarter of the resident lanes
+    *limit = (size_t)props(device).sms * (size_t)std::max(occ, 1) * (size_t)threads / 4;
+    return RT_OK;
+}
+
 rt_err rtgd_set_error(rt_err code, const char *msg) { return fail(code, "%s", msg); }
 
 extern "C" {

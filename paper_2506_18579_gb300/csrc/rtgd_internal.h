@@ -61,6 +61,9 @@ rt_err rtgd_queue_trace(const rt_grid *grid, const rt_fan_desc *fan, rt_ray_resu
 rt_err rtgd_queue_trace_fans(const rt_grid *grid, const rt_fan_desc *const *fans, int n_fans, rt_ray_result *out_dev,
                              size_t out_len, const rt_launch_config *cfg, cudaStream_t st);
 rt_err rtgd_set_error(rt_err code, const char *msg);
+// Largest fan that the automatic lane choice traces at four lanes per ray
+// on this device with cfg's stencil and block size.
+rt_err rtgd_four_lane_limit(int device, const rt_launch_config *cfg, size_t *limit);
 
 namespace rtgd {
 

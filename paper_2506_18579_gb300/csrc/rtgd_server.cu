@@ -7,12 +7,12 @@
 // slot's stream and records an event.  The completion thread polls the
 // in-flight events, copies finished records to the caller's buffer and wakes
 // the waiters.  Requests therefore join the GPU while others are running.
-// With fusion on, mixed-precision requests of at most fuse_max_rays rays are
-// small: the dispatcher admits a small head request together with the queued
-// small requests that can share its launch (same grid, same integrator) up
-// to fuse_max_rays rays in total, and traces them as one four-lane launch (a
-// fused batch occupies one slot).  A GPU that one small fan leaves mostly
-// idle is filled by several.
+// With fusion on, mixed-precision requests that would run at four lanes per
+// ray on their own are small: the dispatcher admits a small head request
+// together with the queued small requests that can share its launch (same
+// grid, same integrator) up to fuse_max_rays rays in total, and traces them
+// as one four-lane launch (a fused batch occupies one slot).  A GPU that one
+// small fan leaves mostly idle is filled by several.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -73,6 +73,7 @@ struct rt_server {
     std::condition_variable cv_dispatch, cv_done;
     std::thread dispatcher, completer;
     uint64_t next_ticket = 1;
+    size_t small_limit = 0;  // fusion: largest small request (rays)
     int inflight = 0;
     bool stopping = false;
 };
@@ -105,7 +106,7 @@ void finish_locked(rt_server *s, Slot &slot, rt_err status) {
 
 // Small requests of a fusing server (always traced by the fused kernel).
 bool is_small(const rt_server *s, const Request &r) {
-    return s->cfg.fuse_max_rays > 0 && r.fan.precision == RT_MIXED && r.n <= (size_t)s->cfg.fuse_max_rays;
+    return s->cfg.fuse_max_rays > 0 && r.fan.precision == RT_MIXED && r.n <= s->small_limit;
 }
 
 // Starts the batch of slot sl (called by the dispatcher with the lock released).
@@ -264,9 +265,17 @@ rt_err rt_server_create(const rt_server_config *cfg, rt_server **out) {
         return rtgd_set_error(RT_EINVAL, "fusion runs a plain kernel at four lanes per ray");
     int n = 0;
     if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) return rtgd_set_error(RT_EUNSUPPORTED, "no CUDA device available");
+    int device = 0;
+    cudaGetDevice(&device);
+    size_t four_lane = 0;
+    if (c.fuse_max_rays > 0) {
+        const rt_err e = rtgd_four_lane_limit(device, &c.launch, &four_lane);
+        if (e != RT_OK) return e;
+    }
     auto *s = new rt_server();
     s->cfg = c;
-    cudaGetDevice(&s->device);
+    s->device = device;
+    s->small_limit = std::min(four_lane, (size_t)std::max(c.fuse_max_rays, 0));
     s->slots.resize(c.max_inflight);
     for (auto &sl : s->slots) {
         if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
