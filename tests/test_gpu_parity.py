@@ -193,20 +193,22 @@ def test_ragged_and_tiny_fans(orc):
                 _close64(gm[ok], ref9[ok], km=MIX_KM, deg=MIX_DEG)
 
 
-def test_fused_requests_match_oracle(orc):
+@pytest.mark.parametrize("interp,stencil", [("gd", rt.RT_STENCIL_QUAD), ("gd", rt.RT_STENCIL_TABLE),
+                                            ("cr", rt.RT_STENCIL_GATHER)])
+def test_fused_requests_match_oracle(orc, interp, stencil):
     """The request server's fused kernel: the small C2-shaped fan split into
     one request per (frequency, azimuth), submitted at once to a fusing
     server (so that requests share launches), stitched back into fan order
-    and compared with the oracle."""
+    and compared with the oracle (GD and the Catmull-Rom option)."""
     w = _c2_small()
     # elevations 1.25 deg apart, so that neighbours show where a ray is near a boundary
     spec = w.fan.replace(rtol=1e-9, freq_mhz=[8.0, 12.0], el_deg=np.linspace(5.0, 55.0, 41))
-    g = rt.Grid(w.grid, w.ne)
+    g = rt.Grid(w.grid, w.ne, table=stencil == rt.RT_STENCIL_TABLE, interp=interp)
     n_f, n_el, n_az = len(spec.freq_mhz), len(spec.el_deg), len(spec.az_deg)
     n_m = spec.n_rays // (n_f * n_el * n_az)
     parts = [(i, a, spec.replace(freq_mhz=[spec.freq_mhz[i]], az_deg=[spec.az_deg[a]]))
              for i in range(n_f) for a in range(n_az)]
-    srv = rt.Server(max_inflight=1, cfg=rt.launch_config(stencil=rt.RT_STENCIL_QUAD), fuse_max_rays=100000)
+    srv = rt.Server(max_inflight=1, cfg=rt.launch_config(stencil=stencil), fuse_max_rays=100000)
     fans = [rt.Fan(p, rt.RT_MIXED) for _, _, p in parts]
     tickets = [srv.submit(g, f) for f in fans]
     full = np.zeros(spec.n_rays, dtype=rt.RESULT_DTYPE)
@@ -219,7 +221,7 @@ def test_fused_requests_match_oracle(orc):
         view[i, :, :, a] = out.reshape(n_m, n_el)
     srv.close()
     assert max(sizes) > 1
-    ref = orc.trace_fan(orc.Grid(w.grid, w.ne), spec)
+    ref = orc.trace_fan(orc.Grid(w.grid, w.ne, interp=interp), spec)
     ok = ~near_boundary(ref, spec)
     assert ok.sum() >= 200  # of 984 rays; the rest neighbour a status change or a range jump
     _close64(full[ok], ref[ok], km=MIX_KM, deg=MIX_DEG)
