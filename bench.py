@@ -506,7 +506,11 @@ def run_ours(args):
                                                          else peaks["fp64_fma_tflops"]),
                          "gather": {"bytes_per_stage_eval": GATHER_BYTES[args.precision],
                                     "achieved_gbs": evals * GATHER_BYTES[args.precision] / sec / 1e9,
-                                    "l2_read_peak_gbs": peaks["l2_read_gbs"]}},
+                                    "l2_read_peak_gbs": peaks["l2_read_gbs"]},
+                         # the fan leaves most of the GPU idle: its floor is its longest
+                         # ray's dependent chain of stage evaluations, traced alone
+                         "latency_floor": {"longest_ray_alone_ms": alone_ms, "fan_ms": mean_ms,
+                                           "frac": alone_ms / mean_ms}},
             "cpu_baseline": cpu,
             "e2e": {"value": n * world / e2e_s, "unit": "rays/s", "h2d_bytes_per_step": fan.host_bytes,
                     "d2h_bytes_per_step": n * 64},
