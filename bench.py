@@ -102,9 +102,10 @@ def parse_args():
                    help="persistent kernel with --kernel: resident blocks per SM (0 = occupancy limit)")
     p.add_argument("--lanes", type=int, default=0, choices=[0, 1, 2, 4],
                    help="lanes per ray with --kernel (0 = the library's choice)")
-    p.add_argument("--workload", choices=["c2", "c4"], default="c2",
+    p.add_argument("--workload", choices=["c2", "c4", "c5"], default="c2",
                    help="fan for the --profile and --one-ray modes: c2 = the anisotropic 24,840-ray fan "
-                        "(the benchmark's workload), c4 = the 495,122-ray ionogram-synthesis batch")
+                        "(the benchmark's workload), c4 = the 495,122-ray ionogram-synthesis batch, "
+                        "c5 = small serving requests fused into one launch (--profile only)")
     p.add_argument("--one-ray", type=int, default=None,
                    help="latency mode: trace only this canonical ray of the fan (alone) --steps times "
                         "and print its time per stage evaluation")
@@ -290,6 +291,11 @@ def run_ours(args):
     from paper_2506_18579_gb300 import workloads as wl
 
     rtbuild.build()
+    if args.workload == "c5":
+        if not args.profile:
+            raise SystemExit("--workload c5 is for the --profile mode (the serving section times it)")
+        profile_fused(rt, wl, args.serve_fuse, max(args.warmup, 1) + 1)
+        return
     if args.workload == "c4" and not (args.profile or args.one_ray is not None):
         raise SystemExit("--workload c4 is for the --profile and --one-ray modes (the batch section times it)")
     w = wl.config2() if args.workload == "c2" else wl.config4()
@@ -774,6 +780,33 @@ def run_interpolants(rt, wl):
     for gr in grids.values():
         gr.close()
     return out
+
+
+def profile_fused(rt, wl, fuse, rounds):
+    """For ncu: `rounds` rounds on the 91x181x151 serving grid, each one large
+    request (which runs unfused and keeps the one slot busy) followed by 64
+    small requests, which queue behind it and go out as fused launches of at
+    most `fuse` rays."""
+    grids = wl.serving_grids()
+    gi = 2
+    spec_g, ne = grids[gi]
+    h = rt.Grid(spec_g, ne)
+    reqs = [f for g, f in wl.serving_requests(2000, 9, [g for g, _ in grids]) if g == gi]
+    sizes = [rt.Fan(f).n_rays for f in reqs]
+    big = reqs[int(np.argmax(sizes))]
+    small = [f for f, n in zip(reqs, sizes) if n <= 2000][:64]
+    srv = rt.Server(max_inflight=1, fuse_max_rays=fuse)
+    per_launch = []
+    for _ in range(rounds):
+        fans = [rt.Fan(big)] + [rt.Fan(f) for f in small]
+        tickets = [srv.submit(h, f) for f in fans]
+        per_launch = [srv.wait(t[0], timeout_s=600.0).batch_size for t in tickets]
+    srv.close()
+    h.close()
+    print(json.dumps({"profile_run": True, "workload": "fused small requests", "rounds": rounds,
+                      "large_request_rays": int(max(sizes)), "small_requests": len(small),
+                      "small_rays": int(sum(rt.Fan(f).n_rays for f in small)),
+                      "requests_per_launch_last_round": per_launch[1:]}), flush=True)
 
 
 def run_serving(rt, wl, seconds, seed=9, slots=8, fuse=16384):
