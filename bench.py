@@ -50,9 +50,10 @@ GATHER_BYTES = {"mixed": 65 * 4, "fp64": 64 * 8}
 # was captured from: a changed kernel reports traffic null.
 KERNEL_SOURCES = ("paper_2506_18579_gb300/csrc/rtgd_kernels.cu", "paper_2506_18579_gb300/csrc/rtgd_device.cuh")
 TRAFFIC = {
-    # profiles/trace_mixed_c2_fan.md: 26.70 MB read + 0.03 MB written
-    ("c2", 1, 3, 4): {"bytes_per_launch": 26728192, "source_sha256": "91c55e6b7720bda6"},
-    # profiles/trace_mixed_c4_batch.md: 20.28 MB read + 1.04 MB written
+    # profiles/trace_mixed_c2_fan.md: 27.03 MB read + 0.04 MB written (96-thread blocks;
+    # 26.73 MB with 128: the block size moves it by ~1 %)
+    ("c2", 1, 3, 4): {"bytes_per_launch": 27071744, "source_sha256": "91c55e6b7720bda6"},
+    # profiles/trace_mixed_c4_batch.md: 20.28 MB read + 1.04 MB written (128-thread blocks)
     ("c4", 1, 3, 1): {"bytes_per_launch": 21322240, "source_sha256": "91c55e6b7720bda6"},
 }
 SMS = 152
@@ -318,7 +319,8 @@ def run_ours(args):
             order=rt.RT_ORDER_CANONICAL if args.order == "canonical" else rt.RT_ORDER_ELEVATION_FASTEST,
             blocks_per_sm=args.blocks_per_sm, lanes_per_ray=args.lanes)
     elif prec == rt.RT_MIXED and not args.no_tune:
-        cfg, tune_ms = rt.rt_tune(grid, fan, max_rays=8192, stream=sptr)
+        # timed on the whole fan: a strided sub-fan has other slowest rays
+        cfg, tune_ms = rt.rt_tune(grid, fan, max_rays=n, stream=sptr)
     if args.one_ray is not None:
         run_one_ray(args, rt, wl, torch, grid, spec, prec, cfg)
         grid.close()
@@ -424,7 +426,7 @@ def run_ours(args):
         out8 = torch.empty(n * 64, dtype=torch.uint8, device="cuda")
         cfg8 = cfg
         if args.kernel is None and prec == rt.RT_MIXED and not args.no_tune:
-            cfg8, _ = rt.rt_tune(grid, fan8, max_rays=8192, stream=sptr)
+            cfg8, _ = rt.rt_tune(grid, fan8, max_rays=n, stream=sptr)
         for _ in range(2):
             rt.rt_trace_device(grid, fan8, out8.data_ptr(), n, cfg=cfg8, stream=sptr)
         t8 = []

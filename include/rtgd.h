@@ -243,7 +243,7 @@ rt_err rt_trace_device_noalloc(const rt_grid *grid, const rt_fan_desc *fan, rt_r
                                size_t out_len, const rt_launch_config *cfg, void *stream);
 
 /* Autotuner: times the candidate launch configurations (kernel x stencil x
- * claim order x lanes per ray x 64 or 128 threads per block) for this grid
+ * claim order x lanes per ray x 32, 64, 96 or 128 threads per block) for this grid
  * and fan shape on `stream`, each candidate on a strided sub-fan of at most
  * max_rays rays (0 = 65536; one warm-up and three timed launches each,
  * every timed launch after a 256 MiB fill that evicts L2), and returns the

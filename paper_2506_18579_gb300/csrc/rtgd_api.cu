@@ -608,7 +608,7 @@ rt_err rt_tune(const rt_grid *grid, const rt_fan_desc *fan, size_t max_rays, voi
             for (int stencil : {RT_STENCIL_GATHER, RT_STENCIL_QUAD, RT_STENCIL_TABLE})
                 for (int order : {RT_ORDER_CANONICAL, RT_ORDER_ELEVATION_FASTEST})
                     for (int lanes : {1, 2, 4})
-                        for (int threads : {64, 128}) {
+                        for (int threads : {32, 64, 96, 128}) {
                         if (throughput && lanes > 1) continue;
                         if (stencil == RT_STENCIL_TABLE && !grid->table) continue;
                         c.kernel = kernel;
