@@ -550,6 +550,19 @@ def one_ray_spec(wl, spec, index):
                         az_deg=np.array([az[ia]]))
 
 
+def richardson_extrapolate(y_h, y_h2, y_h4, floor=1e-9):
+    """Richardson extrapolation of three runs at steps h, h/2, h/4: the
+    observed order p = median over entries of log2(|y_h - y_h2| / |y_h2 -
+    y_h4|) (entries whose last difference is below `floor` are rounding and
+    left out; p = 4 if none remain), and the extrapolated values y_h4 +
+    (y_h4 - y_h2) / (2^p - 1).  Returns (extrapolated, p)."""
+    y_h, y_h2, y_h4 = (np.asarray(a, dtype=np.float64) for a in (y_h, y_h2, y_h4))
+    d1, d2 = np.abs(y_h - y_h2), np.abs(y_h2 - y_h4)
+    big = d2 > floor
+    p = float(np.median(np.log2(d1[big] / d2[big]))) if big.any() else 4.0
+    return y_h4 + (y_h4 - y_h2) / (2.0 ** p - 1.0), p
+
+
 def richardson_table(rt, wl, grid, spec, prec, cfg, stream):
     """Per-output errors against a Richardson-extrapolated reference (Sec.
     IV-B) on a regular sub-fan of the fan (every 5th elevation, every 4th
@@ -573,10 +586,7 @@ def richardson_table(rt, wl, grid, spec, prec, cfg, stream):
     for r in runs[:2] + [ours, same_rtol, conv]:
         ok &= r["status"] == st
     fields = ("group_path_km", "ground_range_km", "az_dev_deg", "apogee_km")
-    d1 = np.abs(runs[0]["group_path_km"] - runs[1]["group_path_km"])[ok]
-    d2 = np.abs(runs[1]["group_path_km"] - runs[2]["group_path_km"])[ok]
-    big = d2 > 1e-9  # below this the differences are rounding, not truncation
-    order = float(np.median(np.log2(d1[big] / d2[big]))) if big.any() else 4.0
+    _, order = richardson_extrapolate(*(r["group_path_km"][ok] for r in runs))
     ref = {f: runs[2][f] + (runs[2][f] - runs[1][f]) / (2.0 ** order - 1.0) for f in fields}
 
     def err(r):

@@ -1,6 +1,7 @@
 """Host-side helpers of bench.py (no GPU): the one-ray fan used for the
-critical-path measurement must be the canonical ray it names, and the
-boundary filter must flag both neighbours of a jump."""
+critical-path measurement must be the canonical ray it names, the boundary
+filter must flag both neighbours of a jump, and the Richardson extrapolation
+must recover a known limit and order."""
 import os
 import sys
 
@@ -38,3 +39,21 @@ def test_near_boundary_flags_both_neighbours_of_a_jump():
     flag = bench.near_boundary(res, spec).reshape(n_el, n_az)
     assert not flag[:, 0].any()
     assert flag[5, 1] and flag[6, 1] and flag[:, 1].sum() == 2
+
+
+def test_richardson_extrapolation_recovers_the_limit_and_the_order():
+    """y(h) = y* + c h^p: three steps h, h/2, h/4 give back p and y* (to
+    rounding), for the fourth order and for the order ~2 that fixed-step RK4
+    shows where the field's gradient is only continuous."""
+    rng = np.random.default_rng(3)
+    y_star = rng.uniform(100.0, 3000.0, 50)
+    c = rng.uniform(0.5, 2.0, 50)
+    for p_true in (4.0, 2.25):
+        ys = [y_star + c * h ** p_true for h in (1.0, 0.5, 0.25)]
+        ref, p = bench.richardson_extrapolate(*ys)
+        assert abs(p - p_true) < 1e-9
+        assert np.max(np.abs(ref - y_star)) < 1e-9 * np.max(y_star)
+    # differences below the floor are rounding: left out, order 4 by default
+    flat = [np.full(5, 7.0)] * 3
+    ref, p = bench.richardson_extrapolate(*flat)
+    assert p == 4.0 and np.all(ref == 7.0)
