@@ -193,16 +193,19 @@ def test_ragged_and_tiny_fans(orc):
                 _close64(gm[ok], ref9[ok], km=MIX_KM, deg=MIX_DEG)
 
 
-@pytest.mark.parametrize("interp,stencil", [("gd", rt.RT_STENCIL_QUAD), ("gd", rt.RT_STENCIL_TABLE),
-                                            ("cr", rt.RT_STENCIL_GATHER)])
-def test_fused_requests_match_oracle(orc, interp, stencil):
+@pytest.mark.parametrize("interp,stencil,integrator", [("gd", rt.RT_STENCIL_QUAD, wl.RKF45),
+                                                       ("gd", rt.RT_STENCIL_TABLE, wl.RKF45),
+                                                       ("cr", rt.RT_STENCIL_GATHER, wl.RKF45),
+                                                       ("gd", rt.RT_STENCIL_QUAD, wl.RK4)])
+def test_fused_requests_match_oracle(orc, interp, stencil, integrator):
     """The request server's fused kernel: the small C2-shaped fan split into
     one request per (frequency, azimuth), submitted at once to a fusing
     server (so that requests share launches), stitched back into fan order
     and compared with the oracle (GD and the Catmull-Rom option)."""
     w = _c2_small()
     # elevations 1.25 deg apart, so that neighbours show where a ray is near a boundary
-    spec = w.fan.replace(rtol=1e-9, freq_mhz=[8.0, 12.0], el_deg=np.linspace(5.0, 55.0, 41))
+    spec = w.fan.replace(rtol=1e-9, freq_mhz=[8.0, 12.0], el_deg=np.linspace(5.0, 55.0, 41),
+                         integrator=integrator, h_km=1.0 if integrator == wl.RKF45 else 2.0)
     g = rt.Grid(w.grid, w.ne, table=stencil == rt.RT_STENCIL_TABLE, interp=interp)
     n_f, n_el, n_az = len(spec.freq_mhz), len(spec.el_deg), len(spec.az_deg)
     n_m = spec.n_rays // (n_f * n_el * n_az)
