@@ -224,6 +224,28 @@ rt_err rt_trace(const rt_grid *grid, const rt_fan_desc *fan, rt_ray_result *out_
 rt_err rt_trace_device(const rt_grid *grid, const rt_fan_desc *fan, rt_ray_result *out_dev,
                        size_t out_len, const rt_launch_config *cfg, void *stream);
 
+/* Several fans on one grid in one launch (e.g. the fans of several
+ * transmitters, or many small requests): fans[0..n_fans-1] (1 <= n_fans <=
+ * 4096), all RT_MIXED and with one integrator.  out_dev (device memory) receives
+ * their records fan after fan: fan k's rt_fan_size(fans[k]) records start
+ * after those of fans 0..k-1, each fan in its own canonical order; out_len
+ * must cover them all.  The launch runs four lanes per ray with cfg's
+ * stencil, block size and ray order (cfg->kernel must be AUTO or PLAIN and
+ * cfg->lanes_per_ray 0 or 4; cfg may be NULL).  A fan's records do not
+ * depend on the other fans of the launch.  They equal those of
+ * rt_trace_device with four lanes per ray on the plain kernel up to float
+ * rounding, because the two kernels are compiled apart.  This is the
+ * kernel a request server with fuse_max_rays > 0 runs for small requests.
+ * Worth it for fans that each leave the GPU mostly idle (up to a quarter of
+ * its resident lanes).  Asynchronous like rt_trace_device: the fan arrays
+ * are read before return; scratch is allocated and released stream-ordered.
+ * Errors: RT_EINVAL (null pointers, n_fans out of range, an invalid or FP64
+ * fan, mixed integrators, out_len too small, a grid on another device, bad
+ * cfg), RT_ENOMEM, RT_ECUDA, RT_EUNSUPPORTED. */
+rt_err rt_trace_fans_device(const rt_grid *grid, const rt_fan_desc *const *fans, int32_t n_fans,
+                            rt_ray_result *out_dev, size_t out_len, const rt_launch_config *cfg,
+                            void *stream);
+
 /* Same as rt_trace_device, for callers that cannot allocate device memory
  * while they trace (an allocator that must not be re-entered, a fixed device
  * memory budget, device memory owned by another runtime).  This call makes no

@@ -533,6 +533,19 @@ rt_err rt_trace_device(const rt_grid *grid, const rt_fan_desc *fan, rt_ray_resul
     return queue_trace(grid, fan, out_dev, out_len, cfg, (cudaStream_t)stream);
 }
 
+rt_err rt_trace_fans_device(const rt_grid *grid, const rt_fan_desc *const *fans, int32_t n_fans,
+                            rt_ray_result *out_dev, size_t out_len, const rt_launch_config *cfg, void *stream) {
+    if (n_fans < 1 || n_fans > 4096) return fail(RT_EINVAL, "n_fans must be in 1..4096 (got %d)", n_fans);
+    if (!fans) return fail(RT_EINVAL, "fans is NULL");
+    for (int k = 0; k < n_fans; ++k)
+        if (!fans[k]) return fail(RT_EINVAL, "fans[%d] is NULL", k);
+    if (cfg && cfg->kernel != RT_KERNEL_AUTO && cfg->kernel != RT_KERNEL_PLAIN)
+        return fail(RT_EINVAL, "rt_trace_fans_device runs a plain kernel (cfg->kernel AUTO or PLAIN)");
+    if (cfg && cfg->lanes_per_ray != 0 && cfg->lanes_per_ray != 4)
+        return fail(RT_EINVAL, "rt_trace_fans_device runs four lanes per ray (cfg->lanes_per_ray 0 or 4)");
+    return rtgd_queue_trace_fans(grid, fans, n_fans, out_dev, out_len, cfg, (cudaStream_t)stream);
+}
+
 rt_err rt_trace(const rt_grid *grid, const rt_fan_desc *fan, rt_ray_result *out_host, size_t out_len,
                 const rt_launch_config *cfg, void *stream) {
     if (!out_host) return fail(RT_EINVAL, "out_host is NULL");

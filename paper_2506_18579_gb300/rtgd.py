@@ -29,7 +29,7 @@ RT_STENCIL_AUTO, RT_STENCIL_GATHER, RT_STENCIL_QUAD, RT_STENCIL_TABLE = 0, 1, 2,
 RT_ORDER_CANONICAL, RT_ORDER_ELEVATION_FASTEST = 0, 1
 
 EXPORTED = ["rt_grid_create", "rt_grid_destroy", "rt_grid_device_bytes", "rt_fan_size",
-            "rt_trace", "rt_trace_device", "rt_tune", "rt_eval_rhs", "rt_last_error",
+            "rt_trace", "rt_trace_device", "rt_trace_fans_device", "rt_tune", "rt_eval_rhs", "rt_last_error",
             "rt_version", "rt_plan_create", "rt_plan_rays", "rt_plan_execute", "rt_plan_destroy",
             "rt_ionogram", "rt_trace_device_noalloc", "rt_server_create", "rt_server_submit",
             "rt_server_wait", "rt_server_destroy", "rt_measure_peaks"]
@@ -140,6 +140,9 @@ def load(path=None):
     L.rt_trace_device.argtypes = [vp, ctypes.POINTER(rt_fan_desc), vp, sz,
                                   ctypes.POINTER(rt_launch_config), vp]
     L.rt_trace_device.restype = ctypes.c_int
+    L.rt_trace_fans_device.argtypes = [vp, ctypes.POINTER(ctypes.POINTER(rt_fan_desc)), ctypes.c_int32, vp, sz,
+                                       ctypes.POINTER(rt_launch_config), vp]
+    L.rt_trace_fans_device.restype = ctypes.c_int
     L.rt_trace_device_noalloc.argtypes = [vp, ctypes.POINTER(rt_fan_desc), vp, sz,
                                           ctypes.POINTER(rt_launch_config), vp]
     L.rt_trace_device_noalloc.restype = ctypes.c_int
@@ -291,6 +294,14 @@ def rt_trace_device(grid, fan, out_ptr, out_len, cfg=None, stream=None):
     """Asynchronous trace into device memory (e.g. torch tensor .data_ptr())."""
     _check(load().rt_trace_device(grid.handle, ctypes.byref(fan.desc), ctypes.c_void_p(out_ptr),
                                   out_len, _cfg_ptr(cfg), stream))
+
+
+def rt_trace_fans_device(grid, fans, out_ptr, out_len, cfg=None, stream=None):
+    """Several fans (Fan objects) on one grid in one launch into device memory;
+    records fan after fan."""
+    arr = (ctypes.POINTER(rt_fan_desc) * max(len(fans), 1))(*[ctypes.pointer(f.desc) for f in fans])
+    _check(load().rt_trace_fans_device(grid.handle, arr, len(fans), ctypes.c_void_p(out_ptr), out_len,
+                                       _cfg_ptr(cfg), stream))
 
 
 class Plan:

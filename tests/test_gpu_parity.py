@@ -230,6 +230,59 @@ def test_fused_requests_match_oracle(orc, interp, stencil, integrator):
     _close64(full[ok], ref[ok], km=MIX_KM, deg=MIX_DEG)
 
 
+def test_trace_fans_device_matches_oracle_and_each_fan_alone(orc):
+    """rt_trace_fans_device: fans of two transmitters 400 km apart and of
+    several frequencies in one launch.  The records come fan after fan.
+    Each fan's records equal, bit for bit, those of the same fan traced
+    alone by the same call, and match the oracle."""
+    torch = pytest.importorskip("torch")
+    w = _c2_small()
+    g = rt.Grid(w.grid, w.ne)
+    og = orc.Grid(w.grid, w.ne)
+    base = w.fan.replace(rtol=1e-9, el_deg=np.linspace(5.0, 55.0, 41), az_deg=[0.0, 120.0, 240.0])
+    specs = [base.replace(freq_mhz=[8.0]), base.replace(freq_mhz=[12.0], tx_lat_deg=base.tx_lat_deg + 2.0),
+             base.replace(freq_mhz=[10.0], modes=wl.MODE_O), base.replace(freq_mhz=[14.0], el_deg=[30.0], az_deg=[45.0])]
+    fans = [rt.Fan(sp, rt.RT_MIXED) for sp in specs]
+    sizes = [f.n_rays for f in fans]
+    n = sum(sizes)
+    cfg = rt.launch_config(stencil=rt.RT_STENCIL_QUAD)
+    out = torch.zeros(n * 64, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.current_stream()
+    rt.rt_trace_fans_device(g, fans, out.data_ptr(), n, cfg=cfg, stream=s.cuda_stream)
+    s.synchronize()
+    res = rt.results_view(out.cpu().numpy(), n)
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    for k, (sp, f) in enumerate(zip(specs, fans)):
+        part = res[off[k]:off[k + 1]]
+        one = torch.zeros(f.n_rays * 64, dtype=torch.uint8, device="cuda")
+        rt.rt_trace_fans_device(g, [f], one.data_ptr(), f.n_rays, cfg=cfg, stream=s.cuda_stream)
+        s.synchronize()
+        assert part.tobytes() == rt.results_view(one.cpu().numpy(), f.n_rays).tobytes(), k
+        ref = orc.trace_fan(og, sp)
+        ok = ~near_boundary(ref, sp) if len(sp.el_deg) > 1 else np.ones(f.n_rays, bool)
+        assert ok.sum() >= min(f.n_rays, 30)
+        _close64(part[ok], ref[ok], km=MIX_KM, deg=MIX_DEG)
+
+
+def test_trace_fans_device_refuses_what_it_cannot_fuse():
+    torch = pytest.importorskip("torch")
+    w = _c2_small()
+    g = rt.Grid(w.grid, w.ne)
+    mixed = rt.Fan(w.fan, rt.RT_MIXED)
+    out = torch.zeros(mixed.n_rays * 2 * 64, dtype=torch.uint8, device="cuda")
+    bad = [([], None), ([rt.Fan(w.fan, rt.RT_FP64)], None),
+           ([mixed, rt.Fan(w.fan.replace(integrator=wl.RK4), rt.RT_MIXED)], None),
+           ([mixed], rt.launch_config(kernel=rt.RT_KERNEL_PERSISTENT)),
+           ([mixed], rt.launch_config(lanes_per_ray=1))]
+    for fans, cfg in bad:
+        with pytest.raises(rt.RtError) as ei:
+            rt.rt_trace_fans_device(g, fans, out.data_ptr(), mixed.n_rays * 2, cfg=cfg)
+        assert ei.value.code == rt.RT_EINVAL
+    with pytest.raises(rt.RtError) as ei:  # out_len below the rays of both fans
+        rt.rt_trace_fans_device(g, [mixed, mixed], out.data_ptr(), mixed.n_rays * 2 - 1)
+    assert ei.value.code == rt.RT_EINVAL
+
+
 def test_statuses_match_oracle(orc):
     w = wl.config1()
     g = rt.Grid(w.grid, w.ne)
