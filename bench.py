@@ -794,6 +794,64 @@ def run_interpolants(rt, wl):
     return out
 
 
+def small_fans_compare(rt, wl, reps=5):
+    """The same 64 small fans (1-2,000 rays each, from the serving mix on the
+    91x181x151 grid) traced three ways: one launch per fan on one stream, one
+    launch per fan spread over 8 streams, and one rt_trace_fans_device
+    launch.  Median wall time of `reps` rounds, CUDA events around each
+    round; rays/s of each way."""
+    import torch
+
+    grids = wl.serving_grids()
+    gi = 2
+    spec_g, ne = grids[gi]
+    h = rt.Grid(spec_g, ne)
+    small = [f for g, f in wl.serving_requests(2000, 9, [g for g, _ in grids])
+             if g == gi and rt.Fan(f).n_rays <= 2000][:64]
+    fans = [rt.Fan(f) for f in small]
+    sizes = [f.n_rays for f in fans]
+    n = sum(sizes)
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    out = torch.empty(n * 64, dtype=torch.uint8, device="cuda")
+    main = torch.cuda.current_stream()
+    side = [torch.cuda.Stream() for _ in range(8)]
+    cfg4 = rt.launch_config(kernel=rt.RT_KERNEL_PLAIN, stencil=rt.RT_STENCIL_QUAD, lanes_per_ray=4)
+
+    def per_fan(streams):
+        for k, f in enumerate(fans):
+            st = streams[k % len(streams)]
+            rt.rt_trace_device(h, f, out.data_ptr() + int(off[k]) * 64, sizes[k], cfg=cfg4, stream=st.cuda_stream)
+
+    def fused(_):
+        rt.rt_trace_fans_device(h, fans, out.data_ptr(), n, cfg=rt.launch_config(stencil=rt.RT_STENCIL_QUAD),
+                                stream=main.cuda_stream)
+
+    res = {}
+    for name, fn, streams in (("one_launch_per_fan_1_stream", per_fan, [main]),
+                              ("one_launch_per_fan_8_streams", per_fan, side),
+                              ("one_fused_launch", fused, None)):
+        ts = []
+        for rep in range(reps + 1):
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(main)
+            if streams is side:
+                for st in side:
+                    st.wait_event(a)
+            fn(streams)
+            if streams is side:
+                for st in side:
+                    main.wait_stream(st)
+            b.record(main)
+            torch.cuda.synchronize()
+            if rep > 0:  # the first round warms up
+                ts.append(a.elapsed_time(b))
+        ms = float(np.median(ts))
+        res[name] = {"ms": ms, "rays_per_s": n / (ms / 1e3)}
+    h.close()
+    return {"fans": len(fans), "rays": int(n), "grid": list(spec_g.shape), **res}
+
+
 def profile_fused(rt, wl, fuse, rounds):
     """For ncu: `rounds` rounds on the 91x181x151 serving grid, each one large
     request (which runs unfused and keeps the one slot busy) followed by 64
@@ -894,7 +952,7 @@ def run_serving(rt, wl, seconds, seed=9, slots=8, fuse=16384):
     mean_rays = wl.serving_mean_rays()
     out = {"grids": [list(g.shape) for g in specs], "max_inflight": slots, "fuse_max_rays": fuse,
            "saturated": sat, "saturated_persistent_kernel": sat_p, "saturated_fused": sat_f,
-           "loads": {}, "loads_fused": {}}
+           "small_fans": small_fans_compare(rt, wl), "loads": {}, "loads_fused": {}}
     rng = np.random.default_rng(seed + 1)
     for frac in (0.1, 0.5, 0.9):
         rate = frac * peak / mean_rays  # requests per second
