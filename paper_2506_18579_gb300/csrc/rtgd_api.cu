@@ -244,7 +244,9 @@ double sync_timeout_s() {
 rt_err sync_with_timeout(cudaStream_t st) {
     const auto t0 = std::chrono::steady_clock::now();
     const double limit = sync_timeout_s();
-    int sleep_us = 20;
+    // polls every <= 100 us for the first second (a fan finishing between
+    // two polls costs the caller at most that), then every <= 2 ms
+    int sleep_us = 10;
     for (;;) {
         const cudaError_t e = cudaStreamQuery(st);
         if (e == cudaSuccess) return RT_OK;
@@ -252,7 +254,7 @@ rt_err sync_with_timeout(cudaStream_t st) {
         const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         if (dt > limit) return fail(RT_ETIMEOUT, "stream did not finish within %.0f s", limit);
         std::this_thread::sleep_for(std::chrono::microseconds(sleep_us));
-        sleep_us = std::min(sleep_us * 2, 1000);
+        sleep_us = std::min(sleep_us * 2, dt < 1.0 ? 100 : 2000);
     }
 }
 
