@@ -654,8 +654,8 @@ rt_err rt_tune(const rt_grid *grid, const rt_fan_desc *fan, size_t max_rays, voi
         if ((r = queue_trace(grid, &sub, out, n, &cc, st)) != RT_OK) break;  // warm-up
         // median of three timed launches: a launch whose slowest ray happened to
         // share its SM with little other work must not decide the choice
-        float ts[3];
-        int nt = 0;
+        std::vector<float> ts;
+        ts.reserve(3);
         for (int rep = 0; rep < 3 && r == RT_OK; ++rep) {
             cudaMemsetAsync(flush, rep, flush_bytes, st);
             cudaEventRecord(e0, st);
@@ -663,12 +663,12 @@ rt_err rt_tune(const rt_grid *grid, const rt_fan_desc *fan, size_t max_rays, voi
             cudaEventRecord(e1, st);
             if (r == RT_OK) r = sync_with_timeout(st);
             float ms = 0.0f;
-            if (r == RT_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) ts[nt++] = ms;
+            if (r == RT_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) ts.push_back(ms);
         }
         if (r != RT_OK) break;
-        if (nt == 0) continue;
-        std::sort(ts, ts + nt);
-        const float t_med = ts[nt / 2];
+        if (ts.empty()) continue;
+        std::sort(ts.begin(), ts.end());
+        const float t_med = ts[ts.size() / 2];
         if (t_med < best_t) {
             best_t = t_med;
             best_c = cc;
