@@ -264,6 +264,27 @@ def test_trace_fans_device_matches_oracle_and_each_fan_alone(orc):
         _close64(part[ok], ref[ok], km=MIX_KM, deg=MIX_DEG)
 
 
+def test_trace_fans_device_with_hundreds_of_one_ray_fans():
+    """300 one-ray fans in one call (the binary search over the fans' first
+    rays, the record offsets) give the records of one 300-elevation fan."""
+    torch = pytest.importorskip("torch")
+    w = _c2_small()
+    g = rt.Grid(w.grid, w.ne)
+    els = np.linspace(3.0, 60.0, 300)
+    whole = rt.Fan(w.fan.replace(freq_mhz=[10.0], modes=wl.MODE_X, el_deg=els, az_deg=[30.0]), rt.RT_MIXED)
+    ones = [rt.Fan(w.fan.replace(freq_mhz=[10.0], modes=wl.MODE_X, el_deg=[e], az_deg=[30.0]), rt.RT_MIXED)
+            for e in els]
+    a = torch.zeros(300 * 64, dtype=torch.uint8, device="cuda")
+    b = torch.zeros(300 * 64, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.current_stream()
+    rt.rt_trace_fans_device(g, [whole], a.data_ptr(), 300, stream=s.cuda_stream)
+    rt.rt_trace_fans_device(g, ones, b.data_ptr(), 300, stream=s.cuda_stream)
+    s.synchronize()
+    ra = rt.results_view(a.cpu().numpy(), 300)
+    assert np.all(ra["status"] != rt.RT_RAY_NOT_RUN)
+    assert ra.tobytes() == rt.results_view(b.cpu().numpy(), 300).tobytes()
+
+
 def test_trace_fans_device_refuses_what_it_cannot_fuse():
     torch = pytest.importorskip("torch")
     w = _c2_small()
