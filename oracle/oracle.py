@@ -203,6 +203,35 @@ def trace_fan(grid: Grid, fan, indices=None, n_threads=0):
     return trace_rays(grid, fan_rays(fan, indices), n_threads)
 
 
+def ionogram_points(res, fan, d_rx):
+    """Oblique-ionogram points (Sec. IV-B-4, read as in the C ABI's
+    rt_ionogram): for each frequency and mode of a one-azimuth fan, wherever
+    the ground ranges D of two neighbouring elevations that both landed lie
+    on either side of the receiver distance d_rx, one point with P' and the
+    elevation interpolated linearly in D; branches numbered 0, 1, ... by
+    elevation within each trace.  res holds per-ray records in canonical
+    order.  Returns (freq_mhz, group_path_km, el_deg, mode, branch) tuples."""
+    pts = []
+    n_el = len(fan.el_deg)
+    modes = fan.mode_list
+    r = np.asarray(res).reshape(len(fan.freq_mhz), len(modes), n_el)
+    for fi, f in enumerate(fan.freq_mhz):
+        for mi, m in enumerate(modes):
+            row = r[fi, mi]
+            br = 0
+            for j in range(n_el - 1):
+                a, b = row[j], row[j + 1]
+                if a["status"] != LANDED or b["status"] != LANDED:
+                    continue
+                fa, fb = a["ground_range_km"] - d_rx, b["ground_range_km"] - d_rx
+                if (fa < 0) != (fb < 0):
+                    t = fa / (fa - fb)
+                    pts.append((f, a["group_path_km"] + t * (b["group_path_km"] - a["group_path_km"]),
+                                fan.el_deg[j] + t * (fan.el_deg[j + 1] - fan.el_deg[j]), m, br))
+                    br += 1
+    return pts
+
+
 def trajectory(grid: Grid, ray, cap=200000):
     """(result, traj) for one ray; traj rows are (P', r, theta, phi, kr, kth, kph, H)."""
     ray = np.ascontiguousarray(ray, dtype=RAY_DTYPE).reshape(1)

@@ -469,31 +469,6 @@ def test_plan_execute_and_graph_replay():
         plan.close()
 
 
-def _ionogram_reference(res, fan, d_rx):
-    """Crossings of D = d_rx between neighbouring elevations of landed rays,
-    P' and elevation interpolated linearly in D (the definition rt_ionogram
-    documents), from per-ray records in canonical order (one azimuth)."""
-    pts = []
-    n_el = len(fan.el_deg)
-    modes = fan.mode_list
-    r = res.reshape(len(fan.freq_mhz), len(modes), n_el)
-    for fi, f in enumerate(fan.freq_mhz):
-        for mi, m in enumerate(modes):
-            row = r[fi, mi]
-            br = 0
-            for j in range(n_el - 1):
-                a, b = row[j], row[j + 1]
-                if a["status"] != 1 or b["status"] != 1:
-                    continue
-                fa, fb = a["ground_range_km"] - d_rx, b["ground_range_km"] - d_rx
-                if (fa < 0) != (fb < 0):
-                    t = fa / (fa - fb)
-                    pts.append((f, a["group_path_km"] + t * (b["group_path_km"] - a["group_path_km"]),
-                                fan.el_deg[j] + t * (fan.el_deg[j + 1] - fan.el_deg[j]), m, br))
-                    br += 1
-    return pts
-
-
 @pytest.mark.parametrize("prec", [rt.RT_FP64, rt.RT_MIXED])
 def test_ionogram_matches_oracle(orc, prec):
     w = wl.config2()
@@ -510,7 +485,7 @@ def test_ionogram_matches_oracle(orc, prec):
     c = np.sin(p1) * np.sin(p2) + np.cos(p1) * np.cos(p2) * np.cos(dl)
     d_rx = w.grid.earth_radius_km * np.arctan2(np.hypot(x, y), c)
     spec = w.fan.replace(freq_mhz=freqs, el_deg=els, az_deg=[np.degrees(np.arctan2(y, x))])
-    ref = _ionogram_reference(orc.trace_fan(orc.Grid(w.grid, w.ne), spec), spec, d_rx)
+    ref = orc.ionogram_points(orc.trace_fan(orc.Grid(w.grid, w.ne), spec), spec, d_rx)
     assert len(ref) == n
     km = FP64_KM if prec == rt.RT_FP64 else MIX_KM
     for p, q in zip(pts, ref):

@@ -224,3 +224,28 @@ def test_rkf45_converges_with_rtol(orc):
         errs.append(np.quantile(np.abs(a["group_path_km"] - ref["group_path_km"])[ok], 0.9))
     assert errs[1] < errs[0] / 20.0, errs
     assert errs[1] < 2e-3, errs
+
+
+def test_ionogram_points_hand_computed(orc):
+    """The ionogram reduction on hand-made records: crossings of the receiver
+    distance between neighbouring landed elevations, P' and elevation linear
+    in D, branches counted per (frequency, mode), no crossing across a ray
+    that did not land."""
+    fan = wl.FanSpec(tx_lat_deg=0.0, tx_lon_deg=0.0, tx_alt_km=0.0, freq_mhz=[5.0, 7.0],
+                     el_deg=[10.0, 20.0, 30.0, 40.0], az_deg=[45.0], modes=wl.MODE_O | wl.MODE_X)
+    res = np.zeros(fan.n_rays, dtype=orc.RESULT_DTYPE).reshape(2, 2, 4)
+    res["status"] = orc.LANDED
+    res["ground_range_km"] = 900.0  # frequency 7 MHz: never reaches 1,500 km
+    # 5 MHz, O: D rises through 1,500 km and falls back through it
+    res[0, 0]["ground_range_km"] = [1000.0, 1400.0, 1600.0, 1200.0]
+    res[0, 0]["group_path_km"] = [1100.0, 1500.0, 1700.0, 1300.0]
+    # 5 MHz, X: the second elevation escapes, so only the last pair counts
+    res[0, 1]["ground_range_km"] = [1000.0, 1600.0, 1700.0, 1300.0]
+    res[0, 1]["group_path_km"] = [1000.0, 1700.0, 1800.0, 1400.0]
+    res[0, 1, 1]["status"] = orc.ESCAPED
+    pts = orc.ionogram_points(res.reshape(-1), fan, 1500.0)
+    want = [(5.0, 1600.0, 25.0, 1, 0), (5.0, 1600.0, 32.5, 1, 1), (5.0, 1600.0, 35.0, -1, 0)]
+    assert len(pts) == len(want)
+    for p, q in zip(pts, want):
+        assert p[0] == q[0] and p[3] == q[3] and p[4] == q[4]
+        assert abs(p[1] - q[1]) < 1e-9 and abs(p[2] - q[2]) < 1e-12
