@@ -50,9 +50,9 @@ GATHER_BYTES = {"mixed": 65 * 4, "fp64": 64 * 8}
 # was captured from: a changed kernel reports traffic null.
 KERNEL_SOURCES = ("paper_2506_18579_gb300/csrc/rtgd_kernels.cu", "paper_2506_18579_gb300/csrc/rtgd_device.cuh")
 TRAFFIC = {
-    # profiles/trace_mixed_c2_fan_dram_by_config.md: the plain kernel on the C2
-    # fan, 96-thread blocks (the block size moves DRAM bytes by ~1 %); key =
-    # (workload, kernel, stencil, lanes per ray)
+    # profiles/trace_mixed_c2_fan_dram_by_config.md: the plain (1) and persistent
+    # (2) kernels on the C2 fan, 96-thread blocks (the block size moves DRAM
+    # bytes by ~1 %); key = (workload, kernel, stencil, lanes per ray)
     ("c2", 1, 1, 1): {"bytes_per_launch": 2132992, "source_sha256": "91c55e6b7720bda6"},
     ("c2", 1, 1, 2): {"bytes_per_launch": 2130944, "source_sha256": "91c55e6b7720bda6"},
     ("c2", 1, 1, 4): {"bytes_per_launch": 2473216, "source_sha256": "91c55e6b7720bda6"},
@@ -62,6 +62,15 @@ TRAFFIC = {
     ("c2", 1, 3, 1): {"bytes_per_launch": 26717184, "source_sha256": "91c55e6b7720bda6"},
     ("c2", 1, 3, 2): {"bytes_per_launch": 27068160, "source_sha256": "91c55e6b7720bda6"},
     ("c2", 1, 3, 4): {"bytes_per_launch": 27088384, "source_sha256": "91c55e6b7720bda6"},
+    ("c2", 2, 1, 1): {"bytes_per_launch": 2358528, "source_sha256": "91c55e6b7720bda6"},
+    ("c2", 2, 1, 2): {"bytes_per_launch": 2136064, "source_sha256": "91c55e6b7720bda6"},
+    ("c2", 2, 1, 4): {"bytes_per_launch": 2135808, "source_sha256": "91c55e6b7720bda6"},
+    ("c2", 2, 2, 1): {"bytes_per_launch": 6005248, "source_sha256": "91c55e6b7720bda6"},
+    ("c2", 2, 2, 2): {"bytes_per_launch": 5745408, "source_sha256": "91c55e6b7720bda6"},
+    ("c2", 2, 2, 4): {"bytes_per_launch": 5397504, "source_sha256": "91c55e6b7720bda6"},
+    ("c2", 2, 3, 1): {"bytes_per_launch": 26865152, "source_sha256": "91c55e6b7720bda6"},
+    ("c2", 2, 3, 2): {"bytes_per_launch": 26757888, "source_sha256": "91c55e6b7720bda6"},
+    ("c2", 2, 3, 4): {"bytes_per_launch": 27103232, "source_sha256": "91c55e6b7720bda6"},
     # profiles/trace_mixed_c4_batch.md: 20.28 MB read + 1.04 MB written (128-thread blocks)
     ("c4", 1, 3, 1): {"bytes_per_launch": 21322240, "source_sha256": "91c55e6b7720bda6"},
 }
