@@ -71,8 +71,15 @@ TRAFFIC = {
     ("c2", 2, 3, 1): {"bytes_per_launch": 26865152, "source_sha256": "91c55e6b7720bda6"},
     ("c2", 2, 3, 2): {"bytes_per_launch": 26757888, "source_sha256": "91c55e6b7720bda6"},
     ("c2", 2, 3, 4): {"bytes_per_launch": 27103232, "source_sha256": "91c55e6b7720bda6"},
-    # profiles/trace_mixed_c4_batch.md: 20.28 MB read + 1.04 MB written (128-thread blocks)
+    # profiles/trace_mixed_c4_batch.md: 20.28 MB read + 1.04 MB written (128-thread blocks);
+    # the other stencils and the persistent kernel, one lane per ray (the only
+    # lane count the autotuner tries on a fan this large)
     ("c4", 1, 3, 1): {"bytes_per_launch": 21322240, "source_sha256": "91c55e6b7720bda6"},
+    ("c4", 1, 1, 1): {"bytes_per_launch": 1655296, "source_sha256": "91c55e6b7720bda6"},
+    ("c4", 1, 2, 1): {"bytes_per_launch": 4627200, "source_sha256": "91c55e6b7720bda6"},
+    ("c4", 2, 1, 1): {"bytes_per_launch": 1880064, "source_sha256": "91c55e6b7720bda6"},
+    ("c4", 2, 2, 1): {"bytes_per_launch": 5474560, "source_sha256": "91c55e6b7720bda6"},
+    ("c4", 2, 3, 1): {"bytes_per_launch": 22156288, "source_sha256": "91c55e6b7720bda6"},
 }
 SMS = 152
 FP32_LANES_PER_SM = 128
