@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define RTGD_API_VERSION 1
+#define RTGD_API_VERSION 2
 
 typedef enum rt_err {
     RT_OK = 0,
@@ -212,15 +212,23 @@ typedef struct rt_launch_config {
  * arrays to the device, runs the kernels on `stream`, copies the results back
  * and synchronises the stream.  cfg may be NULL (defaults).  Device scratch
  * (fan tables, result staging, the persistent kernel's ray counter) is
- * allocated stream-ordered and released before return.
+ * allocated stream-ordered and released stream-ordered.
+ * The wait for the trace is bounded: RTGD_SYNC_TIMEOUT_S seconds (environment
+ * variable, read at every call; default 900).  When it expires the call
+ * returns RT_ETIMEOUT with the trace still queued or running on `stream`
+ * (and its scratch released after it, stream-ordered); out_host is left
+ * untouched and is not written later, because the copy of the records is
+ * queued only after the trace has finished (that copy is then waited for
+ * without a deadline).  On every return the caller owns out_host again.
  * Errors: RT_EINVAL (null pointers, empty or invalid fan, out_len too small,
- * bad cfg), RT_ENOMEM, RT_ECUDA, RT_EUNSUPPORTED. */
+ * bad cfg), RT_ENOMEM, RT_ECUDA, RT_ETIMEOUT, RT_EUNSUPPORTED. */
 rt_err rt_trace(const rt_grid *grid, const rt_fan_desc *fan, rt_ray_result *out_host,
                 size_t out_len, const rt_launch_config *cfg, void *stream);
 
 /* Same as rt_trace but asynchronous: out_dev is device memory (e.g. a PyTorch
  * CUDA tensor) of at least rt_fan_size(fan) records; the call returns once the
- * work is queued on `stream`.  The fan arrays are read before return. */
+ * work is queued on `stream`.  The fan arrays are copied into library memory
+ * before return (pinned or pageable), so the caller may reuse them at once. */
 rt_err rt_trace_device(const rt_grid *grid, const rt_fan_desc *fan, rt_ray_result *out_dev,
                        size_t out_len, const rt_launch_config *cfg, void *stream);
 
@@ -252,14 +260,18 @@ rt_err rt_trace_fans_device(const rt_grid *grid, const rt_fan_desc *const *fans,
  * cudaMalloc/cudaFree (or other allocating) call: its scratch -- the ray
  * counter and the fan tables -- is a fixed array inside the library (16 bytes
  * + 4096 doubles, about 32 KiB, held on every GPU that loads the library until
- * the process exits).  The paper has no counterpart; it is an interface
- * variant of rt_trace_device.  Limits and rules:
+ * the process exits), filled from a fixed host staging array of the same size.
+ * The paper has no counterpart; it is an interface variant of
+ * rt_trace_device.  Limits and rules:
  *   - n_freq + n_el + n_az must not exceed 4096 (RT_EINVAL otherwise).
  *   - All calls share the scratch: work queued by one call must be finished
  *     on the GPU before another call's work starts (calls that overlap on the
- *     GPU, e.g. on two streams, race and give wrong results).
- *   - The first call on a device looks up the scratch's device address; make
- *     that first call before any stream capture on the device.
+ *     GPU, e.g. on two streams, race and give wrong results).  Every call
+ *     resets the ray counter and rewrites the tables it uses.
+ *   - The first call on a device looks up the scratch's device address (a
+ *     runtime query, once per device); make that first call before any stream
+ *     capture begins on the device.
+ *   - The fan arrays are copied before return, as in rt_trace_device.
  * Results, errors and stream semantics are those of rt_trace_device. */
 rt_err rt_trace_device_noalloc(const rt_grid *grid, const rt_fan_desc *fan, rt_ray_result *out_dev,
                                size_t out_len, const rt_launch_config *cfg, void *stream);
@@ -334,9 +346,15 @@ rt_err rt_ionogram(const rt_grid *grid, const rt_ionogram_desc *desc, rt_ionogra
 /* A request server for fans of uneven size against resident grids
  * (continuous batching).  Submitted requests wait in a FIFO; a dispatcher
  * thread admits them as soon as one of max_inflight stream slots is free and
- * cudaMemGetInfo reports at least mem_reserve_bytes of device memory free
- * after the request's own needs (results + fan tables), so requests that
- * arrive while others run are traced concurrently with them on the GPU.  A
+ * the free device memory (cudaMemGetInfo, or the caller's free_bytes
+ * function) stays at least mem_reserve_bytes above the request's own needs
+ * (twice its records plus 4 KiB of fan tables per request; the grids are
+ * resident and already in use), so requests that arrive while others run are
+ * traced concurrently with them on the GPU.  A request that does not fit
+ * waits for running requests to finish; when none runs, it is admitted if its
+ * own needs fit in the free memory (the reserve is then waived, so a lone
+ * request always makes progress) and otherwise finishes at once with status
+ * RT_ENOMEM, without touching the GPU, while the requests behind it proceed.  A
  * completion thread copies each result to the caller's host buffer (through
  * pinned staging) and wakes rt_server_wait.  Every request uses the launch
  * configuration given at creation, so its records equal those of rt_trace
@@ -365,6 +383,12 @@ typedef struct rt_server_config {
                                     as without fusion. */
     size_t mem_reserve_bytes;    /* device memory kept free by admission */
     rt_launch_config launch;     /* kernel choice for every request (zero = library defaults) */
+    /* Optional: the device memory admission may use, asked before every
+     * admission decision (from the dispatcher thread) instead of
+     * cudaMemGetInfo's free bytes -- e.g. a budget shared with another
+     * runtime on the same GPU.  NULL: cudaMemGetInfo. */
+    size_t (*free_bytes)(void *user);
+    void *free_bytes_user;
 } rt_server_config;
 
 typedef struct rt_request_stats {

@@ -296,6 +296,31 @@ FanDev fill_fandev(const rt_grid *grid, const rt_fan_desc *fan, size_t n, int or
     return f;
 }
 
+// The device scratch image of a fan: a zeroed 16-byte ray counter followed
+// by the frequency, elevation and azimuth tables, written into
+// library-owned pageable host memory (fan_image_bytes(fan) bytes at img).
+// Uploading this copy (one cudaMemcpyAsync) instead of the caller's arrays
+// means the caller may change or free its arrays as soon as the call
+// returns, whether they are pinned or not: a copy from pageable memory has
+// read its source when cudaMemcpyAsync returns.
+size_t fan_image_bytes(const rt_fan_desc *fan) {
+    return 16 + ((size_t)fan->n_freq + fan->n_el + fan->n_az) * sizeof(double);
+}
+
+void fan_image_into(const rt_fan_desc *fan, char *img) {
+    std::memset(img, 0, 16);
+    double *tab = (double *)(img + 16);
+    std::memcpy(tab, fan->freq_mhz, fan->n_freq * sizeof(double));
+    std::memcpy(tab + fan->n_freq, fan->el_deg, fan->n_el * sizeof(double));
+    std::memcpy(tab + fan->n_freq + fan->n_el, fan->az_deg, fan->n_az * sizeof(double));
+}
+
+std::vector<char> fan_image(const rt_fan_desc *fan) {
+    std::vector<char> img(fan_image_bytes(fan));
+    fan_image_into(fan, img.data());
+    return img;
+}
+
 // Queues one trace: scratch allocation, fan upload, kernel, scratch release.
 rt_err queue_trace(const rt_grid *grid, const rt_fan_desc *fan, rt_ray_result *out_dev, size_t out_len,
                    const rt_launch_config *cfg, cudaStream_t st) {
@@ -313,20 +338,12 @@ rt_err queue_trace(const rt_grid *grid, const rt_fan_desc *fan, rt_ray_result *o
     int order = 0;
     if ((r = make_plan(grid, fan, n, cfg, &lp, &order)) != RT_OK) return r;
 
-    const size_t n_tab = (size_t)fan->n_freq + fan->n_el + fan->n_az;
-    const size_t bytes = 16 + n_tab * sizeof(double);
+    const std::vector<char> img = fan_image(fan);
     char *ws = nullptr;
-    CUDA_TRY(cudaMallocAsync((void **)&ws, bytes, st));
+    CUDA_TRY(cudaMallocAsync((void **)&ws, img.size(), st));
     unsigned long long *counter = (unsigned long long *)ws;
     double *tab = (double *)(ws + 16);
-    cudaError_t e = cudaMemsetAsync(counter, 0, 16, st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(tab, fan->freq_mhz, fan->n_freq * sizeof(double), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(tab + fan->n_freq, fan->el_deg, fan->n_el * sizeof(double), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(tab + fan->n_freq + fan->n_el, fan->az_deg, fan->n_az * sizeof(double),
-                            cudaMemcpyHostToDevice, st);
+    cudaError_t e = cudaMemcpyAsync(ws, img.data(), img.size(), cudaMemcpyHostToDevice, st);
     const FanDev f = fill_fandev(grid, fan, n, order, tab);
     if (e == cudaSuccess) e = launch_trace(grid->g, f, out_dev, counter, lp, st);
     const cudaError_t e2 = cudaFreeAsync(ws, st);
@@ -560,11 +577,16 @@ rt_err rt_trace(const rt_grid *grid, const rt_fan_desc *fan, rt_ray_result *out_
     rt_ray_result *dev = nullptr;
     CUDA_TRY(cudaMallocAsync((void **)&dev, n * sizeof(rt_ray_result), st));
     r = queue_trace(grid, fan, dev, n, cfg, st);
+    // The bounded wait covers the trace.  The copy into out_host is queued
+    // only once the trace has finished, and waited for without a deadline (a
+    // copy of finished records), so that a call returning RT_ETIMEOUT has
+    // queued no write into out_host: the caller's buffer is free on return
+    // whatever the status.
     if (r == RT_OK) r = sync_with_timeout(st);
     if (r == RT_OK) {
-        const cudaError_t e = cudaMemcpyAsync(out_host, dev, n * sizeof(rt_ray_result), cudaMemcpyDeviceToHost, st);
+        cudaError_t e = cudaMemcpyAsync(out_host, dev, n * sizeof(rt_ray_result), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) r = cuda_fail(e, "result copy");
-        else r = sync_with_timeout(st);
     }
     const cudaError_t e2 = cudaFreeAsync(dev, st);
     if (r == RT_OK && e2 != cudaSuccess) r = cuda_fail(e2, "cudaFreeAsync");
@@ -851,6 +873,16 @@ rt_err rt_ionogram(const rt_grid *grid, const rt_ionogram_desc *d, rt_ionogram_p
     return RT_OK;
 }
 
+}  // extern "C"
+
+namespace {
+// Host staging of rt_trace_device_noalloc's fan image (fixed size, no allocation).
+std::mutex g_noalloc_img_mu;
+char g_noalloc_img[16 + kNoallocMaxTable * sizeof(double)];
+}  // namespace
+
+extern "C" {
+
 rt_err rt_trace_device_noalloc(const rt_grid *grid, const rt_fan_desc *fan, rt_ray_result *out_dev,
                                size_t out_len, const rt_launch_config *cfg, void *stream) {
     rt_err r = validate_fan(fan);
@@ -877,11 +909,15 @@ rt_err rt_trace_device_noalloc(const rt_grid *grid, const rt_fan_desc *fan, rt_r
     cudaStream_t st = (cudaStream_t)stream;
     unsigned long long *counter = (unsigned long long *)scratch;
     double *tab = (double *)((char *)scratch + 16);
-    CUDA_TRY(cudaMemsetAsync(counter, 0, 16, st));  // the array keeps the last call's contents
-    CUDA_TRY(cudaMemcpyAsync(tab, fan->freq_mhz, fan->n_freq * sizeof(double), cudaMemcpyHostToDevice, st));
-    CUDA_TRY(cudaMemcpyAsync(tab + fan->n_freq, fan->el_deg, fan->n_el * sizeof(double), cudaMemcpyHostToDevice, st));
-    CUDA_TRY(cudaMemcpyAsync(tab + fan->n_freq + fan->n_el, fan->az_deg, fan->n_az * sizeof(double),
-                             cudaMemcpyHostToDevice, st));
+    // one copy of the fan image: its leading 16 zero bytes reset the ray
+    // counter (the array keeps the last call's contents), the tables follow.
+    // The image is staged in a fixed host array (no allocation) that the
+    // lock keeps to one call at a time until cudaMemcpyAsync has read it.
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_img_mu);
+        fan_image_into(fan, g_noalloc_img);
+        CUDA_TRY(cudaMemcpyAsync(scratch, g_noalloc_img, fan_image_bytes(fan), cudaMemcpyHostToDevice, st));
+    }
     const FanDev f = fill_fandev(grid, fan, n, order, tab);
     CUDA_TRY(launch_trace(grid->g, f, out_dev, counter, lp, st));
     return RT_OK;

@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
+#include <cstdio>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -104,6 +105,21 @@ void finish_locked(rt_server *s, Slot &slot, rt_err status) {
     s->cv_dispatch.notify_all();
 }
 
+// Device memory a batch of n rays from k requests takes while it runs: its
+// records (n x 64 bytes, stream-ordered) and the fan tables and launch
+// metadata, counted generously (twice the records plus 4 KiB per request).
+// The grids it reads are resident and already counted as used memory.
+size_t admission_bytes(size_t n, size_t k) { return n * sizeof(rt_ray_result) * 2 + 4096 * k; }
+
+// Free device memory as admission sees it: the caller's budget function if
+// one is configured, otherwise cudaMemGetInfo.
+size_t free_device_bytes(rt_server *s) {
+    if (s->cfg.free_bytes) return s->cfg.free_bytes(s->cfg.free_bytes_user);
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return 0;
+    return free_b;
+}
+
 // Small requests of a fusing server (always traced by the fused kernel).
 bool is_small(const rt_server *s, const Request &r) {
     return s->cfg.fuse_max_rays > 0 && r.fan.precision == RT_MIXED && r.n <= s->small_limit;
@@ -174,15 +190,34 @@ void dispatch_loop(rt_server *s) {
                 n_batch += q.n;
             }
         }
-        // admission by device memory: the batch's records + tables must fit above the reserve
-        size_t free_b = 0, total_b = 0;
-        const size_t need = n_batch * sizeof(rt_ray_result) * 2 + 4096 * pick.size();
+        // admission by device memory: the batch's device scratch must fit
+        // above the reserve while other requests run; an idle server admits
+        // any batch that fits at all, and refuses (RT_ENOMEM) one that does not
+        const size_t need = admission_bytes(n_batch, pick.size());
         lk.unlock();
-        cudaMemGetInfo(&free_b, &total_b);
+        const size_t free_b = free_device_bytes(s);
         lk.lock();
         if (free_b < need + s->cfg.mem_reserve_bytes && s->inflight > 0) {
             // wait for a running request to release memory
             s->cv_dispatch.wait_for(lk, std::chrono::milliseconds(2));
+            continue;
+        }
+        if (free_b < need && pick.size() > 1 && admission_bytes(head.n, 1) <= free_b) {
+            pick.resize(1);  // nothing runs: the head request goes alone
+        } else if (free_b < need) {
+            // nothing runs and the head request alone does not fit: refuse it
+            // (its fused companions stay queued) without touching the GPU
+            auto rp = s->queue.front();
+            s->queue.pop_front();
+            rp->t_admit = Clock::now();
+            rp->batch_size = 1;
+            rp->status = RT_ENOMEM;
+            char msg[160];
+            std::snprintf(msg, sizeof(msg), "server: request needs %zu bytes of device memory, %zu free", need, free_b);
+            rp->msg = msg;
+            rp->t_done = rp->t_admit;
+            rp->done = true;
+            s->cv_done.notify_all();
             continue;
         }
         // the queue only grows at its back while the lock was released, so

@@ -88,9 +88,13 @@ class rt_ionogram_desc(ctypes.Structure):
                 ("h_max_km", ctypes.c_double)]
 
 
+FREE_BYTES_FN = ctypes.CFUNCTYPE(ctypes.c_size_t, ctypes.c_void_p)
+
+
 class rt_server_config(ctypes.Structure):
     _fields_ = [("max_inflight", ctypes.c_int32), ("fuse_max_rays", ctypes.c_int32),
-                ("mem_reserve_bytes", ctypes.c_size_t), ("launch", rt_launch_config)]
+                ("mem_reserve_bytes", ctypes.c_size_t), ("launch", rt_launch_config),
+                ("free_bytes", FREE_BYTES_FN), ("free_bytes_user", ctypes.c_void_p)]
 
 
 class rt_request_stats(ctypes.Structure):
@@ -361,9 +365,14 @@ def rt_trace_device_noalloc(grid, fan, out_ptr, out_len, cfg=None, stream=None):
 class Server:
     """rt_server: continuous-batching request server on the current device."""
 
-    def __init__(self, max_inflight=8, mem_reserve_bytes=0, cfg=None, fuse_max_rays=0):
+    def __init__(self, max_inflight=8, mem_reserve_bytes=0, cfg=None, fuse_max_rays=0, free_bytes=None):
+        """free_bytes: optional Python callable returning the device memory
+        (bytes) admission may use, asked from the server's dispatcher thread
+        instead of cudaMemGetInfo."""
+        self._free_fn = FREE_BYTES_FN(lambda _user: int(free_bytes())) if free_bytes is not None \
+            else FREE_BYTES_FN()
         c = rt_server_config(max_inflight, fuse_max_rays, mem_reserve_bytes,
-                             cfg if cfg is not None else rt_launch_config())
+                             cfg if cfg is not None else rt_launch_config(), self._free_fn, None)
         h = ctypes.c_void_p()
         _check(load().rt_server_create(ctypes.byref(c), ctypes.byref(h)))
         self.handle = h

@@ -99,7 +99,7 @@ def test_every_struct_size_and_field_offset_matches(tmp_path):
 
 def test_version_and_fan_size(lib):
     from paper_2506_18579_gb300 import workloads as wl
-    assert rt.rt_version() == 1
+    assert rt.rt_version() == 2
     w = wl.config2(elev_step=1.0, az_step=30.0)
     fan = rt.Fan(w.fan)
     assert fan.n_rays == w.fan.n_rays == 3 * 2 * 58 * 12
