@@ -873,6 +873,8 @@ __device__ __forceinline__ float face_distance_f(const GridDev &g, const Base32 
 struct Lane {
     double y[3];              // r (km), theta, phi (rad): the FP64 position
     double P;                 // group path (km)
+    float inc_hi[4], inc_lo[4];  // increments of (r, theta, phi, P') not yet added to y and P,
+                                 // as compensated float pairs (see lane_fold)
     float k_hi[3], k_lo[3];   // wave vector as a compensated float pair
     float r_prev;             // radius at the start of the last accepted step
     double la, lfa, lb, lfb;  // crossing bracket (step size, signed r - target)
@@ -898,7 +900,7 @@ __device__ __forceinline__ RayPhys<float> lane_phys(const GridDev &g, const Lane
     p.m[0] = g.mf[0];
     p.m[1] = g.mf[1];
     p.m[2] = g.mf[2];
-    p.iso = g.b0 == 0.0;
+    p.iso = g.iso != 0;
     p.mode = L.mode;
     return p;
 }
@@ -949,6 +951,8 @@ __device__ void lane_begin_ray(Lane &L, const GridDev &g, const FanDev &f, long 
         L.k_lo[i] = 0.0f;
     }
     L.P = 0.0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) L.inc_hi[i] = L.inc_lo[i] = 0.0f;
     L.h = f.h0_f;
     L.apo = (float)(f.tx_r - g.R_E);
     L.n_steps = L.n_att = L.n_ev = 0;
@@ -959,7 +963,27 @@ __device__ void lane_begin_ray(Lane &L, const GridDev &g, const FanDev &f, long 
     base_from_state(g, y, L.b);
 }
 
-// Double copy of the full state (position, wave vector hi + lo).
+// Adds the pending increments to the FP64 position and group path.  An
+// accepted step adds its float increments of r, theta, phi and P' to
+// compensated float pairs (TwoSum: hi + lo carries their sum to ~2^-48
+// relative), and the pairs reach the double state only here: at the base
+// resync every kResyncSteps steps, before a landing / exit solve and when the
+// ray ends.  So the FP64 pipe (1/64 of the FP32 rate on GB300) sees four
+// conversions and additions per component every kResyncSteps steps instead of
+// two per component every step; the position agrees with step-by-step double
+// accumulation to ~1e-12 km.
+__device__ __forceinline__ void lane_fold(Lane &L) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        L.y[i] += (double)L.inc_hi[i] + (double)L.inc_lo[i];
+        L.inc_hi[i] = L.inc_lo[i] = 0.0f;
+    }
+    L.P += (double)L.inc_hi[3] + (double)L.inc_lo[3];
+    L.inc_hi[3] = L.inc_lo[3] = 0.0f;
+}
+
+// Double copy of the full state (position, wave vector hi + lo); the pending
+// increments must have been folded in.
 __device__ __forceinline__ void lane_state(const Lane &L, double y[6]) {
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -972,6 +996,7 @@ __device__ __forceinline__ void lane_finish(Lane &L, const GridDev &g, const Fan
                                             bool writer = true) {
     L.active = false;
     if (!writer) return;
+    lane_fold(L);
     const double az = f.az[L.out_id % f.n_az] * kDeg2Rad;
     finish_result(f.tx_th, f.tx_ph, az, L.y[1], L.y[2], L.P, (double)L.apo, L.status, L.n_steps, L.n_att, L.n_ev,
                   g.R_E, out + L.out_id);
@@ -988,7 +1013,10 @@ __device__ __forceinline__ void lane_limit_step(Lane &L, const GridDev &g, const
             L.at_face = true;
         }
     }
-    if (f.has_max_path && L.P + (double)L.hs > f.max_path) L.hs = (float)(f.max_path - L.P);
+    if (f.has_max_path) {
+        const double P = L.P + ((double)L.inc_hi[3] + (double)L.inc_lo[3]);
+        if (P + (double)L.hs > f.max_path) L.hs = (float)(f.max_path - P);
+    }
 }
 
 // Sets up the next step attempt from the current state; returns false when
@@ -1201,6 +1229,7 @@ __device__ bool lane_end_attempt(Lane &L, const GridDev &g, const FanDev &f) {
     const bool lands = alt_new < 0.0f;
     if (lands || alt_new > g.top_f) {
         // ground return or exit through the grid top inside this step
+        lane_fold(L);
         const double r_new = L.y[0] + (double)dy4[0];
         L.landing = true;
         L.exiting = !lands;
@@ -1218,10 +1247,10 @@ __device__ bool lane_end_attempt(Lane &L, const GridDev &g, const FanDev &f) {
     L.r_prev = L.b.r;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        L.y[i] += (double)dy4[i];
+        two_sum_add(L.inc_hi[i], L.inc_lo[i], dy4[i]);
         two_sum_add(L.k_hi[i], L.k_lo[i], dy4[3 + i]);
     }
-    L.P += (double)L.hs;
+    two_sum_add(L.inc_hi[3], L.inc_lo[3], L.hs);
     ++L.n_steps;
     L.apo = fmaxf(L.apo, alt_new);
     L.have_prev = true;
@@ -1230,6 +1259,7 @@ __device__ bool lane_end_attempt(Lane &L, const GridDev &g, const FanDev &f) {
     L.k1_valid = false;
     if (++L.since_sync >= kResyncSteps) {
         L.since_sync = 0;
+        lane_fold(L);
         double y[6];
         lane_state(L, y);
         base_from_state(g, y, L.b);
@@ -1244,9 +1274,12 @@ __device__ bool lane_end_attempt(Lane &L, const GridDev &g, const FanDev &f) {
             return true;
         }
     }
-    if (f.has_max_path && L.P >= f.max_path - 1e-6) {
-        L.status = RT_RAY_MAX_PATH;
-        return true;
+    if (f.has_max_path) {
+        lane_fold(L);
+        if (L.P >= f.max_path - 1e-6) {
+            L.status = RT_RAY_MAX_PATH;
+            return true;
+        }
     }
     L.h = h_next;
     return !lane_next_attempt(L, f);
