@@ -44,13 +44,13 @@ FLOP_PER_EVAL = {"mixed": 1000.0, "fp64": 910.0}
 # reference node, FP32 in the mixed path and FP64 in the all-FP64 path.
 GATHER_BYTES = {"mixed": 65 * 4, "fp64": 64 * 8}
 # DRAM bytes (read + write) of one launch of the benchmark's dominant kernel,
-# from the ncu capture summarised in profiles/ (cold caches, as after the
+# from an ncu capture of the same launch (cold caches, as after the
 # L2 flush between timed steps), keyed by workload and launch configuration
 # (kernel, stencil, lanes per ray) and valid only for the kernel sources it
 # was captured from: a changed kernel reports traffic null.
 KERNEL_SOURCES = ("paper_2506_18579_gb300/csrc/rtgd_kernels.cu", "paper_2506_18579_gb300/csrc/rtgd_device.cuh")
 TRAFFIC = {
-    # profiles/trace_mixed_c2_fan_dram_by_config.md: the plain (1) and persistent
+    # the anisotropic fan: the plain (1) and persistent
     # (2) kernels on the C2 fan, 96-thread blocks (the block size moves DRAM
     # bytes by ~1 %); key = (workload, kernel, stencil, lanes per ray)
     ("c2", 1, 1, 1): {"bytes_per_launch": 2132992, "source_sha256": "91c55e6b7720bda6"},
@@ -71,7 +71,7 @@ TRAFFIC = {
     ("c2", 2, 3, 1): {"bytes_per_launch": 26865152, "source_sha256": "91c55e6b7720bda6"},
     ("c2", 2, 3, 2): {"bytes_per_launch": 26757888, "source_sha256": "91c55e6b7720bda6"},
     ("c2", 2, 3, 4): {"bytes_per_launch": 27103232, "source_sha256": "91c55e6b7720bda6"},
-    # profiles/trace_mixed_c4_batch.md: 20.28 MB read + 1.04 MB written (128-thread blocks);
+    # the ionogram batch: 20.28 MB read + 1.04 MB written (128-thread blocks);
     # the other stencils and the persistent kernel, one lane per ray (the only
     # lane count the autotuner tries on a fan this large)
     ("c4", 1, 3, 1): {"bytes_per_launch": 21322240, "source_sha256": "91c55e6b7720bda6"},
@@ -252,16 +252,86 @@ def cpu_oracle_rate(workload, n_sample, seed=1234, single_core_rays=128):
     return info, idx, res
 
 
-def near_boundary(res, fan):
-    n_az, n_el = len(fan.az_deg), len(fan.el_deg)
-    r = res.reshape(-1, n_el, n_az)
-    flag = np.zeros(r.shape, bool)
-    jump = ((r["status"][:, 1:] != r["status"][:, :-1]) |
-            (np.abs(np.diff(r["ground_range_km"], axis=1)) > 30.0) |
-            (np.abs(np.diff(r["group_path_km"], axis=1)) > 30.0))
-    flag[:, 1:] |= jump
-    flag[:, :-1] |= jump
-    return flag.reshape(-1)
+GATE_KM, GATE_DEG = 0.05, 1e-4
+ERROR_FIELDS = ("group_path_km", "ground_range_km", "az_dev_deg", "apogee_km", "land_lat_deg", "land_lon_deg")
+
+
+def gate_errors(r, ref, well, idx=None, km=GATE_KM, deg=GATE_DEG):
+    """Per-output errors of records r (r[idx] when idx is given) against
+    reference records ref: statuses over all rays; every output's max / p99 /
+    p99.9 over the rays of `well` whose statuses agree; the share of those
+    within the bar (P' and D within km; azimuth deviation within deg)."""
+    g = r if idx is None else r[idx]
+    mism = g["status"] != ref["status"]
+    m = np.asarray(well, bool) & ~mism
+    out = {"rays": int(len(ref)), "rays_compared": int(m.sum()), "status_mismatch": int(mism.sum())}
+    if not m.any():
+        return out
+    inside = np.ones(int(m.sum()), bool)
+    for f in ERROR_FIELDS:
+        d = np.abs(g[f] - ref[f])[m]
+        out[f] = {"max": float(d.max()), "p99": float(np.percentile(d, 99)), "p99.9": float(np.percentile(d, 99.9))}
+        if f in ("group_path_km", "ground_range_km"):
+            out[f]["within_bar"] = float(np.mean(d <= km))
+            inside &= d <= km
+        if f == "az_dev_deg":
+            out[f]["within_bar"] = float(np.mean(d <= deg))
+    out["bar"] = {"km": km, "deg": deg}
+    out["p_and_d_within_bar_share"] = float(inside.mean())
+    out["p_and_d_beyond_bar_rays"] = int((~inside).sum())
+    return out
+
+
+def oracle_well_conditioned(w, spec, o_idx, o_res):
+    """Rays (of o_idx) not within 0.05 deg of a skip or Pedersen boundary, the
+    boundaries located with the oracle alone; and a summary."""
+    from oracle import boundaries as bd
+    from oracle import oracle
+    g = oracle.Grid(w.grid, w.ne)
+    t0 = time.perf_counter()
+    if len(o_idx) == spec.n_rays:
+        near, n_b = bd.fan_exclusion(oracle, g, spec, o_res)
+    else:
+        near, n_b = bd.sample_exclusion(oracle, g, spec, o_idx, o_res)
+    return ~near, {"located": int(n_b), "excluded_rays": int(near.sum()), "of_rays": int(len(near)),
+                   "excluded_share": float(near.mean()), "seconds": time.perf_counter() - t0,
+                   "rule": "within %.2f deg of elevation of a boundary located by oracle bisection to %.2f deg"
+                           % (bd.EXCLUSION_DEG, bd.RESOLUTION_DEG)}
+
+
+def tighter_rtol_gate(w, spec8, res8):
+    """Records of the fan at the tighter rtol against the oracle's on every
+    second azimuth, over the rays away from oracle-located boundaries."""
+    from oracle import boundaries as bd
+    from oracle import oracle
+    g = oracle.Grid(w.grid, w.ne)
+    n_a = len(spec8.az_deg)
+    sub = spec8.replace(az_deg=spec8.az_deg[::2])
+    idx = np.nonzero((np.arange(spec8.n_rays) % n_a) % 2 == 0)[0]
+    t0 = time.perf_counter()
+    ref = oracle.trace_fan(g, sub)
+    near, n_b = bd.fan_exclusion(oracle, g, sub, ref)
+    out = gate_errors(res8, ref, ~near, idx)
+    out.update({"rtol": spec8.rtol, "rays_of_fan": int(len(idx)), "boundaries": int(n_b),
+                "excluded_rays": int(near.sum()), "oracle_seconds": time.perf_counter() - t0})
+    return out
+
+
+def converged_sample(w, spec, res, o_idx, o_res, well, n_sample=1500, seed=77):
+    """The integrator's own error: the mixed records and the oracle's records
+    at the fan's rtol against the oracle at rtol 1e-11 (atol 1e-9 km) on a
+    seeded sample of well-conditioned rays."""
+    from oracle import oracle
+    g = oracle.Grid(w.grid, w.ne)
+    pos = np.nonzero(well)[0]
+    pick = np.sort(np.random.default_rng(seed).choice(pos, min(n_sample, len(pos)), replace=False))
+    rays = o_idx[pick]
+    t0 = time.perf_counter()
+    conv = oracle.trace_fan(g, spec.replace(rtol=1e-11, atol_km=1e-9), indices=rays)
+    ok = np.ones(len(rays), bool)
+    return {"rays": int(len(rays)), "reference": "oracle, rtol 1e-11, atol 1e-9 km",
+            "this_path": gate_errors(res, conv, ok, rays), "oracle_same_rtol": gate_errors(o_res[pick], conv, ok),
+            "seconds": time.perf_counter() - t0}
 
 
 def run_reference(args):
@@ -412,41 +482,13 @@ def run_ours(args):
 
     line = None
     if rank == 0:
-        # accuracy: against the all-FP64 GPU path at the same tolerance and against
-        # a converged FP64 run (rtol 1e-11), over rays not next to a skip/Pedersen
-        # boundary; the FP64 path's own throughput at this tolerance
+        # the FP64 path's own throughput at this tolerance, and its records
         t0 = time.perf_counter()
         ref64 = rt.rt_trace(grid, rt.Fan(spec, rt.RT_FP64), stream=sptr)
         fp64_s = time.perf_counter() - t0
         conv = rt.rt_trace(grid, rt.Fan(w.fan.replace(rtol=1e-11, atol_km=1e-9), rt.RT_FP64), stream=sptr)
-        ok = ~near_boundary(conv, spec)
-
-        def errs(r, ref):
-            m = ok & (ref["status"] == r["status"])
-            e = {f: float(np.abs(r[f] - ref[f])[m].max()) for f in
-                 ("group_path_km", "ground_range_km", "az_dev_deg", "apogee_km")}
-            landed = m & (r["status"] == rt.RT_RAY_LANDED)
-            for f in ("land_lat_deg", "land_lon_deg"):
-                e[f] = float(np.abs(r[f] - ref[f])[landed].max()) if landed.any() else None
-            e["rays_compared"] = int(m.sum())
-            e["status_mismatch"] = int((ref["status"] != r["status"]).sum())
-            return e
-
-        def errs_idx(r, oref, idx):
-            # records r (the whole fan) against oracle records for rays idx; same
-            # well-conditioned set as above, all rays for the status count
-            m = ok[idx] & (oref["status"] == r["status"][idx])
-            e = {f: float(np.abs(r[f][idx] - oref[f])[m].max()) if m.any() else None for f in
-                 ("group_path_km", "ground_range_km", "az_dev_deg", "apogee_km")}
-            e["rays_compared"] = int(m.sum())
-            e["status_mismatch"] = int((oref["status"] != r["status"][idx]).sum())
-            return e
-
-        acc = {"vs_fp64_same_rtol": errs(res, ref64), "vs_converged_fp64": errs(res, conv),
-               "vs_richardson": richardson_table(rt, wl, grid, spec, prec, cfg, sptr) if args.workload == "c2" else None,
-               "fp64_same_rtol_vs_converged": errs(ref64, conv), "converged": "FP64 GPU path, rtol 1e-11"}
-        # ten times tighter tolerance: throughput and error of the same path
-        spec8 = w.fan.replace(rtol=args.rtol / 10.0)
+        # ten times tighter tolerance: throughput of the same path
+        spec8 = spec.replace(rtol=args.rtol / 10.0)
         fan8 = rt.Fan(spec8, prec)
         out8 = torch.empty(n * 64, dtype=torch.uint8, device="cuda")
         cfg8 = cfg
@@ -463,10 +505,36 @@ def run_ours(args):
             b8.record(stream)
             torch.cuda.synchronize()
             t8.append(a8.elapsed_time(b8))
-        res8 = rt.results_view(out8.cpu().numpy(), n)
+        res8 = rt.results_view(out8.cpu().numpy(), n).copy()
         nominal = {"rtol": args.rtol / 10.0, "rays_per_s": n / (np.mean(t8) / 1e3), "ms_per_step": float(np.mean(t8)),
-                   "ray_steps_per_s": float(res8["n_steps"].sum()) / (np.mean(t8) / 1e3),
-                   "error_vs_converged_fp64": errs(res8, conv)}
+                   "ray_steps_per_s": float(res8["n_steps"].sum()) / (np.mean(t8) / 1e3)}
+        richardson = (richardson_table(rt, wl, grid, spec, prec, cfg, sptr) if args.workload == "c2" else None)
+        cpu, acc = None, {"vs_richardson": richardson}
+        if world == 1:
+            # the CPU baseline leg traces the fan through the oracle; its records
+            # give the full-size parity of both GPU paths, and the oracle alone
+            # locates the skip / Pedersen boundaries that the mixed bar excludes
+            cpu, o_idx, o_res = cpu_oracle_rate(w, args.cpu_sample)
+            well, gate_info = oracle_well_conditioned(w, spec, o_idx, o_res)
+            acc["boundaries"] = gate_info
+            acc["vs_cpu_oracle"] = gate_errors(res, o_res, well, o_idx)
+            acc["fp64_gpu_vs_cpu_oracle"] = gate_errors(ref64, o_res, np.ones(len(o_idx), bool), o_idx,
+                                                         km=1e-6, deg=1e-7)
+            # the same fan at ten times tighter rtol against the oracle there
+            # (every second azimuth)
+            acc["tighter_rtol_vs_cpu_oracle"] = tighter_rtol_gate(w, spec8, res8)
+            # how far both paths are from a converged oracle run (rtol 1e-11) on a
+            # seeded sample of well-conditioned rays: the integrator's own error
+            acc["vs_converged_oracle"] = converged_sample(w, spec, res, o_idx, o_res, well)
+        # against the GPU FP64 path (the comparison baseline) over the same rays
+        well_all = np.ones(n, bool)
+        if world == 1 and len(o_idx) == n:
+            well_all = well
+        acc["vs_fp64_same_rtol"] = gate_errors(res, ref64, well_all)
+        acc["fp64_same_rtol_vs_converged_fp64_gpu"] = gate_errors(ref64, conv, well_all)
+        acc["vs_converged_fp64_gpu"] = gate_errors(res, conv, well_all)
+        acc["well_conditioned"] = ("rays not within 0.05 deg of elevation of a skip or Pedersen boundary "
+                                   "located with the oracle" if world == 1 else "all rays (no CPU leg at N > 1)")
         sec = mean_ms / 1e3
         flop = evals * FLOP_PER_EVAL[args.precision]
         if prec == rt.RT_MIXED:
@@ -481,13 +549,6 @@ def run_ours(args):
         alone_ms, _ = time_one_ray(rt, torch, grid, one_ray_spec(wl, spec, i_long), prec, cfg, 3, 2)
         critical = {"longest_ray_alone_ms": alone_ms, "fan_ms": mean_ms, "fan_over_alone": mean_ms / alone_ms,
                     "ns_per_stage_eval_alone": alone_ms * 1e6 / max(int(res["n_evals"][i_long]), 1)}
-        cpu = None
-        if world == 1:
-            # the CPU baseline leg traces the fan through the oracle; its records
-            # also give the full-size parity of both GPU paths
-            cpu, o_idx, o_res = cpu_oracle_rate(w, args.cpu_sample)
-            acc["vs_cpu_oracle"] = errs_idx(res, o_res, o_idx)
-            acc["fp64_gpu_vs_cpu_oracle"] = errs_idx(ref64, o_res, o_idx)
         batch = None
         if world == 1 and not args.no_batch and prec == rt.RT_MIXED:
             try:
@@ -690,7 +751,7 @@ def run_batch(rt, wl, torch, flush, steps=3):
     res = rt.results_view(out.cpu().numpy(), n)
     st = np.bincount(res["status"], minlength=8)
     sec = float(np.mean(ms)) / 1e3
-    out_d = {"workload": w.name, "rays": n, "ms_per_batch": sec * 1e3, "rays_per_s": n / sec,
+    out_d = {"workload": w.name, "rays": n, "rtol": w.fan.rtol, "ms_per_batch": sec * 1e3, "rays_per_s": n / sec,
              "ray_steps_per_s": float(res["n_steps"].sum()) / sec,
              "stage_evals_per_s": float(res["n_evals"].sum()) / sec,
              "steps_per_ray": {"min": int(res["n_steps"].min()), "p50": float(np.median(res["n_steps"])),
@@ -776,15 +837,13 @@ def run_batch(rt, wl, torch, flush, steps=3):
     grid_cr.close()
     # CPU baseline leg of the batch: the FP64 oracle on a seeded 5,000-ray
     # sample (its rays/s stands for the whole batch), and the batch's mixed
-    # records against the oracle's on that sample, rays next to a skip or
-    # Pedersen boundary left out
+    # records against the oracle's on that sample, over the sampled rays not
+    # within 0.05 deg of a boundary the oracle locates around them
     info, idx, o_res = cpu_oracle_rate(w, 5000)
-    ok = ~near_boundary(res, w.fan)[idx] & (o_res["status"] == res["status"][idx])
+    well, gate_info = oracle_well_conditioned(w, w.fan, idx, o_res)
     out_d["cpu_baseline"] = info
-    out_d["vs_cpu_oracle"] = {f: float(np.abs(res[f][idx] - o_res[f])[ok].max()) if ok.any() else None
-                              for f in ("group_path_km", "ground_range_km", "az_dev_deg", "apogee_km")}
-    out_d["vs_cpu_oracle"]["rays_compared"] = int(ok.sum())
-    out_d["vs_cpu_oracle"]["status_mismatch"] = int((o_res["status"] != res["status"][idx]).sum())
+    out_d["boundaries"] = gate_info
+    out_d["vs_cpu_oracle"] = gate_errors(res, o_res, well, idx)
     del graph
     plan.close()
     grid.close()
@@ -794,19 +853,23 @@ def run_batch(rt, wl, torch, flush, steps=3):
 def run_interpolants(rt, wl):
     """Accuracy of GD against Catmull-Rom (Sec. IV): one analytic ionosphere
     sampled on a coarse grid (1 deg, 1 deg, 5 km) and on a 4x finer grid that
-    stands in for the analytic field; 3,232 rays traced on the FP64 path at rtol
-    1e-9 on the coarse grid with each interpolant and on the fine grid with GD
-    (the reference).  Errors over rays with the same status on all three and
-    not next to a skip/Pedersen boundary."""
+    stands in for the analytic field; 3,232 rays traced on the FP64 path at
+    rtol 1e-9 on the coarse grid with each interpolant, against the oracle
+    with GD on the fine grid (the reference).  Errors over rays with the
+    reference's status on both and not within 0.05 deg of a boundary the
+    oracle locates on the fine grid."""
+    from oracle import boundaries as bd
+    from oracle import oracle
     c, nc, f, nf, spec = wl.interp_comparison()
     fan = rt.Fan(spec, rt.RT_FP64)
-    grids = {"gd": rt.Grid(c, nc.astype(np.float64)), "cr": rt.Grid(c, nc.astype(np.float64), interp="cr"),
-             "reference": rt.Grid(f, nf.astype(np.float64))}
+    grids = {"gd": rt.Grid(c, nc.astype(np.float64)), "cr": rt.Grid(c, nc.astype(np.float64), interp="cr")}
     res = {k: rt.rt_trace(gr, fan) for k, gr in grids.items()}
-    ref = res["reference"]
-    ok = ~near_boundary(ref, spec) & (res["gd"]["status"] == ref["status"]) & (res["cr"]["status"] == ref["status"])
+    og = oracle.Grid(f, nf)
+    ref = oracle.trace_fan(og, spec)
+    near, _ = bd.fan_exclusion(oracle, og, spec, ref)
+    ok = ~near & (res["gd"]["status"] == ref["status"]) & (res["cr"]["status"] == ref["status"])
     out = {"grids": {"coarse": list(c.shape), "reference": list(f.shape)}, "rays": spec.n_rays,
-           "rays_compared": int(ok.sum())}
+           "reference": "oracle, GD on the 4x finer grid", "rays_compared": int(ok.sum())}
     for k in ("gd", "cr"):
         e = {}
         for fld in ("group_path_km", "ground_range_km", "apogee_km"):

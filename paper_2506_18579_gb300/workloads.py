@@ -226,10 +226,12 @@ def config2(seed=2, dtype=np.float32, elev_step=0.5, az_step=10.0, freqs=(8.0, 1
                     g, ne.astype(dtype), fan, notes=dict(tid=info, seed=seed))
 
 
-def config4(seed=4, dtype=np.float32, rtol=1e-7) -> Workload:
+def config4(seed=4, dtype=np.float32, rtol=1e-8) -> Workload:
     """Ionogram-synthesis batch: 181x361x301 grid (0.5 deg, 0.5 deg, 2 km),
     two-layer Chapman + TID + 20 % day/night gradient; 2-30 MHz step 0.1 x
-    elevations 1-89 deg step 0.1 x O and X (495,122 rays)."""
+    elevations 1-89 deg step 0.1 x O and X (495,122 rays); RKF45 at rtol
+    1e-8, the anisotropic fan case's tolerance (the batch's accuracy is held
+    to the same bar)."""
     rng = np.random.default_rng(seed)
     g = centred_grid(TX[0], TX[1], 181, 361, 301, 0.5, 0.5, 2.0, **dipole_field(TX[1]))
     ne, info = two_layer_ne(g, rng, daynight=0.2)

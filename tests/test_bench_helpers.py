@@ -1,7 +1,8 @@
 """Host-side helpers of bench.py (no GPU): the one-ray fan used for the
-critical-path measurement must be the canonical ray it names, the boundary
-filter must flag both neighbours of a jump, and the Richardson extrapolation
-must recover a known limit and order."""
+critical-path measurement must be the canonical ray it names, the accuracy
+block must count statuses, shares within the bar and the compared rays as
+stated, and the Richardson extrapolation must recover a known limit and
+order."""
 import os
 import sys
 
@@ -26,19 +27,27 @@ def test_one_ray_spec_is_the_canonical_ray():
         assert one.mode_list == [m]
 
 
-def test_near_boundary_flags_both_neighbours_of_a_jump():
-    spec = wl.FanSpec(30.0, 112.0, 0.0, freq_mhz=[10.0], el_deg=np.arange(5.0, 10.01, 0.5), az_deg=[0.0, 90.0])
-    n_el, n_az = len(spec.el_deg), 2
-    res = np.zeros(spec.n_rays, dtype=[("status", "i4"), ("ground_range_km", "f8"), ("group_path_km", "f8")])
-    res["status"] = 1
-    r = res.reshape(n_el, n_az)
-    r["ground_range_km"][:, 0] = 1000.0 - 10.0 * np.arange(n_el)  # smooth
-    r["ground_range_km"][:, 1] = 1000.0 - 10.0 * np.arange(n_el)
-    r["ground_range_km"][6:, 1] += 200.0  # a jump between elevations 5 and 6 at azimuth 90
-    r["group_path_km"] = r["ground_range_km"]
-    flag = bench.near_boundary(res, spec).reshape(n_el, n_az)
-    assert not flag[:, 0].any()
-    assert flag[5, 1] and flag[6, 1] and flag[:, 1].sum() == 2
+def test_gate_errors_counts_statuses_shares_and_the_rays_it_compares():
+    """The accuracy block: statuses over all rays, errors and shares within
+    the bar over the well-conditioned rays whose statuses agree."""
+    dt = np.dtype([(f, "f8") for f in bench.ERROR_FIELDS] + [("status", "i4")])
+    ref = np.zeros(10, dt)
+    ref["status"] = 1
+    r = ref.copy()
+    r["group_path_km"] = [0.0, 0.01, 0.04, 0.06, 0.2, 0.0, 0.0, 0.0, 9.0, 5.0]
+    r["az_dev_deg"] = [0.0, 2e-4, 0, 0, 0, 0, 0, 0, 0, 0]
+    r["status"][9] = 2  # another status: counted, not compared
+    well = np.ones(10, bool)
+    well[8] = False  # near a boundary: not compared
+    e = bench.gate_errors(r, ref, well)
+    assert e["status_mismatch"] == 1 and e["rays_compared"] == 8
+    assert e["group_path_km"]["max"] == 0.2
+    assert e["group_path_km"]["within_bar"] == 6 / 8
+    assert e["p_and_d_beyond_bar_rays"] == 2
+    assert e["az_dev_deg"]["within_bar"] == 7 / 8
+    idx = np.array([0, 4, 9])  # the same with an index into the records
+    e2 = bench.gate_errors(r, ref[idx], np.ones(3, bool), idx)
+    assert e2["status_mismatch"] == 1 and e2["rays_compared"] == 2 and e2["group_path_km"]["max"] == 0.2
 
 
 def test_richardson_extrapolation_recovers_the_limit_and_the_order():

@@ -1,15 +1,37 @@
 """Parity of the CUDA tracer with the FP64 CPU oracle, through the C ABI.
 
-Tolerances: the all-FP64 path agrees within 1e-6 km in group path and ground
-range and 1e-7 deg in azimuth deviation; the mixed path within 0.05 km and
-1e-4 deg, over rays that are not next to a skip or Pedersen boundary (a
-status change or a range jump between neighbouring elevations).  Sizes: full
-fans where the oracle finishes in seconds, seeded samples of the full-size
-fans otherwise, plus ragged and degenerate cases.
+Tolerances: the all-FP64 path agrees within 1e-6 km in group path, ground
+range and apogee and 1e-7 deg in azimuth deviation; the mixed path within
+0.05 km and 1e-4 deg over rays that are not within 0.05 deg of elevation of
+a skip or Pedersen boundary.  The boundaries are located with the oracle
+alone (oracle/boundaries.py: a status change or a jump of ground range or
+group path between neighbouring elevations, bisected in elevation with the
+oracle to below 0.01 deg; a smooth steep stretch is not a boundary), never
+from the records under test.
+
+Sizes: whole fans where the oracle finishes in seconds, the whole 24,840-ray
+anisotropic fan at the tolerance the benchmark times (rtol 1e-8), a seeded
+5,000-ray sample of the 495,122-ray ionogram batch at its timed rtol, plus
+ragged and degenerate cases.
+
+At rtol 1e-8 the integrator's own truncation error on grazing rays (low
+elevation: a vertical error shows up ~1/sin(el) times larger in the landing
+point) reaches 0.1-0.2 km -- in the oracle too, against a run converged at
+rtol 1e-11.  A mixed-path ray whose float error estimate tips one discrete
+step decision (accept/reject, the quantised step factor, a face-aligned
+step) the other way than the oracle's takes a different step sequence, and
+on such rays the two then differ by that truncation error.  The whole-fan
+checks therefore bound the share of well-conditioned rays outside the bar
+(and how far out they may be), and the bar holds for every well-conditioned
+ray at ten times tighter rtol.  Azimuth deviation is the bearing of the end
+point: for rays ending a few km from the transmitter (near-vertical rays)
+1e-4 deg is millimetres, below the mixed path's position resolution, so it
+too is checked as a share.
 """
 import numpy as np
 import pytest
 
+from oracle import boundaries as bd
 from paper_2506_18579_gb300 import build as rtbuild
 from paper_2506_18579_gb300 import rtgd as rt
 from paper_2506_18579_gb300 import workloads as wl
@@ -18,6 +40,10 @@ pytestmark = pytest.mark.gpu
 
 FP64_KM, FP64_DEG = 1e-6, 1e-7
 MIX_KM, MIX_DEG = 0.05, 1e-4
+# whole-fan bounds of the mixed path at the timed tolerance (see the docstring)
+MIX_SHARE_KM, MIX_CAP_KM = 0.9995, 0.5  # share of well-conditioned rays within MIX_KM; cap for the rest
+MIX_SHARE_DEG, MIX_CAP_DEG = 0.995, 1e-3
+MIX_STATUS_SHARE = 0.001  # at most 0.1 % of rays may end with another status than the oracle's
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -38,18 +64,32 @@ def _close64(gpu, ref, idx=None, km=FP64_KM, deg=FP64_DEG):
         assert np.all(d <= tol), (f, d.max(), int(np.argmax(d)))
 
 
-def near_boundary(res, fan):
-    """Rays adjacent (in elevation) to a status change or a jump of ground
-    range or group path larger than 30 km between neighbouring elevations."""
-    n_az, n_el = len(fan.az_deg), len(fan.el_deg)
-    r = res.reshape(-1, n_el, n_az)
-    flag = np.zeros(r.shape, bool)
-    jump = ((r["status"][:, 1:] != r["status"][:, :-1]) |
-            (np.abs(np.diff(r["ground_range_km"], axis=1)) > 30.0) |
-            (np.abs(np.diff(r["group_path_km"], axis=1)) > 30.0))
-    flag[:, 1:] |= jump
-    flag[:, :-1] |= jump
-    return flag.reshape(-1)
+def _mixed_vs_oracle(gpu, ref, well, what=""):
+    """Whole-fan bounds of mixed records against oracle records: statuses,
+    then P' and D (the accuracy gate) and the azimuth deviation over the
+    well-conditioned rays with the oracle's status.  Returns the share of
+    well-conditioned rays within the bar."""
+    n = len(ref)
+    mism = gpu["status"] != ref["status"]
+    assert mism.sum() <= MIX_STATUS_SHARE * n, (what, int(mism.sum()))
+    m = well & ~mism
+    assert m.sum() >= 0.9 * well.sum(), what
+    inside = np.ones(n, bool)
+    for f in ("group_path_km", "ground_range_km"):
+        d = np.abs(gpu[f] - ref[f])[m]
+        assert np.mean(d <= MIX_KM) >= MIX_SHARE_KM, (what, f, int((d > MIX_KM).sum()), d.max())
+        assert d.max() <= MIX_CAP_KM, (what, f, d.max())
+        inside[m] &= np.abs(gpu[f] - ref[f])[m] <= MIX_KM
+    d = np.abs(gpu["az_dev_deg"] - ref["az_dev_deg"])[m]
+    assert np.mean(d <= MIX_DEG) >= MIX_SHARE_DEG, (what, int((d > MIX_DEG).sum()), d.max())
+    assert d.max() <= MIX_CAP_DEG, (what, d.max())
+    return float(inside[m].mean())
+
+
+def _well(orc, og, spec, ref):
+    """Rays not within 0.05 deg of a boundary located with the oracle."""
+    mask, _ = bd.fan_exclusion(orc, og, spec, ref)
+    return ~mask
 
 
 # ------------------------------------------------------------------ RHS
@@ -109,15 +149,34 @@ def test_fp64_rkf45_small_fan(orc):
     assert np.mean(gpu["n_attempts"] == ref["n_attempts"]) > 0.98
 
 
-def test_fp64_config2_full_size_sampled(orc):
+@pytest.fixture(scope="module")
+def c2_oracle(orc):
+    """The whole 24,840-ray anisotropic fan at the benchmark's rtol 1e-8:
+    oracle records (all host cores, ~10 s) and the rays away from the
+    boundaries the oracle locates."""
     w = wl.config2()
-    assert w.fan.n_rays == 24840
+    assert w.fan.n_rays == 24840 and w.fan.rtol == 1e-8
+    og = orc.Grid(w.grid, w.ne)
+    ref = orc.trace_fan(og, w.fan)
+    return w, og, ref, _well(orc, og, w.fan, ref)
+
+
+def test_fp64_config2_whole_fan_against_the_oracle(c2_oracle):
+    """Every ray of the fan, no exclusion: identical statuses, and the FP64
+    tolerance on all but at most 0.02 % of the rays (a step decision within
+    round-off of its threshold, e.g. a fused multiply-add on the GPU against
+    the oracle's separate rounding, may go the other way), those within 1e-3 km."""
+    w, _, ref, _ = c2_oracle
     g = rt.Grid(w.grid, w.ne)
     gpu = rt.rt_trace(g, rt.Fan(w.fan, rt.RT_FP64))
-    idx = wl.sample_indices(w.fan.n_rays, 48, seed=21)
-    ref = orc.trace_fan(orc.Grid(w.grid, w.ne), w.fan, indices=idx)
-    _close64(gpu[idx], ref)
-    assert np.all(gpu["status"] != rt.RT_RAY_NOT_RUN)
+    assert np.array_equal(gpu["status"], ref["status"])
+    off = np.zeros(len(ref), bool)
+    for f, tol in (("group_path_km", FP64_KM), ("ground_range_km", FP64_KM), ("apogee_km", FP64_KM),
+                   ("az_dev_deg", FP64_DEG)):
+        d = np.abs(gpu[f] - ref[f])
+        off |= d > tol
+        assert d.max() <= (1e-3 if f != "az_dev_deg" else 1e-5), (f, d.max())
+    assert off.sum() <= 0.0002 * len(ref), np.nonzero(off)[0]
 
 
 # ------------------------------------------------------------ mixed path
@@ -130,48 +189,47 @@ def test_mixed_config1_all_rays(orc, kernel):
     _close64(gpu, ref, km=MIX_KM, deg=MIX_DEG)
 
 
-def test_mixed_config2_full_size(orc):
-    """C2 at full size, every kernel and stencil variant.  Accuracy is judged
-    at rtol 1e-9, for each variant: at the C2 setting of
-    1e-8 the integrator's own error reaches ~0.1 km on long-range rays (in FP64
-    too), so two runs whose step sequences differ (the mixed path's FP32 error
-    estimate sees round-off at the 1e-8 level) cannot agree to 0.05 km there."""
-    w = wl.config2()
+def _variants():
+    """Every launch configuration the autotuner may choose for the fan (kernel
+    x stencil, the library's lane choice) and a few explicit lane counts."""
+    keys = [(st, kern, 0) for st in (rt.RT_STENCIL_GATHER, rt.RT_STENCIL_QUAD, rt.RT_STENCIL_TABLE)
+            for kern in (rt.RT_KERNEL_PLAIN, rt.RT_KERNEL_PERSISTENT)]
+    return keys + [(rt.RT_STENCIL_QUAD, rt.RT_KERNEL_PERSISTENT, 1), (rt.RT_STENCIL_TABLE, rt.RT_KERNEL_PLAIN, 1),
+                   (rt.RT_STENCIL_TABLE, rt.RT_KERNEL_PLAIN, 2), (rt.RT_STENCIL_GATHER, rt.RT_KERNEL_PLAIN, 4)]
+
+
+def test_mixed_config2_whole_fan_against_the_oracle(c2_oracle):
+    """The benchmark's workload itself (24,840 rays, rtol 1e-8), every launch
+    configuration the tuner may time, against the oracle's records of the
+    whole fan, over the rays away from oracle-located boundaries."""
+    w, _, ref, well = c2_oracle
+    assert well.mean() > 0.98  # boundaries exclude a few rays, not a band
     g = rt.Grid(w.grid, w.ne, table=True)
     fan = rt.Fan(w.fan, rt.RT_MIXED)
-    outs = {}
-    for st in (rt.RT_STENCIL_GATHER, rt.RT_STENCIL_QUAD, rt.RT_STENCIL_TABLE):
-        for kern in (rt.RT_KERNEL_PLAIN, rt.RT_KERNEL_PERSISTENT):
-            outs[(st, kern)] = rt.rt_trace(g, fan, cfg=rt.launch_config(kernel=kern, stencil=st))
-    for v in outs.values():
-        assert np.all(v["status"] != rt.RT_RAY_NOT_RUN)
+    for key in _variants():
+        st, kern, lanes = key
+        res = rt.rt_trace(g, fan, cfg=rt.launch_config(kernel=kern, stencil=st, lanes_per_ray=lanes))
+        assert np.all(res["status"] != rt.RT_RAY_NOT_RUN), key
+        _mixed_vs_oracle(res, ref, well, key)
 
-    spec = w.fan.replace(rtol=1e-9)
-    fp64 = rt.rt_trace(g, rt.Fan(spec, rt.RT_FP64))
-    conv = rt.rt_trace(g, rt.Fan(w.fan.replace(rtol=1e-11, atol_km=1e-9), rt.RT_FP64))
-    ok = ~near_boundary(fp64, spec)
-    assert ok.mean() > 0.6
-    keys = [(st, kern, 0) for st, kern in outs] + [
-        (rt.RT_STENCIL_QUAD, rt.RT_KERNEL_PERSISTENT, 1), (rt.RT_STENCIL_QUAD, rt.RT_KERNEL_PERSISTENT, 4),
-        (rt.RT_STENCIL_TABLE, rt.RT_KERNEL_PLAIN, 2), (rt.RT_STENCIL_GATHER, rt.RT_KERNEL_PLAIN, 4)]
-    variants = {k: rt.rt_trace(g, rt.Fan(spec, rt.RT_MIXED),
-                               cfg=rt.launch_config(kernel=k[1], stencil=k[0], lanes_per_ray=k[2]))
-                for k in keys}
-    mixed = variants[(rt.RT_STENCIL_QUAD, rt.RT_KERNEL_PERSISTENT, 0)]
-    for key, mv in variants.items():
-        same = (mv["status"] == fp64["status"]) & (conv["status"] == fp64["status"])
-        assert same[ok].mean() > 0.999, key
-        m = ok & same
-        for ref in (fp64, conv):
-            for f, tol in (("group_path_km", MIX_KM), ("ground_range_km", MIX_KM), ("az_dev_deg", MIX_DEG)):
-                d = np.abs(mv[f] - ref[f])[m]
-                assert np.all(d <= tol), (key, f, d.max())
-    m = ok & (mixed["status"] == fp64["status"])
-    idx = wl.sample_indices(w.fan.n_rays, 48, seed=22)
-    idx = idx[m[idx]]
-    ref = orc.trace_fan(orc.Grid(w.grid, w.ne), spec, indices=idx)
-    _close64(mixed[idx], ref, km=MIX_KM, deg=MIX_DEG)
-    _close64(fp64[idx], ref)
+
+def test_mixed_config2_tighter_rtol_meets_the_bar_on_every_ray(orc):
+    """At rtol 1e-9 the truncation error of a diverged step sequence is well
+    inside 0.05 km: every well-conditioned ray of the fan (every second
+    azimuth, 12,420 rays) meets the mixed bar in P', D and the apogee."""
+    w = wl.config2()
+    spec = w.fan.replace(rtol=1e-9, az_deg=w.fan.az_deg[::2])
+    og = orc.Grid(w.grid, w.ne)
+    ref = orc.trace_fan(og, spec)
+    well = _well(orc, og, spec, ref)
+    g = rt.Grid(w.grid, w.ne, table=True)
+    for st, lanes in ((rt.RT_STENCIL_TABLE, 4), (rt.RT_STENCIL_QUAD, 1)):
+        res = rt.rt_trace(g, rt.Fan(spec, rt.RT_MIXED), cfg=rt.launch_config(stencil=st, lanes_per_ray=lanes))
+        m = well & (res["status"] == ref["status"])
+        assert (~(res["status"] == ref["status"])).sum() <= MIX_STATUS_SHARE * len(ref)
+        for f in ("group_path_km", "ground_range_km", "apogee_km"):
+            d = np.abs(res[f] - ref[f])[m]
+            assert d.max() <= MIX_KM, (st, lanes, f, d.max(), int((d > MIX_KM).sum()))
 
 
 # --------------------------------------------------------- edge cases
@@ -185,7 +243,7 @@ def test_ragged_and_tiny_fans(orc):
         _close64(rt.rt_trace(g, rt.Fan(spec, rt.RT_FP64)), ref)
         spec9 = spec.replace(rtol=1e-9)
         ref9 = orc.trace_fan(og, spec9)
-        ok = ~near_boundary(ref9, spec9)
+        ok = _well(orc, og, spec9, ref9)
         for kern in (rt.RT_KERNEL_PLAIN, rt.RT_KERNEL_PERSISTENT):
             for lanes in (1, 2, 4):
                 gm = rt.rt_trace(g, rt.Fan(spec9, rt.RT_MIXED),
@@ -224,8 +282,9 @@ def test_fused_requests_match_oracle(orc, interp, stencil, integrator):
         view[i, :, :, a] = out.reshape(n_m, n_el)
     srv.close()
     assert max(sizes) > 1
-    ref = orc.trace_fan(orc.Grid(w.grid, w.ne, interp=interp), spec)
-    ok = ~near_boundary(ref, spec)
+    og = orc.Grid(w.grid, w.ne, interp=interp)
+    ref = orc.trace_fan(og, spec)
+    ok = _well(orc, og, spec, ref)
     assert ok.sum() >= 200  # of 984 rays; the rest neighbour a status change or a range jump
     _close64(full[ok], ref[ok], km=MIX_KM, deg=MIX_DEG)
 
@@ -259,7 +318,7 @@ def test_trace_fans_device_matches_oracle_and_each_fan_alone(orc):
         s.synchronize()
         assert part.tobytes() == rt.results_view(one.cpu().numpy(), f.n_rays).tobytes(), k
         ref = orc.trace_fan(og, sp)
-        ok = ~near_boundary(ref, sp) if len(sp.el_deg) > 1 else np.ones(f.n_rays, bool)
+        ok = _well(orc, og, sp, ref)
         assert ok.sum() >= min(f.n_rays, 30)
         _close64(part[ok], ref[ok], km=MIX_KM, deg=MIX_DEG)
 
@@ -430,7 +489,7 @@ def test_catmull_rom_option_matches_oracle(orc):
     spec = w.fan.replace(integrator=wl.RK4, h_km=1.0, el_deg=[8.0, 20.0, 32.0, 44.0], az_deg=[0.0, 120.0])
     ref_r = orc.trace_fan(og, spec)
     _close64(rt.rt_trace(g, rt.Fan(spec, rt.RT_FP64)), ref_r)
-    ok = ~near_boundary(ref_r, spec)
+    ok = _well(orc, og, spec, ref_r)
     for lanes in (1, 2, 4):
         gm = rt.rt_trace(g, rt.Fan(spec, rt.RT_MIXED), cfg=rt.launch_config(lanes_per_ray=lanes))
         _close64(gm[ok], ref_r[ok], km=MIX_KM, deg=MIX_DEG)
@@ -496,14 +555,28 @@ def test_ionogram_matches_oracle(orc, prec):
         np.testing.assert_allclose([p["el_deg"] for p in pts], [q[2] for q in ref], atol=1e-6)
 
 
-def test_config4_batched_fan_in_captured_graph(orc):
-    """The ionogram-synthesis batch at full size: 181x361x301 grid, 281
-    frequencies x 881 elevations x O/X = 495,122 rays of 50-5000 steps, run as
-    one plan captured in a CUDA graph (mixed; plain and persistent kernel) and
-    by the FP64 kernel; sampled rays against the oracle."""
-    torch = pytest.importorskip("torch")
+@pytest.fixture(scope="module")
+def c4_sample(orc):
+    """The ionogram-synthesis batch at its timed rtol: a seeded 5,000-ray
+    sample traced by the oracle, and which of those rays lie away from the
+    boundaries the oracle locates around them."""
     w = wl.config4()
-    assert w.fan.n_rays == 495122
+    assert w.fan.n_rays == 495122 and w.fan.rtol == 1e-8
+    og = orc.Grid(w.grid, w.ne)
+    idx = wl.sample_indices(w.fan.n_rays, 5000, seed=1234)
+    ref = orc.trace_fan(og, w.fan, indices=idx)
+    near, _ = bd.sample_exclusion(orc, og, w.fan, idx, ref)
+    return w, idx, ref, ~near
+
+
+def test_config4_batched_fan_in_captured_graph(c4_sample):
+    """The ionogram-synthesis batch at full size and its timed rtol 1e-8:
+    181x361x301 grid, 281 frequencies x 881 elevations x O/X = 495,122 rays of
+    50-5000 steps, run as one plan captured in a CUDA graph (mixed; plain and
+    persistent kernel) and by the FP64 kernel; 5,000 seeded rays of each
+    against the oracle."""
+    torch = pytest.importorskip("torch")
+    w, idx, ref, well = c4_sample
     g = rt.Grid(w.grid, w.ne)
     n = w.fan.n_rays
     plan = rt.Plan(g, rt.Fan(w.fan, rt.RT_MIXED))
@@ -521,13 +594,18 @@ def test_config4_batched_fan_in_captured_graph(orc):
     assert st[rt.RT_RAY_LANDED] > 0.1 * n and st[rt.RT_RAY_ESCAPED] > 0.1 * n  # mixed outcomes
     steps = mixed["n_steps"]
     assert steps.min() < 100 and steps.max() > 1000  # uneven ray lengths
-    fp64 = rt.rt_trace(g, rt.Fan(w.fan, rt.RT_FP64))
-    idx = wl.sample_indices(n, 24, seed=44)
-    ref = orc.trace_fan(orc.Grid(w.grid, w.ne), w.fan, indices=idx)
-    _close64(fp64[idx], ref)
-    ok = ~near_boundary(fp64, w.fan)[idx] & (mixed["status"][idx] == ref["status"])
-    _close64(mixed[idx][ok], ref[ok], km=MIX_KM, deg=MIX_DEG)
+    assert well.mean() > 0.98
+    _mixed_vs_oracle(mixed[idx], ref, well, "plain graph")
     plan.close()
+    fp64 = rt.rt_trace(g, rt.Fan(w.fan, rt.RT_FP64))[idx]  # every sampled ray, no exclusion
+    assert np.array_equal(fp64["status"], ref["status"])
+    off = np.zeros(len(idx), bool)
+    for f, tol in (("group_path_km", FP64_KM), ("ground_range_km", FP64_KM), ("apogee_km", FP64_KM),
+                   ("az_dev_deg", FP64_DEG)):
+        d = np.abs(fp64[f] - ref[f])
+        off |= d > tol
+        assert d.max() <= (1e-3 if f != "az_dev_deg" else 1e-5), (f, d.max())
+    assert off.sum() <= 2, np.nonzero(off)[0]
     # the same batch as one persistent launch (lane groups claim rays from an
     # atomic counter), also captured in a graph and replayed twice
     cfg = rt.launch_config(kernel=rt.RT_KERNEL_PERSISTENT, stencil=rt.RT_STENCIL_QUAD, lanes_per_ray=1,
@@ -546,30 +624,5 @@ def test_config4_batched_fan_in_captured_graph(orc):
     pers = rt.results_view(outp.cpu().numpy(), n).copy()
     assert pers.tobytes() == first.tobytes()  # replays are deterministic
     assert np.all(pers["status"] != rt.RT_RAY_NOT_RUN)
-    # The two kernels run the same per-ray arithmetic, but their instantiations
-    # may contract a few multiply-adds differently; at this batch's rtol 1e-7 a
-    # handful of sensitive rays turn such last-bit differences into different
-    # step sequences.  Nearly every ray must agree within the mixed tolerance.
-    well = ~near_boundary(mixed, w.fan) & (pers["status"] == mixed["status"])
-    assert well.sum() > 0.9 * n and (pers["status"] != mixed["status"]).sum() < 0.001 * n
-    close = np.ones(n, bool)
-    for f, tol in (("group_path_km", MIX_KM), ("ground_range_km", MIX_KM), ("az_dev_deg", MIX_DEG)):
-        close &= np.abs(pers[f] - mixed[f]) <= tol
-    assert close[well].mean() > 0.999, (close[well].mean(), int((~close[well]).sum()))
+    _mixed_vs_oracle(pers[idx], ref, well, "persistent graph")
     pplan.close()
-
-
-def test_config4_inputs_at_the_precision_forms_tolerance(orc):
-    """The batch's inputs (181x361x301 grid, day/night gradient) traced at
-    rtol 1e-8, the tolerance of the precision form: the mixed path meets its
-    bar (0.05 km, 1e-4 deg) against the oracle on sampled rays away from skip
-    and Pedersen boundaries.  (At the batch's own rtol 1e-7 the two differ by
-    the integrator's truncation error instead.)"""
-    w = wl.config4(rtol=1e-8)
-    g = rt.Grid(w.grid, w.ne)
-    mixed = rt.rt_trace(g, rt.Fan(w.fan, rt.RT_MIXED))
-    idx = wl.sample_indices(w.fan.n_rays, 300, seed=48)
-    ref = orc.trace_fan(orc.Grid(w.grid, w.ne), w.fan, indices=idx)
-    ok = ~near_boundary(mixed, w.fan)[idx] & (mixed["status"][idx] == ref["status"])
-    assert ok.sum() > 250
-    _close64(mixed[idx][ok], ref[ok], km=MIX_KM, deg=MIX_DEG)
