@@ -259,8 +259,9 @@ rt_err rt_trace_fans_device(const rt_grid *grid, const rt_fan_desc *const *fans,
  * memory budget, device memory owned by another runtime).  This call makes no
  * cudaMalloc/cudaFree (or other allocating) call: its scratch -- the ray
  * counter and the fan tables -- is a fixed array inside the library (16 bytes
- * + 4096 doubles, about 32 KiB, held on every GPU that loads the library until
- * the process exits), filled from a fixed host staging array of the same size.
+ * + 3 x 4096 doubles, about 96 KiB, held on every GPU that loads the library
+ * until the process exits), filled from a fixed host staging array of the
+ * same size.
  * The paper has no counterpart; it is an interface variant of
  * rt_trace_device.  Limits and rules:
  *   - n_freq + n_el + n_az must not exceed 4096 (RT_EINVAL otherwise).
@@ -305,6 +306,38 @@ rt_err rt_plan_create(const rt_grid *grid, const rt_fan_desc *fan, const rt_laun
 size_t rt_plan_rays(const rt_plan *plan);
 rt_err rt_plan_execute(const rt_plan *plan, rt_ray_result *out_dev, size_t out_len, void *stream);
 rt_err rt_plan_destroy(rt_plan *plan);
+
+/* Longest-first order for a plan (batched uneven fans; the paper has no
+ * counterpart: it traces one scan at a time on a CPU).  A batch of uneven
+ * rays lasts as long as its most expensive rays take one after the other; this
+ * call lets a plan start those first and give them more lanes.
+ *   cost_dev: device records of an earlier trace of a fan of the same shape
+ *     (rt_plan_rays(plan) records, canonical order): the plan's previous
+ *     execution, or the same scan on the previous ionosphere snapshot.  A
+ *     ray's expected cost is the largest n_evals within `spread` (0..64)
+ *     elevation and frequency steps of it (same mode and azimuth) in those
+ *     records, so that a boundary that moved a few steps between snapshots
+ *     keeps its rays marked expensive.  NULL: back to the plan's own order.
+ *   long_factor > 0 (mixed-precision plans): rays whose expected cost is at
+ *     least long_factor times the median (at most a sixteenth of the rays)
+ *     are traced at four lanes per ray by a plain launch of their own, on a
+ *     second, high-priority stream forked from and joined back to the
+ *     execute call's stream; *n_long (may be NULL) receives their number.
+ *   flags: by default the other rays are handed out in descending order of
+ *     expected cost as well (rays of costs within 2^(1/8) of each other keep
+ *     their canonical order); RT_PLAN_REST_IN_PLAN_ORDER keeps the plan's own
+ *     claim order for them.
+ * rt_plan_execute traces the other rays with the plan's launch
+ * configuration.  A ray's record does
+ * not depend on the order; rays in the four-lane launch give the records of
+ * a four-lane plain trace (their contraction sums in another order).  The
+ * execute step stays graph-capturable (the fork and join are stream events).
+ * Blocking: copies the costs to the host, sorts and uploads the order.  Not
+ * concurrent with an execution of the same plan.  Errors: RT_EINVAL,
+ * RT_ENOMEM, RT_ECUDA, RT_ETIMEOUT. */
+enum { RT_PLAN_REST_IN_PLAN_ORDER = 1u };
+rt_err rt_plan_order(rt_plan *plan, const rt_ray_result *cost_dev, int32_t spread, double long_factor,
+                     uint32_t flags, size_t *n_long, void *stream);
 
 /* --------------------------------------------------------------- ionogram */
 /* Oblique-ionogram synthesis (Sec. IV-B-4: joint frequency-elevation scan,

@@ -11,6 +11,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -258,13 +259,13 @@ rt_err sync_with_timeout(cudaStream_t st) {
     }
 }
 
-// Device view of a fan whose tables (freq, el, az) start at tab.
+// Device view of a fan whose tables (fan_tables_into) start at tab.
 FanDev fill_fandev(const rt_grid *grid, const rt_fan_desc *fan, size_t n, int order, const double *tab) {
     FanDev f;
     std::memset(&f, 0, sizeof(f));
-    f.freq = tab;
-    f.el = tab + fan->n_freq;
-    f.az = tab + fan->n_freq + fan->n_el;
+    f.freq = (const FanFreq *)tab;
+    f.el = (const FanEl *)(tab + 2 * (size_t)fan->n_freq);
+    f.az = (const FanAz *)(tab + 2 * (size_t)fan->n_freq + 2 * (size_t)fan->n_el);
     f.n_freq = fan->n_freq;
     f.n_el = fan->n_el;
     f.n_az = fan->n_az;
@@ -296,28 +297,51 @@ FanDev fill_fandev(const rt_grid *grid, const rt_fan_desc *fan, size_t n, int or
     return f;
 }
 
+// The tables of a fan (layout FanFreq[n_freq], FanEl[n_el], FanAz[n_az], all
+// in doubles: fan_table_doubles) written to dst.  The float factors are the
+// double expressions rounded once; the sines and cosines are the host's.
+void fan_tables_into(const rt_grid *grid, const rt_fan_desc *fan, double *dst) {
+    FanFreq *fq = (FanFreq *)dst;
+    FanEl *fe = (FanEl *)(dst + 2 * (size_t)fan->n_freq);
+    FanAz *fa = (FanAz *)(dst + 2 * (size_t)fan->n_freq + 2 * (size_t)fan->n_el);
+    for (int i = 0; i < fan->n_freq; ++i) {
+        const double f_hz = fan->freq_mhz[i] * 1e6;
+        fq[i].f_hz = f_hz;
+        fq[i].xfac = (float)(kPlasmaHz2PerM3 / (f_hz * f_hz));
+        fq[i].ab0 = (float)(kGyroHzPerTesla / f_hz * grid->desc.field.b0_tesla);
+    }
+    for (int i = 0; i < fan->n_el; ++i) {
+        const double el = fan->el_deg[i] * kDeg2Rad;
+        fe[i].s = std::sin(el);
+        fe[i].c = std::cos(el);
+    }
+    for (int i = 0; i < fan->n_az; ++i) {
+        const double az = fan->az_deg[i] * kDeg2Rad;
+        fa[i].s = std::sin(az);
+        fa[i].c = std::cos(az);
+        fa[i].rad = az;
+    }
+}
+
 // The device scratch image of a fan: a zeroed 16-byte ray counter followed
-// by the frequency, elevation and azimuth tables, written into
-// library-owned pageable host memory (fan_image_bytes(fan) bytes at img).
-// Uploading this copy (one cudaMemcpyAsync) instead of the caller's arrays
-// means the caller may change or free its arrays as soon as the call
-// returns, whether they are pinned or not: a copy from pageable memory has
-// read its source when cudaMemcpyAsync returns.
+// by the fan's tables, built in library-owned pageable host memory
+// (fan_image_bytes(fan) bytes at img).  Uploading this image (one
+// cudaMemcpyAsync) instead of the caller's arrays means the caller may change
+// or free its arrays as soon as the call returns, whether they are pinned or
+// not: a copy from pageable memory has read its source when cudaMemcpyAsync
+// returns.
 size_t fan_image_bytes(const rt_fan_desc *fan) {
-    return 16 + ((size_t)fan->n_freq + fan->n_el + fan->n_az) * sizeof(double);
+    return 16 + fan_table_doubles(fan->n_freq, fan->n_el, fan->n_az) * sizeof(double);
 }
 
-void fan_image_into(const rt_fan_desc *fan, char *img) {
+void fan_image_into(const rt_grid *grid, const rt_fan_desc *fan, char *img) {
     std::memset(img, 0, 16);
-    double *tab = (double *)(img + 16);
-    std::memcpy(tab, fan->freq_mhz, fan->n_freq * sizeof(double));
-    std::memcpy(tab + fan->n_freq, fan->el_deg, fan->n_el * sizeof(double));
-    std::memcpy(tab + fan->n_freq + fan->n_el, fan->az_deg, fan->n_az * sizeof(double));
+    fan_tables_into(grid, fan, (double *)(img + 16));
 }
 
-std::vector<char> fan_image(const rt_fan_desc *fan) {
+std::vector<char> fan_image(const rt_grid *grid, const rt_fan_desc *fan) {
     std::vector<char> img(fan_image_bytes(fan));
-    fan_image_into(fan, img.data());
+    fan_image_into(grid, fan, img.data());
     return img;
 }
 
@@ -338,7 +362,7 @@ rt_err queue_trace(const rt_grid *grid, const rt_fan_desc *fan, rt_ray_result *o
     int order = 0;
     if ((r = make_plan(grid, fan, n, cfg, &lp, &order)) != RT_OK) return r;
 
-    const std::vector<char> img = fan_image(fan);
+    const std::vector<char> img = fan_image(grid, fan);
     char *ws = nullptr;
     CUDA_TRY(cudaMallocAsync((void **)&ws, img.size(), st));
     unsigned long long *counter = (unsigned long long *)ws;
@@ -372,7 +396,7 @@ rt_err rtgd_queue_trace_fans(const rt_grid *grid, const rt_fan_desc *const *fans
         if (fans[k]->precision != RT_MIXED) return fail(RT_EINVAL, "fused trace: mixed-precision fans only");
         if (fans[k]->integrator != fans[0]->integrator) return fail(RT_EINVAL, "fused trace: fans differ in integrator");
         n_total += fan_rays(fans[k]);
-        n_tab += (size_t)fans[k]->n_freq + fans[k]->n_el + fans[k]->n_az;
+        n_tab += fan_table_doubles(fans[k]->n_freq, fans[k]->n_el, fans[k]->n_az);
     }
     if (out_len < n_total) return fail(RT_EINVAL, "out_len %zu < %zu rays", out_len, n_total);
     if (n_total >= ((size_t)1 << 31)) return fail(RT_EINVAL, "fused trace too large (at most 2^31 - 1 rays)");
@@ -400,13 +424,11 @@ rt_err rtgd_queue_trace_fans(const rt_grid *grid, const rt_fan_desc *const *fans
     for (int k = 0; k < n_fans; ++k) {
         const rt_fan_desc *fk = fans[k];
         const size_t nk = fan_rays(fk);
-        std::memcpy(tab_h + t, fk->freq_mhz, fk->n_freq * sizeof(double));
-        std::memcpy(tab_h + t + fk->n_freq, fk->el_deg, fk->n_el * sizeof(double));
-        std::memcpy(tab_h + t + fk->n_freq + fk->n_el, fk->az_deg, fk->n_az * sizeof(double));
+        fan_tables_into(grid, fk, tab_h + t);
         fd[k] = fill_fandev(grid, fk, nk, order, tab_d + t);
         first[k] = acc;
         acc += (long long)nk;
-        t += (size_t)fk->n_freq + fk->n_el + fk->n_az;
+        t += fan_table_doubles(fk->n_freq, fk->n_el, fk->n_az);
     }
     first[n_fans] = acc;
     cudaError_t e = cudaMemcpyAsync(ws, blob.data(), bytes, cudaMemcpyHostToDevice, st);
@@ -716,6 +738,13 @@ struct rt_plan {
     LaunchPlan lp;
     size_t n = 0;
     char *ws = nullptr;  // ray counter (16 B) + fan tables
+    // longest-first order (rt_plan_order): claim order over all rays, the
+    // first n_long of which run in a four-lane launch on the side stream
+    int *perm = nullptr;
+    size_t n_long = 0;
+    LaunchPlan lp_long;
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 rt_err rt_plan_create(const rt_grid *grid, const rt_fan_desc *fan, const rt_launch_config *cfg, rt_plan **out) {
@@ -735,14 +764,10 @@ rt_err rt_plan_create(const rt_grid *grid, const rt_fan_desc *fan, const rt_laun
         delete p;
         return r;
     }
-    const size_t n_tab = (size_t)fan->n_freq + fan->n_el + fan->n_az;
-    cudaError_t e = cudaMalloc((void **)&p->ws, 16 + n_tab * sizeof(double));
+    const std::vector<char> img = fan_image(grid, fan);
+    cudaError_t e = cudaMalloc((void **)&p->ws, img.size());
     double *tab = (double *)(p->ws + 16);
-    if (e == cudaSuccess) e = cudaMemcpy(tab, fan->freq_mhz, fan->n_freq * sizeof(double), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(tab + fan->n_freq, fan->el_deg, fan->n_el * sizeof(double), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(tab + fan->n_freq + fan->n_el, fan->az_deg, fan->n_az * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->ws, img.data(), img.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(p->ws);
         delete p;
@@ -762,13 +787,135 @@ rt_err rt_plan_execute(const rt_plan *plan, rt_ray_result *out_dev, size_t out_l
     if (out_len < plan->n) return fail(RT_EINVAL, "out_len %zu < %zu rays", out_len, plan->n);
     cudaStream_t st = (cudaStream_t)stream;
     CUDA_TRY(cudaMemsetAsync(plan->ws, 0, 16, st));
-    CUDA_TRY(launch_trace(plan->grid->g, plan->f, out_dev, (unsigned long long *)plan->ws, plan->lp, st));
+    if (!plan->perm) {
+        CUDA_TRY(launch_trace(plan->grid->g, plan->f, out_dev, (unsigned long long *)plan->ws, plan->lp, st));
+        return RT_OK;
+    }
+    // ordered: the n_long most expensive rays at four lanes each on the side
+    // stream (forked from and joined back to `stream`, so the two launches
+    // run concurrently and a capture of `stream` records both), the rest in
+    // descending cost order on `stream`
+    FanDev fl = plan->f, fb = plan->f;
+    fl.perm = fb.perm = plan->perm;
+    fl.perm_off = 0;
+    fl.n_rays = (long long)plan->n_long;
+    fb.perm_off = (long long)plan->n_long;
+    fb.n_rays = (long long)(plan->n - plan->n_long);
+    if (plan->n_long > 0) {
+        CUDA_TRY(cudaEventRecord(plan->fork, st));
+        CUDA_TRY(cudaStreamWaitEvent(plan->side, plan->fork, 0));
+        CUDA_TRY(launch_trace(plan->grid->g, fl, out_dev, nullptr, plan->lp_long, plan->side));
+        CUDA_TRY(cudaEventRecord(plan->join, plan->side));
+    }
+    CUDA_TRY(launch_trace(plan->grid->g, fb, out_dev, (unsigned long long *)plan->ws, plan->lp, st));
+    if (plan->n_long > 0) CUDA_TRY(cudaStreamWaitEvent(st, plan->join, 0));
+    return RT_OK;
+}
+
+rt_err rt_plan_order(rt_plan *plan, const rt_ray_result *cost_dev, int32_t spread, double long_factor,
+                     uint32_t flags, size_t *n_long, void *stream) {
+    if (!plan) return fail(RT_EINVAL, "plan is NULL");
+    if (spread < 0 || spread > 64) return fail(RT_EINVAL, "spread must be in 0..64");
+    if (flags & ~(uint32_t)RT_PLAN_REST_IN_PLAN_ORDER) return fail(RT_EINVAL, "unknown flags 0x%x", flags);
+    if (!std::isfinite(long_factor)) return fail(RT_EINVAL, "long_factor must be finite");
+    if (n_long) *n_long = 0;
+    if (!cost_dev) {  // back to the plan's own order
+        if (plan->perm) cudaFree(plan->perm);
+        plan->perm = nullptr;
+        plan->n_long = 0;
+        return RT_OK;
+    }
+    const size_t n = plan->n;
+    cudaStream_t st = (cudaStream_t)stream;
+    // the n_evals field of every record (a strided copy)
+    std::vector<int32_t> ev(n);
+    CUDA_TRY(cudaMemcpy2DAsync(ev.data(), sizeof(int32_t), (const char *)cost_dev + offsetof(rt_ray_result, n_evals),
+                               sizeof(rt_ray_result), sizeof(int32_t), n, cudaMemcpyDeviceToHost, st));
+    rt_err r = sync_with_timeout(st);
+    if (r != RT_OK) return r;
+    // expected cost: the largest cost within `spread` elevation and frequency
+    // steps of the same mode and azimuth (canonical order [freq][mode][el][az])
+    const FanDev &f = plan->f;
+    const long long n_f = f.n_freq, n_m = f.n_modes, n_e = f.n_el, n_a = f.n_az;
+    std::vector<int32_t> tmp(n), cost(n);
+    auto at = [&](long long q, long long m, long long e, long long a) { return ((q * n_m + m) * n_e + e) * n_a + a; };
+    for (long long q = 0; q < n_f; ++q)
+        for (long long m = 0; m < n_m; ++m)
+            for (long long e = 0; e < n_e; ++e)
+                for (long long a = 0; a < n_a; ++a) {
+                    int32_t v = 0;
+                    for (long long d = std::max(0LL, e - spread); d <= std::min(n_e - 1, e + spread); ++d)
+                        v = std::max(v, ev[at(q, m, d, a)]);
+                    tmp[at(q, m, e, a)] = v;
+                }
+    for (long long q = 0; q < n_f; ++q)
+        for (long long m = 0; m < n_m; ++m)
+            for (long long e = 0; e < n_e; ++e)
+                for (long long a = 0; a < n_a; ++a) {
+                    int32_t v = 0;
+                    for (long long d = std::max(0LL, q - spread); d <= std::min(n_f - 1, q + spread); ++d)
+                        v = std::max(v, tmp[at(d, m, e, a)]);
+                    cost[at(q, m, e, a)] = v;
+                }
+    // descending cost, eight buckets per octave (rays of one bucket keep
+    // their canonical order, so neighbours stay together): a counting sort
+    auto key = [](int32_t c) { return (int)std::floor(8.0 * std::log2((double)std::max(c, 1))); };
+    constexpr int kKeys = 8 * 32;
+    std::vector<size_t> start(kKeys + 1, 0);
+    for (size_t i = 0; i < n; ++i) ++start[kKeys - 1 - key(cost[i]) + 1];
+    for (int k = 0; k < kKeys; ++k) start[k + 1] += start[k];
+    std::vector<int> perm(n);
+    for (size_t i = 0; i < n; ++i) perm[start[kKeys - 1 - key(cost[i])]++] = (int)i;
+    // the four-lane share: rays whose expected cost is at least long_factor
+    // times the median (mixed path only), at most a sixteenth of the rays
+    size_t nl = 0;
+    if (long_factor > 0.0 && f.precision == RT_MIXED) {
+        std::vector<int32_t> sorted(cost);
+        std::nth_element(sorted.begin(), sorted.begin() + (long long)(n / 2), sorted.end());
+        const double thr = long_factor * (double)sorted[n / 2];
+        while (nl < n / 16 && (double)cost[perm[nl]] >= thr) ++nl;
+    }
+    if (flags & RT_PLAN_REST_IN_PLAN_ORDER) {
+        // the other rays in the plan's own claim order
+        std::vector<char> is_long(n, 0);
+        for (size_t i = 0; i < nl; ++i) is_long[perm[i]] = 1;
+        size_t k = nl;
+        for (long long c = 0; c < (long long)n; ++c) {
+            long long ray = c;
+            if (f.order == RT_ORDER_ELEVATION_FASTEST) {  // as the kernels' claim_to_ray
+                const long long e = c % n_e, rest = c / n_e, a = rest % n_a, fm = rest / n_a;
+                ray = (fm * n_e + e) * n_a + a;
+            }
+            if (!is_long[ray]) perm[k++] = (int)ray;
+        }
+    }
+    if (!plan->perm) CUDA_TRY(cudaMalloc((void **)&plan->perm, n * sizeof(int)));
+    CUDA_TRY(cudaMemcpy(plan->perm, perm.data(), n * sizeof(int), cudaMemcpyHostToDevice));
+    if (!plan->side) {
+        int lo = 0, hi = 0;
+        CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        // the four-lane launch gets the highest priority: when both launches
+        // have blocks waiting, an SM that frees up takes one of its blocks
+        CUDA_TRY(cudaStreamCreateWithPriority(&plan->side, cudaStreamNonBlocking, hi));
+        CUDA_TRY(cudaEventCreateWithFlags(&plan->fork, cudaEventDisableTiming));
+        CUDA_TRY(cudaEventCreateWithFlags(&plan->join, cudaEventDisableTiming));
+    }
+    plan->n_long = nl;
+    plan->lp_long = plan->lp;
+    plan->lp_long.kernel = RT_KERNEL_PLAIN;
+    plan->lp_long.lanes = 4;
+    plan->lp_long.blocks = 0;
+    if (n_long) *n_long = nl;
     return RT_OK;
 }
 
 rt_err rt_plan_destroy(rt_plan *plan) {
     if (!plan) return RT_OK;
-    const cudaError_t e = cudaFree(plan->ws);
+    cudaError_t e = cudaFree(plan->ws);
+    if (plan->perm) cudaFree(plan->perm);
+    if (plan->side) cudaStreamDestroy(plan->side);
+    if (plan->fork) cudaEventDestroy(plan->fork);
+    if (plan->join) cudaEventDestroy(plan->join);
     delete plan;
     if (e != cudaSuccess) return cuda_fail(e, "rt_plan_destroy");
     return RT_OK;
@@ -878,7 +1025,7 @@ rt_err rt_ionogram(const rt_grid *grid, const rt_ionogram_desc *d, rt_ionogram_p
 namespace {
 // Host staging of rt_trace_device_noalloc's fan image (fixed size, no allocation).
 std::mutex g_noalloc_img_mu;
-char g_noalloc_img[16 + kNoallocMaxTable * sizeof(double)];
+char g_noalloc_img[kNoallocScratchBytes];
 }  // namespace
 
 extern "C" {
@@ -905,7 +1052,7 @@ rt_err rt_trace_device_noalloc(const rt_grid *grid, const rt_fan_desc *fan, rt_r
     void *scratch = nullptr;
     size_t cap = 0;
     CUDA_TRY(noalloc_scratch(dev, &scratch, &cap));
-    if (16 + n_tab * sizeof(double) > cap) return fail(RT_EINVAL, "fan tables exceed the fixed scratch");
+    if (fan_image_bytes(fan) > cap) return fail(RT_EINVAL, "fan tables exceed the fixed scratch");
     cudaStream_t st = (cudaStream_t)stream;
     unsigned long long *counter = (unsigned long long *)scratch;
     double *tab = (double *)((char *)scratch + 16);
@@ -915,7 +1062,7 @@ rt_err rt_trace_device_noalloc(const rt_grid *grid, const rt_fan_desc *fan, rt_r
     // lock keeps to one call at a time until cudaMemcpyAsync has read it.
     {
         std::lock_guard<std::mutex> lk(g_noalloc_img_mu);
-        fan_image_into(fan, g_noalloc_img);
+        fan_image_into(grid, fan, g_noalloc_img);
         CUDA_TRY(cudaMemcpyAsync(scratch, g_noalloc_img, fan_image_bytes(fan), cudaMemcpyHostToDevice, st));
     }
     const FanDev f = fill_fandev(grid, fan, n, order, tab);

@@ -12,11 +12,34 @@ struct GridSizes {
     int n_lat, n_lon, n_alt;
 };
 
+// Per-fan tables the host prepares (fan_tables_into): per frequency the
+// frequency and the float factors of the mixed path, per elevation and
+// azimuth the sines and cosines of the launch direction -- computed once per
+// fan instead of once per ray (a double division or sincos costs a warp many
+// cycles of GB300's 1/64-rate FP64 pipe, and a persistent kernel's refills run
+// it for one lane at a time).
+struct FanFreq {
+    double f_hz;      // frequency (Hz)
+    float xfac;       // 80.6 / f^2 (X = xfac Ne), rounded from double
+    float ab0;        // f_H / f per tesla times the dipole's B0, rounded from double
+};
+struct FanEl {
+    double s, c;      // sin, cos of the elevation
+};
+struct FanAz {
+    double s, c;      // sin, cos of the azimuth
+    double rad;       // azimuth (rad)
+};
+// Doubles a fan's tables take: 2 per frequency, 2 per elevation, 3 per azimuth.
+inline size_t fan_table_doubles(int n_freq, int n_el, int n_az) {
+    return 2 * (size_t)n_freq + 2 * (size_t)n_el + 3 * (size_t)n_az;
+}
+
 // Device view of a fan (arrays in device memory) plus the integrator settings.
 struct FanDev {
-    const double *freq;  // MHz
-    const double *el;    // degrees
-    const double *az;    // degrees
+    const FanFreq *freq;
+    const FanEl *el;
+    const FanAz *az;
     int n_freq, n_el, n_az, n_modes;
     int mode0, mode1;    // mode sign of mode index 0 / 1 (+1 ordinary, -1 extraordinary)
     int integrator, precision, max_steps, order;
@@ -26,6 +49,10 @@ struct FanDev {
     double land_tol;            // |r - R_E| accepted by the landing solve (km)
     float rtol_f, atol_f, h0_f, hmin_f, hmax_f;
     int has_max_path;           // max_path > 0
+    // Optional claim order (an ordered plan): claim c of this launch traces
+    // canonical ray perm[perm_off + c]; n_rays then counts this launch's rays.
+    const int *perm;
+    long long perm_off;
 };
 
 struct LaunchPlan {
@@ -71,9 +98,11 @@ cudaError_t launch_ionogram(const rt_ray_result *res, const double *freq, const 
                             int mode0, int n_el, double d_rx, rt_ionogram_point *out, unsigned long long cap,
                             unsigned long long *count, cudaStream_t st);
 
-// Scratch of rt_trace_device_noalloc (rtgd_noalloc.cu): ray counter + at
-// most kNoallocMaxTable fan-table entries.
+// Scratch of rt_trace_device_noalloc (rtgd_noalloc.cu): ray counter + the
+// tables of a fan with n_freq + n_el + n_az <= kNoallocMaxTable (at most 3
+// doubles per entry).
 constexpr int kNoallocMaxTable = 4096;
+constexpr size_t kNoallocScratchBytes = 16 + 3 * (size_t)kNoallocMaxTable * sizeof(double);
 cudaError_t noalloc_scratch(int device, void **ptr, size_t *bytes);
 
 cudaError_t launch_eval_rhs(const GridDev &g, const double *ys, double *dys, double *mu2s, double freq_mhz, int mode,

@@ -137,9 +137,12 @@ cudaError_t launch_grid_prep(const void *raw, int dtype, const GridSizes &sz, do
 
 // ====================================================================== fan
 // Canonical ray index -> (frequency, mode, elevation, azimuth) of the fan,
-// order [freq][mode][el][az].
+// order [freq][mode][el][az], with the per-fan table entries of each.
 struct RayParams {
-    double f_hz, el, az;  // el, az in radians
+    double f_hz;
+    float xfac, ab0;        // the mixed path's per-frequency factors
+    double se, ce, sa, ca;  // sin, cos of elevation and azimuth
+    double az;              // azimuth (rad)
     int mode;
 };
 
@@ -154,9 +157,14 @@ __device__ __forceinline__ RayParams ray_params(const FanDev &f, long long id64)
     const unsigned m = rest2 % (unsigned)f.n_modes;
     const unsigned q = rest2 / (unsigned)f.n_modes;
     RayParams p;
-    p.f_hz = f.freq[q] * 1e6;
-    p.el = f.el[e] * kDeg2Rad;
-    p.az = f.az[a] * kDeg2Rad;
+    p.f_hz = f.freq[q].f_hz;
+    p.xfac = f.freq[q].xfac;
+    p.ab0 = f.freq[q].ab0;
+    p.se = f.el[e].s;
+    p.ce = f.el[e].c;
+    p.sa = f.az[a].s;
+    p.ca = f.az[a].c;
+    p.az = f.az[a].rad;
     p.mode = (m == 0) ? f.mode0 : f.mode1;
     return p;
 }
@@ -165,6 +173,7 @@ __device__ __forceinline__ RayParams ray_params(const FanDev &f, long long id64)
 // neighbouring elevations of one azimuth together (similar paths, so the
 // lanes of a warp gather from nearby cells).
 __device__ __forceinline__ long long claim_to_ray(const FanDev &f, long long c64) {
+    if (f.perm) return f.perm[f.perm_off + c64];
     if (f.order != RT_ORDER_ELEVATION_FASTEST) return c64;
     const unsigned c = (unsigned)c64;
     const unsigned e = c % (unsigned)f.n_el;
@@ -360,26 +369,15 @@ __device__ __forceinline__ double step_factor(R err) {
 }
 
 // Launch direction (elevation above the horizontal, azimuth clockwise from
-// north; the theta unit vector points south) and position of a ray.
-// The direction is computed out of line (once per ray).
-__device__ __noinline__ void launch_k(double el, double az, double *k) {
-    double se, ce, sa, ca;
-    sincos(el, &se, &ce);
-    sincos(az, &sa, &ca);
-    k[0] = se;
-    k[1] = -ce * ca;
-    k[2] = ce * sa;
-}
-
+// north; the theta unit vector points south) and position of a ray, from the
+// fan's sine and cosine tables.
 __device__ __forceinline__ void launch_dir(const FanDev &f, const RayParams &p, double y[6]) {
     y[0] = f.tx_r;
     y[1] = f.tx_th;
     y[2] = f.tx_ph;
-    double k[3];
-    launch_k(p.el, p.az, k);
-    y[3] = k[0];
-    y[4] = k[1];
-    y[5] = k[2];
+    y[3] = p.se;
+    y[4] = -p.ce * p.ca;
+    y[5] = p.ce * p.sa;
 }
 
 // Group path to the next cell face the ray reaches, predicted linearly from
@@ -546,9 +544,10 @@ __device__ void trace_ray_fp64(const GridDev &g, const FanDev &f, long long id, 
 __global__ void __launch_bounds__(128) trace_fp64_kernel(GridDev g, FanDev f, rt_ray_result *__restrict__ out) {
     const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (id >= f.n_rays) return;
+    const long long ray = claim_to_ray(f, id);
     rt_ray_result r;
-    trace_ray_fp64(g, f, id, &r);
-    out[id] = r;
+    trace_ray_fp64(g, f, ray, &r);
+    out[ray] = r;
 }
 
 // =============================================================== mixed path
@@ -877,8 +876,6 @@ struct Lane {
                                  // as compensated float pairs (see lane_fold)
     float k_hi[3], k_lo[3];   // wave vector as a compensated float pair
     float r_prev;             // radius at the start of the last accepted step
-    double la, lfa, lb, lfb;  // crossing bracket (step size, signed r - target)
-    double r_target;          // R_E (ground) or R_E + top (exit through the grid top)
     float h, hs;              // next step / step of the current attempt (km)
     float h_prev, dr_prev;    // last accepted step and its dr/dP' at the start
     float apo;                // reflection height so far (km)
@@ -888,8 +885,19 @@ struct Lane {
     float xfac, ab0;
     Base32 b;
     int out_id, mode;
-    int n_steps, n_att, n_ev, status, side, land_it, since_sync;
+    int n_steps, n_att, n_ev, status, since_sync;
     bool active, launch, landing, exiting, have_prev, k1_valid, at_face;
+};
+
+// State of the landing / exit solve of one lane (Illinois regula falsi on the
+// step size: bracket [la, lb] with signed distances lfa, lfb from the target
+// radius).  Used only on a ray's last step: the persistent kernel keeps it in
+// a per-thread shared-memory slot (its refill code leaves fewer registers for
+// the ray state; measured 8 % faster on the 495k-ray batch), the plain
+// kernels in registers.
+struct LandState {
+    double la, lfa, lb, lfb;
+    int side, it;
 };
 
 __device__ __forceinline__ RayPhys<float> lane_phys(const GridDev &g, const Lane &L) {
@@ -936,11 +944,21 @@ __device__ __forceinline__ void accumulate_next(Lane &L, const Tableau &T, int s
     }
 }
 
-__device__ void lane_begin_ray(Lane &L, const GridDev &g, const FanDev &f, long long id) {
+// Base of the transmitter position (the launch state of every ray of the
+// fan; the wave vector part is set per ray).
+__device__ __forceinline__ Base32 tx_base(const GridDev &g, const FanDev &f) {
+    return base_of(g.lat0, g.lon0, g.inv_dlat, g.inv_dlon, g.R_E, g.alt0, g.inv_dalt, f.tx_r, f.tx_th, f.tx_ph, 0.0,
+                   0.0, 0.0);
+}
+
+// Starts ray `id`: per-ray constants from the fan's tables, FP64 launch
+// state, and the float base: the transmitter's (btx, shared by the fan) with
+// this ray's wave vector.
+__device__ void lane_begin_ray(Lane &L, const GridDev &g, const FanDev &f, long long id, const Base32 &btx) {
     const RayParams p = ray_params(f, id);
     L.out_id = (int)id;
-    L.xfac = (float)(kPlasmaHz2PerM3 / (p.f_hz * p.f_hz));
-    L.ab0 = (float)(kGyroHzPerTesla / p.f_hz * g.b0);
+    L.xfac = p.xfac;
+    L.ab0 = p.ab0;
     L.mode = p.mode;
     double y[6];
     launch_dir(f, p, y);
@@ -960,7 +978,9 @@ __device__ void lane_begin_ray(Lane &L, const GridDev &g, const FanDev &f, long 
     L.status = RT_RAY_NOT_RUN;
     L.have_prev = L.k1_valid = L.landing = L.exiting = false;
     L.launch = true;
-    base_from_state(g, y, L.b);
+    L.b = btx;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) L.b.k[i] = (float)y[3 + i];
 }
 
 // Adds the pending increments to the FP64 position and group path.  An
@@ -997,7 +1017,7 @@ __device__ __forceinline__ void lane_finish(Lane &L, const GridDev &g, const Fan
     L.active = false;
     if (!writer) return;
     lane_fold(L);
-    const double az = f.az[L.out_id % f.n_az] * kDeg2Rad;
+    const double az = f.az[L.out_id % f.n_az].rad;
     finish_result(f.tx_th, f.tx_ph, az, L.y[1], L.y[2], L.P, (double)L.apo, L.status, L.n_steps, L.n_att, L.n_ev,
                   g.R_E, out + L.out_id);
 }
@@ -1161,7 +1181,7 @@ __device__ __noinline__ double bracket_first(double lb, double lfa, double lfb) 
 
 // Bookkeeping after an attempt: landing/exit solve, accept or reject, state
 // update in double.  Returns true when the ray has finished (status set).
-__device__ bool lane_end_attempt(Lane &L, const GridDev &g, const FanDev &f) {
+__device__ bool lane_end_attempt(Lane &L, const GridDev &g, const FanDev &f, LandState &ls) {
     const double RE = g.R_E;
     const float hf = L.hs;
     ++L.n_att;
@@ -1176,18 +1196,19 @@ __device__ bool lane_end_attempt(Lane &L, const GridDev &g, const FanDev &f) {
     if (L.landing) {
         // Illinois regula falsi on the step size: f(h*) = +-(r(step(h*)) - target)
         const double sg = L.exiting ? -1.0 : 1.0;
-        const double fc = sg * ((L.y[0] - L.r_target) + (double)dy4[0]);
-        ++L.land_it;
+        const double r_target = L.exiting ? RE + g.top : RE;
+        const double fc = sg * ((L.y[0] - r_target) + (double)dy4[0]);
+        ++ls.it;
         const double c = (double)L.hs;
-        const bool done = fabs(fc) < f.land_tol || L.land_it >= 60 || fabs(L.lb - L.la) < 1e-9 || !fin;
+        const bool done = fabs(fc) < f.land_tol || ls.it >= 60 || fabs(ls.lb - ls.la) < 1e-9 || !fin;
         if (!done) {
-            Bracket B{L.la, L.lfa, L.lb, L.lfb, L.side};
+            Bracket B{ls.la, ls.lfa, ls.lb, ls.lfb, ls.side};
             L.hs = (float)bracket_update(B, c, fc);
-            L.la = B.la;
-            L.lfa = B.lfa;
-            L.lb = B.lb;
-            L.lfb = B.lfb;
-            L.side = B.side;
+            ls.la = B.la;
+            ls.lfa = B.lfa;
+            ls.lb = B.lb;
+            ls.lfb = B.lfb;
+            ls.side = B.side;
             return !lane_next_attempt(L, f);
         }
         if (!fin) {
@@ -1233,15 +1254,15 @@ __device__ bool lane_end_attempt(Lane &L, const GridDev &g, const FanDev &f) {
         const double r_new = L.y[0] + (double)dy4[0];
         L.landing = true;
         L.exiting = !lands;
-        L.r_target = lands ? RE : RE + g.top;
+        const double r_target = lands ? RE : RE + g.top;
         const double sg = lands ? 1.0 : -1.0;
-        L.la = 0.0;
-        L.lfa = sg * (L.y[0] - L.r_target);
-        L.lb = (double)L.hs;
-        L.lfb = sg * (r_new - L.r_target);
-        L.side = 0;
-        L.land_it = 0;
-        L.hs = (float)bracket_first(L.lb, L.lfa, L.lfb);
+        ls.la = 0.0;
+        ls.lfa = sg * (L.y[0] - r_target);
+        ls.lb = (double)L.hs;
+        ls.lfb = sg * (r_new - r_target);
+        ls.side = 0;
+        ls.it = 0;
+        L.hs = (float)bracket_first(ls.lb, ls.lfa, ls.lfb);
         return !lane_next_attempt(L, f);
     }
     L.r_prev = L.b.r;
@@ -1286,12 +1307,17 @@ __device__ bool lane_end_attempt(Lane &L, const GridDev &g, const FanDev &f) {
 }
 
 // Loads the Butcher table of the fan's integrator into shared memory; the
-// stage loop reads it at a warp-uniform stage index (broadcast reads).
-__device__ __forceinline__ void load_tableau(Tableau &T, int integrator) {
+// stage loop reads it at a warp-uniform stage index (broadcast reads).  With
+// btx, also the transmitter's base of fan f (computed once per block: it is
+// double arithmetic, and the persistent kernel would otherwise redo it for
+// every lane it refills).
+__device__ __forceinline__ void load_tableau(Tableau &T, int integrator, Base32 *btx = nullptr,
+                                             const GridDev *g = nullptr, const FanDev *f = nullptr) {
     const Tableau &src = c_tab[integrator == RT_RKF45 ? 1 : 0];
     const float *s = (const float *)&src;
     float *d = (float *)&T;
     for (int i = threadIdx.x; i < (int)(sizeof(Tableau) / sizeof(float)); i += blockDim.x) d[i] = s[i];
+    if (btx && threadIdx.x == 0) *btx = tx_base(*g, *f);
     __syncthreads();
 }
 
@@ -1310,7 +1336,8 @@ __device__ __forceinline__ unsigned group_mask(int lane) {
 template <int STENCIL, int G, int IP>
 __global__ void __launch_bounds__(128, G == 1 ? 3 : 2) trace_mixed_plain_kernel(GridDev g, FanDev f, rt_ray_result *__restrict__ out) {
     __shared__ Tableau T;
-    load_tableau(T, f.integrator);
+    __shared__ Base32 btx;
+    load_tableau(T, f.integrator, &btx, &g, &f);
     const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long id = tid / G;
     if (id >= f.n_rays) return;  // whole groups leave together
@@ -1318,13 +1345,17 @@ __global__ void __launch_bounds__(128, G == 1 ? 3 : 2) trace_mixed_plain_kernel(
     const unsigned gmask = group_mask<G>(lane);
     Lane L;
     L.active = true;
-    lane_begin_ray(L, g, f, claim_to_ray(f, id));
+    lane_begin_ray(L, g, f, claim_to_ray(f, id), btx);
     bool done = lane_launch<STENCIL, G, IP>(L, g, f, q, gmask);
+    // the landing state stays in registers here (a shared-memory slot per
+    // thread would take L1 that the sample gathers use; measured 3 % slower on
+    // the 495k-ray batch), unlike in the persistent kernel
+    LandState land;
     // bounded: every attempt counts against max_steps, so max_steps + 1 attempts end every ray
     const long long max_att = (long long)f.max_steps + 2;
     for (long long it = 0; it < max_att && !done; ++it) {
         lane_attempt<STENCIL, G, IP>(L, g, f, T, q, gmask);
-        done = lane_end_attempt(L, g, f);
+        done = lane_end_attempt(L, g, f, land);
     }
     if (!done) L.status = RT_RAY_MAX_STEPS;
     lane_finish(L, g, f, out, q == 0);
@@ -1338,7 +1369,9 @@ __global__ void __launch_bounds__(128, G == 1 ? 3 : 2) trace_mixed_persistent_ke
                                                                      rt_ray_result *__restrict__ out,
                                                                      unsigned long long *__restrict__ counter) {
     __shared__ Tableau T;
-    load_tableau(T, f.integrator);
+    __shared__ Base32 btx;
+    __shared__ LandState land[128];
+    load_tableau(T, f.integrator, &btx, &g, &f);
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, q = lane % G;
     const unsigned gmask = group_mask<G>(lane);
@@ -1364,7 +1397,7 @@ __global__ void __launch_bounds__(128, G == 1 ? 3 : 2) trace_mixed_persistent_ke
                 const unsigned long long c = base + __popc(idle & ((1u << lane) - 1u)) / G;
                 if (c < (unsigned long long)n) {
                     L.active = true;
-                    lane_begin_ray(L, g, f, claim_to_ray(f, (long long)c));
+                    lane_begin_ray(L, g, f, claim_to_ray(f, (long long)c), btx);
                     if (lane_launch<STENCIL, G, IP>(L, g, f, q, gmask)) lane_finish(L, g, f, out, q == 0);
                 }
             }
@@ -1379,7 +1412,7 @@ __global__ void __launch_bounds__(128, G == 1 ? 3 : 2) trace_mixed_persistent_ke
         }
         if (L.active) {
             lane_attempt<STENCIL, G, IP>(L, g, f, T, q, gmask);
-            if (lane_end_attempt(L, g, f)) lane_finish(L, g, f, out, q == 0);
+            if (lane_end_attempt(L, g, f, land[threadIdx.x])) lane_finish(L, g, f, out, q == 0);
         }
     }
 }
@@ -1412,12 +1445,13 @@ __global__ void __launch_bounds__(128, 2) trace_mixed_fans_kernel(GridDev g, con
     const unsigned gmask = group_mask<G>(lane);
     Lane L;
     L.active = true;
-    lane_begin_ray(L, g, f, claim_to_ray(f, i - first[lo]));
+    lane_begin_ray(L, g, f, claim_to_ray(f, i - first[lo]), tx_base(g, f));
     bool done = lane_launch<STENCIL, G, IP>(L, g, f, q, gmask);
+    LandState land;
     const long long max_att = (long long)f.max_steps + 2;
     for (long long it = 0; it < max_att && !done; ++it) {
         lane_attempt<STENCIL, G, IP>(L, g, f, T, q, gmask);
-        done = lane_end_attempt(L, g, f);
+        done = lane_end_attempt(L, g, f, land);
     }
     if (!done) L.status = RT_RAY_MAX_STEPS;
     lane_finish(L, g, f, out + first[lo], q == 0);

@@ -17,9 +17,9 @@
 
 namespace rtgd {
 
-// 16 bytes of ray counter followed by at most kNoallocMaxTable doubles
-// (frequencies, elevations, azimuths of the fan).
-static __device__ __align__(256) unsigned char g_noalloc_scratch[16 + kNoallocMaxTable * sizeof(double)];
+// 16 bytes of ray counter followed by the fan's tables: at most
+// 3 x kNoallocMaxTable doubles (about 96 KiB).
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
 static std::mutex g_noalloc_mu;
 static std::map<int, void *> g_noalloc_ptr;
