@@ -128,10 +128,12 @@ def parse_args():
                    help="persistent kernel with --kernel: resident blocks per SM (0 = occupancy limit)")
     p.add_argument("--lanes", type=int, default=0, choices=[0, 1, 2, 4],
                    help="lanes per ray with --kernel (0 = the library's choice)")
-    p.add_argument("--workload", choices=["c2", "c4", "c5"], default="c2",
+    p.add_argument("--workload", choices=["c2", "c4", "c4sub", "c5"], default="c2",
                    help="fan for the --profile and --one-ray modes: c2 = the anisotropic 24,840-ray fan "
                         "(the benchmark's workload), c4 = the 495,122-ray ionogram-synthesis batch, "
-                        "c5 = small serving requests fused into one launch (--profile only)")
+                        "c4sub = every eighth frequency of that batch (63,432 rays, for captures that "
+                        "replay the kernel many times), c5 = small serving requests fused into one launch "
+                        "(--profile only)")
     p.add_argument("--one-ray", type=int, default=None,
                    help="latency mode: trace only this canonical ray of the fan (alone) --steps times "
                         "and print its time per stage evaluation")
@@ -392,10 +394,12 @@ def run_ours(args):
             raise SystemExit("--workload c5 is for the --profile mode (the serving section times it)")
         profile_fused(rt, wl, args.serve_fuse, max(args.warmup, 1) + 1)
         return
-    if args.workload == "c4" and not (args.profile or args.one_ray is not None):
+    if args.workload in ("c4", "c4sub") and not (args.profile or args.one_ray is not None):
         raise SystemExit("--workload c4 is for the --profile and --one-ray modes (the batch section times it)")
     w = wl.config2() if args.workload == "c2" else wl.config4()
     spec = w.fan.replace(rtol=args.rtol) if args.workload == "c2" else w.fan
+    if args.workload == "c4sub":
+        spec = spec.replace(freq_mhz=spec.freq_mhz[::8])
     prec = rt.RT_MIXED if args.precision == "mixed" else rt.RT_FP64
     grid = rt.Grid(w.grid, w.ne, table=(prec == rt.RT_MIXED and
                                         (args.kernel is None or args.stencil == "table")))
@@ -749,6 +753,7 @@ def run_batch(rt, wl, torch, flush, steps=3):
         torch.cuda.synchronize()
         ms.append(a.elapsed_time(b))
     res = rt.results_view(out.cpu().numpy(), n)
+    out_first = out.clone()
     st = np.bincount(res["status"], minlength=8)
     sec = float(np.mean(ms)) / 1e3
     out_d = {"workload": w.name, "rays": n, "rtol": w.fan.rtol, "ms_per_batch": sec * 1e3, "rays_per_s": n / sec,
@@ -815,6 +820,56 @@ def run_batch(rt, wl, torch, flush, steps=3):
                                             "lanes_per_ray": cfg_p.lanes_per_ray}}
     del pgraph
     pplan.close()
+    # longest-first (rt_plan_order): the costs come from the same scan traced
+    # on a later snapshot of the ionosphere (the TID advanced by 5 % of its
+    # period, about a minute for a 200 km TID at 150 m/s), as a scan repeated on
+    # successive snapshots has them, or from the plan's own previous execution
+    # (the same ionosphere); the most expensive rays (six times the median
+    # cost) run at four lanes each on a second stream, all in descending cost
+    w5 = wl.config4(tid_phase_shift=0.05)
+    g5 = rt.Grid(w5.grid, w5.ne)
+    prev = torch.empty(n * 64, dtype=torch.uint8, device="cuda")
+    rt.rt_trace_device(g5, rt.Fan(w5.fan, rt.RT_MIXED), prev.data_ptr(), n,
+                       cfg=rt.launch_config(kernel=rt.RT_KERNEL_PLAIN, stencil=rt.RT_STENCIL_QUAD, lanes_per_ray=1),
+                       stream=side.cuda_stream)
+    own = torch.empty(n * 64, dtype=torch.uint8, device="cuda")
+    own.copy_(out_first)
+    torch.cuda.synchronize()
+    g5.close()
+    out_d["ordered"] = {"spread": 2, "long_factor": 6.0,
+                        "cost_sources": {"later_snapshot": "the same scan on the ionosphere with the TID advanced by "
+                                                           "5 % of its period",
+                                         "own_previous": "the plan's previous execution (same ionosphere)"}}
+    ordered_sample = {}
+    for name, c, src in (("plain", cfg, prev), ("persistent", cfg_p, prev), ("plain_own_previous", cfg, own)):
+        oplan = rt.Plan(grid, fan, cfg=c)
+        n_long = oplan.order(src.data_ptr(), spread=2, long_factor=6.0, stream=side.cuda_stream)
+        ograph = torch.cuda.CUDAGraph()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(ograph, stream=side):
+                oplan.execute(out.data_ptr(), n, stream=side.cuda_stream)
+        torch.cuda.synchronize()
+        ograph.replay()
+        t_o = []
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(cur)
+            ograph.replay()
+            b.record(cur)
+            torch.cuda.synchronize()
+            t_o.append(a.elapsed_time(b))
+        res_o = rt.results_view(out.cpu().numpy(), n)
+        ordered_sample[name] = res_o[wl.sample_indices(n, 5000, 1234)].copy()  # the oracle leg's sample
+        out_d["ordered"][name] = {"ms_per_batch": float(np.mean(t_o)), "rays_per_s": n / (float(np.mean(t_o)) / 1e3),
+                                  "four_lane_rays": int(n_long),
+                                  "stage_evals_per_s": float(res_o["n_evals"].sum()) / (float(np.mean(t_o)) / 1e3),
+                                  "launch": {"kernel": c.kernel, "stencil": c.stencil, "block_threads": c.block_threads,
+                                             "lanes_per_ray": c.lanes_per_ray}}
+        del ograph
+        oplan.close()
+    del prev, own
     # cost of the interpolant (Sec. IV: GD against Catmull-Rom): the same batch,
     # the same launch configuration, on a Catmull-Rom copy of the grid; time
     # per stage evaluation (the two fields differ slightly, so do the paths)
@@ -844,6 +899,8 @@ def run_batch(rt, wl, torch, flush, steps=3):
     out_d["cpu_baseline"] = info
     out_d["boundaries"] = gate_info
     out_d["vs_cpu_oracle"] = gate_errors(res, o_res, well, idx)
+    for name, rec in ordered_sample.items():
+        out_d["ordered"][name]["vs_cpu_oracle"] = gate_errors(rec, o_res, well)
     del graph
     plan.close()
     grid.close()

@@ -27,10 +27,11 @@ RT_FP64, RT_MIXED = 0, 1
 RT_KERNEL_AUTO, RT_KERNEL_PLAIN, RT_KERNEL_PERSISTENT = 0, 1, 2
 RT_STENCIL_AUTO, RT_STENCIL_GATHER, RT_STENCIL_QUAD, RT_STENCIL_TABLE = 0, 1, 2, 3
 RT_ORDER_CANONICAL, RT_ORDER_ELEVATION_FASTEST = 0, 1
+RT_PLAN_REST_IN_PLAN_ORDER = 1
 
 EXPORTED = ["rt_grid_create", "rt_grid_destroy", "rt_grid_device_bytes", "rt_fan_size",
             "rt_trace", "rt_trace_device", "rt_trace_fans_device", "rt_tune", "rt_eval_rhs", "rt_last_error",
-            "rt_version", "rt_plan_create", "rt_plan_rays", "rt_plan_execute", "rt_plan_destroy",
+            "rt_version", "rt_plan_create", "rt_plan_rays", "rt_plan_execute", "rt_plan_destroy", "rt_plan_order",
             "rt_ionogram", "rt_trace_device_noalloc", "rt_server_create", "rt_server_submit",
             "rt_server_wait", "rt_server_destroy", "rt_measure_peaks"]
 
@@ -165,6 +166,8 @@ def load(path=None):
     L.rt_plan_execute.restype = ctypes.c_int
     L.rt_plan_destroy.argtypes = [vp]
     L.rt_plan_destroy.restype = ctypes.c_int
+    L.rt_plan_order.argtypes = [vp, vp, ctypes.c_int32, ctypes.c_double, ctypes.c_uint32, ctypes.POINTER(sz), vp]
+    L.rt_plan_order.restype = ctypes.c_int
     L.rt_ionogram.argtypes = [vp, ctypes.POINTER(rt_ionogram_desc), vp, sz, ctypes.POINTER(sz),
                               ctypes.POINTER(rt_launch_config), vp]
     L.rt_ionogram.restype = ctypes.c_int
@@ -324,6 +327,16 @@ class Plan:
 
     def execute(self, out_ptr, out_len, stream=None):
         _check(load().rt_plan_execute(self.handle, ctypes.c_void_p(out_ptr), out_len, stream))
+
+    def order(self, cost_ptr, spread=2, long_factor=0.0, rest_in_plan_order=False, stream=None):
+        """rt_plan_order: longest-first order from device records at cost_ptr
+        (None: back to the plan's own order); returns the number of rays
+        traced at four lanes each."""
+        n_long = ctypes.c_size_t()
+        _check(load().rt_plan_order(self.handle, None if cost_ptr is None else ctypes.c_void_p(cost_ptr),
+                                    int(spread), float(long_factor), RT_PLAN_REST_IN_PLAN_ORDER if rest_in_plan_order else 0,
+                                    ctypes.byref(n_long), stream))
+        return n_long.value
 
     def close(self):
         if self.handle:

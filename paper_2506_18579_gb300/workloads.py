@@ -150,12 +150,13 @@ def _great_circle_km(lat1, lon1, lat2, lon2, re=EARTH_RADIUS_KM):
 
 
 def tid_factor(lat, lon, rng, amp=0.05, wavelength_km=200.0, sigma_km=600.0,
-               centre=(30.0, 112.0), spread_deg=5.0):
-    """Multiplicative TID perturbation on a (lat, lon) mesh (degrees)."""
+               centre=(30.0, 112.0), spread_deg=5.0, phase_shift=0.0):
+    """Multiplicative TID perturbation on a (lat, lon) mesh (degrees).
+    phase_shift (cycles) advances the wave: the same disturbance a little later."""
     lat_c = centre[0] + rng.uniform(-spread_deg, spread_deg)
     lon_c = centre[1] + rng.uniform(-spread_deg, spread_deg)
     direction = rng.uniform(0.0, 2.0 * np.pi)
-    phase = rng.uniform(0.0, 2.0 * np.pi)
+    phase = rng.uniform(0.0, 2.0 * np.pi) + 2.0 * np.pi * phase_shift
     rho = _great_circle_km(lat_c, lon_c, lat, lon)
     dn = np.radians(lat - lat_c) * EARTH_RADIUS_KM
     de = np.radians(lon - lon_c) * EARTH_RADIUS_KM * np.cos(np.radians(lat_c))
@@ -179,12 +180,12 @@ def dipole_field(tx_lon, b0=3.1e-5, tilt_deg=11.0):
 
 
 def two_layer_ne(grid: GridSpec, rng, foe=3.0, hme=110.0, he=10.0, fof2_lo=6.0, fof2_hi=10.0,
-                 hmf2=300.0, hf2=50.0, tid_amp=0.05, daynight=0.0, centre=(30.0, 112.0)):
+                 hmf2=300.0, hf2=50.0, tid_amp=0.05, daynight=0.0, centre=(30.0, 112.0), tid_phase_shift=0.0):
     lat, lon, alt = grid.axes()
     LAT, LON, ALT = np.meshgrid(lat, lon, alt, indexing="ij")
     fof2 = fof2_lo + (fof2_hi - fof2_lo) * (LAT - lat[0]) / (lat[-1] - lat[0])
     ne = chapman(ALT, nm_from_fo(foe), hme, he) + chapman(ALT, nm_from_fo(fof2), hmf2, hf2)
-    tid, info = tid_factor(LAT[:, :, 0], LON[:, :, 0], rng, amp=tid_amp, centre=centre)
+    tid, info = tid_factor(LAT[:, :, 0], LON[:, :, 0], rng, amp=tid_amp, centre=centre, phase_shift=tid_phase_shift)
     ne = ne * tid[:, :, None]
     if daynight:
         half = 0.5 * (lon[-1] - lon[0])
@@ -226,15 +227,16 @@ def config2(seed=2, dtype=np.float32, elev_step=0.5, az_step=10.0, freqs=(8.0, 1
                     g, ne.astype(dtype), fan, notes=dict(tid=info, seed=seed))
 
 
-def config4(seed=4, dtype=np.float32, rtol=1e-8) -> Workload:
+def config4(seed=4, dtype=np.float32, rtol=1e-8, tid_phase_shift=0.0) -> Workload:
     """Ionogram-synthesis batch: 181x361x301 grid (0.5 deg, 0.5 deg, 2 km),
     two-layer Chapman + TID + 20 % day/night gradient; 2-30 MHz step 0.1 x
     elevations 1-89 deg step 0.1 x O and X (495,122 rays); RKF45 at rtol
     1e-8, the anisotropic fan case's tolerance (the batch's accuracy is held
-    to the same bar)."""
+    to the same bar).  tid_phase_shift (cycles) gives a later snapshot of the
+    same ionosphere: the TID advanced along its direction of travel."""
     rng = np.random.default_rng(seed)
     g = centred_grid(TX[0], TX[1], 181, 361, 301, 0.5, 0.5, 2.0, **dipole_field(TX[1]))
-    ne, info = two_layer_ne(g, rng, daynight=0.2)
+    ne, info = two_layer_ne(g, rng, daynight=0.2, tid_phase_shift=tid_phase_shift)
     fan = FanSpec(*TX, freq_mhz=np.round(np.arange(2.0, 30.0 + 1e-9, 0.1), 10),
                   el_deg=np.round(np.arange(1.0, 89.0 + 1e-9, 0.1), 10), az_deg=[45.0],
                   modes=MODE_O | MODE_X, integrator=RKF45, h_km=1.0, rtol=rtol, atol_km=1e-6,
