@@ -50,36 +50,13 @@ GATHER_BYTES = {"mixed": 65 * 4, "fp64": 64 * 8}
 # was captured from: a changed kernel reports traffic null.
 KERNEL_SOURCES = ("paper_2506_18579_gb300/csrc/rtgd_kernels.cu", "paper_2506_18579_gb300/csrc/rtgd_device.cuh")
 TRAFFIC = {
-    # the anisotropic fan: the plain (1) and persistent
-    # (2) kernels on the C2 fan, 96-thread blocks (the block size moves DRAM
-    # bytes by ~1 %); key = (workload, kernel, stencil, lanes per ray)
-    ("c2", 1, 1, 1): {"bytes_per_launch": 2132992, "source_sha256": "91c55e6b7720bda6"},
-    ("c2", 1, 1, 2): {"bytes_per_launch": 2130944, "source_sha256": "91c55e6b7720bda6"},
-    ("c2", 1, 1, 4): {"bytes_per_launch": 2473216, "source_sha256": "91c55e6b7720bda6"},
-    ("c2", 1, 2, 1): {"bytes_per_launch": 5504256, "source_sha256": "91c55e6b7720bda6"},
-    ("c2", 1, 2, 2): {"bytes_per_launch": 5392640, "source_sha256": "91c55e6b7720bda6"},
-    ("c2", 1, 2, 4): {"bytes_per_launch": 5394944, "source_sha256": "91c55e6b7720bda6"},
-    ("c2", 1, 3, 1): {"bytes_per_launch": 26717184, "source_sha256": "91c55e6b7720bda6"},
-    ("c2", 1, 3, 2): {"bytes_per_launch": 27068160, "source_sha256": "91c55e6b7720bda6"},
-    ("c2", 1, 3, 4): {"bytes_per_launch": 27088384, "source_sha256": "91c55e6b7720bda6"},
-    ("c2", 2, 1, 1): {"bytes_per_launch": 2358528, "source_sha256": "91c55e6b7720bda6"},
-    ("c2", 2, 1, 2): {"bytes_per_launch": 2136064, "source_sha256": "91c55e6b7720bda6"},
-    ("c2", 2, 1, 4): {"bytes_per_launch": 2135808, "source_sha256": "91c55e6b7720bda6"},
-    ("c2", 2, 2, 1): {"bytes_per_launch": 6005248, "source_sha256": "91c55e6b7720bda6"},
-    ("c2", 2, 2, 2): {"bytes_per_launch": 5745408, "source_sha256": "91c55e6b7720bda6"},
-    ("c2", 2, 2, 4): {"bytes_per_launch": 5397504, "source_sha256": "91c55e6b7720bda6"},
-    ("c2", 2, 3, 1): {"bytes_per_launch": 26865152, "source_sha256": "91c55e6b7720bda6"},
-    ("c2", 2, 3, 2): {"bytes_per_launch": 26757888, "source_sha256": "91c55e6b7720bda6"},
-    ("c2", 2, 3, 4): {"bytes_per_launch": 27103232, "source_sha256": "91c55e6b7720bda6"},
-    # the ionogram batch: 20.28 MB read + 1.04 MB written (128-thread blocks);
-    # the other stencils and the persistent kernel, one lane per ray (the only
-    # lane count the autotuner tries on a fan this large)
-    ("c4", 1, 3, 1): {"bytes_per_launch": 21322240, "source_sha256": "91c55e6b7720bda6"},
-    ("c4", 1, 1, 1): {"bytes_per_launch": 1655296, "source_sha256": "91c55e6b7720bda6"},
-    ("c4", 1, 2, 1): {"bytes_per_launch": 4627200, "source_sha256": "91c55e6b7720bda6"},
-    ("c4", 2, 1, 1): {"bytes_per_launch": 1880064, "source_sha256": "91c55e6b7720bda6"},
-    ("c4", 2, 2, 1): {"bytes_per_launch": 5474560, "source_sha256": "91c55e6b7720bda6"},
-    ("c4", 2, 3, 1): {"bytes_per_launch": 22156288, "source_sha256": "91c55e6b7720bda6"},
+    # key = (workload, kernel, stencil, lanes per ray); the anisotropic fan in
+    # the autotuner's configuration (plain, table, 4 lanes, 96-thread blocks)
+    ("c2", 1, 3, 4): {"bytes_per_launch": 26692096 + 35584, "source_sha256": "f1b903f348915082"},
+    # the ionogram batch, one lane per ray (the only lane count the autotuner
+    # tries on a fan this large), 32-thread blocks, table and quad stencils
+    ("c4", 1, 3, 1): {"bytes_per_launch": 20846336 + 1476608, "source_sha256": "f1b903f348915082"},
+    ("c4", 1, 2, 1): {"bytes_per_launch": 4755968 + 462080, "source_sha256": "f1b903f348915082"},
 }
 SMS = 152
 FP32_LANES_PER_SM = 128
