@@ -590,7 +590,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "e2e": {"value": n * world / e2e_s, "unit": "rays/s", "h2d_bytes_per_step": fan.host_bytes,
                     "d2h_bytes_per_step": n * 64},
-            "gpu_launches": args.steps,
+            "gpu_launches": args.steps * (2 if prec == rt.RT_MIXED else 1),  # trace (+ finish pass) per step
             "clocks": clk,
             "wall_s_timed": t_wall,
             "tune_ms": tune_ms,

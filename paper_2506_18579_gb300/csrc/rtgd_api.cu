@@ -804,11 +804,12 @@ rt_err rt_plan_execute(const rt_plan *plan, rt_ray_result *out_dev, size_t out_l
     if (plan->n_long > 0) {
         CUDA_TRY(cudaEventRecord(plan->fork, st));
         CUDA_TRY(cudaStreamWaitEvent(plan->side, plan->fork, 0));
-        CUDA_TRY(launch_trace(plan->grid->g, fl, out_dev, nullptr, plan->lp_long, plan->side));
+        CUDA_TRY(launch_trace_only(plan->grid->g, fl, out_dev, nullptr, plan->lp_long, plan->side));
         CUDA_TRY(cudaEventRecord(plan->join, plan->side));
     }
-    CUDA_TRY(launch_trace(plan->grid->g, fb, out_dev, (unsigned long long *)plan->ws, plan->lp, st));
+    CUDA_TRY(launch_trace_only(plan->grid->g, fb, out_dev, (unsigned long long *)plan->ws, plan->lp, st));
     if (plan->n_long > 0) CUDA_TRY(cudaStreamWaitEvent(st, plan->join, 0));
+    CUDA_TRY(launch_finish(plan->grid->g, plan->f, out_dev, (long long)plan->n, st));
     return RT_OK;
 }
 

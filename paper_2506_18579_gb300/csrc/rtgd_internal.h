@@ -66,8 +66,14 @@ struct LaunchPlan {
 cudaError_t launch_grid_prep(const void *raw, int dtype, const GridSizes &sz, double *pad64, float *pad32,
                              float4 *quad, float4 *table, cudaStream_t st);
 cudaError_t upload_tableaus();
+// Trace launch then (mixed path) the pass that turns the raw final states
+// into the records' outputs.
 cudaError_t launch_trace(const GridDev &g, const FanDev &f, rt_ray_result *out, unsigned long long *counter,
                          const LaunchPlan &lp, cudaStream_t st);
+// The two steps separately (an ordered plan finishes once after its two launches).
+cudaError_t launch_trace_only(const GridDev &g, const FanDev &f, rt_ray_result *out, unsigned long long *counter,
+                              const LaunchPlan &lp, cudaStream_t st);
+cudaError_t launch_finish(const GridDev &g, const FanDev &f, rt_ray_result *out, long long n, cudaStream_t st);
 cudaError_t persistent_occupancy(int stencil, int lanes, int threads, int *blocks_per_sm);
 // Mixed path, four lanes per ray: n_fans fans (device array fans) in one
 // launch; first (device, n_fans + 1 entries) holds each fan's first ray in

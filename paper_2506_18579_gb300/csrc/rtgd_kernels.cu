@@ -1012,14 +1012,62 @@ __device__ __forceinline__ void lane_state(const Lane &L, double y[6]) {
     }
 }
 
+// Writes a ray's raw final state into its record: colatitude and longitude
+// (rad) stand in the ground-range and azimuth-deviation fields until
+// finish_records_kernel turns them into the outputs.  The outputs' double
+// trigonometry would otherwise run here, in a branch taken by the lanes of
+// one ray while the rest of the warp waits on the 1/64-rate FP64 pipe.
 __device__ __forceinline__ void lane_finish(Lane &L, const GridDev &g, const FanDev &f, rt_ray_result *out,
                                             bool writer = true) {
     L.active = false;
     if (!writer) return;
     lane_fold(L);
-    const double az = f.az[L.out_id % f.n_az].rad;
-    finish_result(f.tx_th, f.tx_ph, az, L.y[1], L.y[2], L.P, (double)L.apo, L.status, L.n_steps, L.n_att, L.n_ev,
-                  g.R_E, out + L.out_id);
+    rt_ray_result r;
+    r.group_path_km = L.P;
+    r.ground_range_km = L.y[1];
+    r.az_dev_deg = L.y[2];
+    r.apogee_km = (double)L.apo;
+    r.land_lat_deg = 0.0;
+    r.land_lon_deg = 0.0;
+    r.status = L.status;
+    r.n_steps = L.n_steps;
+    r.n_attempts = L.n_att;
+    r.n_evals = L.n_ev;
+    out[L.out_id] = r;
+}
+
+// Final outputs of the mixed path's records, one thread per record (a
+// converged pass after the trace): record k of a fan holds the raw final
+// state lane_finish wrote; k is its canonical index, which gives the launch
+// azimuth.
+__global__ void finish_records_kernel(double R_E, FanDev f, rt_ray_result *__restrict__ out, long long n) {
+    const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const rt_ray_result r = out[k];
+    const double az = f.az[(unsigned)k % (unsigned)f.n_az].rad;
+    finish_result(f.tx_th, f.tx_ph, az, r.ground_range_km, r.az_dev_deg, r.group_path_km, r.apogee_km, r.status,
+                  r.n_steps, r.n_attempts, r.n_evals, R_E, out + k);
+}
+
+// The same for the records of several fans traced in one launch: record i
+// belongs to fan k with first[k] <= i < first[k + 1].
+__global__ void finish_fans_records_kernel(double R_E, const FanDev *__restrict__ fans,
+                                           const long long *__restrict__ first, int n_fans,
+                                           rt_ray_result *__restrict__ out) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= first[n_fans]) return;
+    int lo = 0, hi = n_fans - 1;
+    while (lo < hi) {  // largest k with first[k] <= i
+        const int mid = (lo + hi + 1) >> 1;
+        if (first[mid] <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    const FanDev &f = fans[lo];
+    const long long k = i - first[lo];
+    const rt_ray_result r = out[i];
+    const double az = f.az[(unsigned)k % (unsigned)f.n_az].rad;
+    finish_result(f.tx_th, f.tx_ph, az, r.ground_range_km, r.az_dev_deg, r.group_path_km, r.apogee_km, r.status,
+                  r.n_steps, r.n_attempts, r.n_evals, R_E, out + i);
 }
 
 // Once k1 is known: end an adaptive step just past the next cell face, and
@@ -1636,8 +1684,8 @@ static cudaError_t launch_mixed(const GridDev &g, const FanDev &f, rt_ray_result
     }
 }
 
-cudaError_t launch_trace(const GridDev &g, const FanDev &f, rt_ray_result *out, unsigned long long *counter,
-                         const LaunchPlan &lp, cudaStream_t st) {
+cudaError_t launch_trace_only(const GridDev &g, const FanDev &f, rt_ray_result *out, unsigned long long *counter,
+                              const LaunchPlan &lp, cudaStream_t st) {
     if (f.n_rays == 0) return cudaSuccess;
     if (f.precision == RT_FP64) {
         const int threads = 128;
@@ -1650,6 +1698,20 @@ cudaError_t launch_trace(const GridDev &g, const FanDev &f, rt_ray_result *out, 
         case RT_STENCIL_TABLE: return launch_mixed<RT_STENCIL_TABLE>(g, f, out, counter, lp, st);
         default: return launch_mixed<RT_STENCIL_QUAD>(g, f, out, counter, lp, st);
     }
+}
+
+cudaError_t launch_finish(const GridDev &g, const FanDev &f, rt_ray_result *out, long long n, cudaStream_t st) {
+    if (f.precision == RT_FP64 || n == 0) return cudaSuccess;  // the FP64 kernel writes final records itself
+    const int threads = 128;
+    finish_records_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, st>>>(g.R_E, f, out, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trace(const GridDev &g, const FanDev &f, rt_ray_result *out, unsigned long long *counter,
+                         const LaunchPlan &lp, cudaStream_t st) {
+    const cudaError_t e = launch_trace_only(g, f, out, counter, lp, st);
+    if (e != cudaSuccess) return e;
+    return launch_finish(g, f, out, f.n_rays, st);
 }
 
 template <int STENCIL>
@@ -1667,14 +1729,22 @@ cudaError_t launch_trace_fans(const GridDev &g, const FanDev *fans, const long l
                               long long n_total, int integrator, rt_ray_result *out, const LaunchPlan &lp,
                               cudaStream_t st) {
     if (n_total == 0) return cudaSuccess;
+    cudaError_t e;
     switch (lp.stencil) {
         case RT_STENCIL_GATHER:
-            return launch_fans_s<RT_STENCIL_GATHER>(g, fans, first, n_fans, n_total, integrator, out, lp.threads, st);
+            e = launch_fans_s<RT_STENCIL_GATHER>(g, fans, first, n_fans, n_total, integrator, out, lp.threads, st);
+            break;
         case RT_STENCIL_TABLE:
-            return launch_fans_s<RT_STENCIL_TABLE>(g, fans, first, n_fans, n_total, integrator, out, lp.threads, st);
+            e = launch_fans_s<RT_STENCIL_TABLE>(g, fans, first, n_fans, n_total, integrator, out, lp.threads, st);
+            break;
         default:
-            return launch_fans_s<RT_STENCIL_QUAD>(g, fans, first, n_fans, n_total, integrator, out, lp.threads, st);
+            e = launch_fans_s<RT_STENCIL_QUAD>(g, fans, first, n_fans, n_total, integrator, out, lp.threads, st);
     }
+    if (e != cudaSuccess) return e;
+    const int threads = 128;
+    finish_fans_records_kernel<<<(unsigned)((n_total + threads - 1) / threads), threads, 0, st>>>(g.R_E, fans, first,
+                                                                                                 n_fans, out);
+    return cudaGetLastError();
 }
 
 template <int STENCIL>
