@@ -670,7 +670,7 @@ __device__ __forceinline__ bool stage_cell(int i0, float t, int n, int &i, float
     // floor of t clamped to +-1e6 (keeps the int sum far from overflow) without
     // conversion instructions: adding 1.5 * 2^23 rounds to the nearest integer,
     // which sits in the low mantissa bits; one less if that rounded up.  A NaN
-    // t clamps to -1e6 and then fails the fraction test below.
+    // t clamps to -1e6 and then fails the cell index test below.
     const float magic = 12582912.0f;
     const float tc = fminf(fmaxf(t, -1e6f), 1e6f);
     const float big = tc + magic;
@@ -680,10 +680,11 @@ __device__ __forceinline__ bool stage_cell(int i0, float t, int n, int &i, float
     int ii = i0 + (__float_as_int(big) - __float_as_int(magic)) - (up ? 1 : 0);
     float tr = t - fl;
     const bool last = (ii == n - 1) & (tr == 0.0f);  // the last node: cell n-2 at t = 1
-    // NaN fails the first two tests; an offset beyond the clamp fails them too
-    const bool ok = (tr >= 0.0f) & (tr <= 1.0f) & (ii >= 0) & ((ii < n - 1) | last);
     ii = last ? n - 2 : ii;
     tr = last ? 1.0f : tr;
+    // tr = t - floor(t) lies in [0, 1] by construction, so the cell index alone
+    // decides; a NaN or an offset beyond the clamp puts it ~1e6 cells out
+    const bool ok = (unsigned)ii < (unsigned)(n - 1);
     i = ok ? ii : 0;
     tt = ok ? tr : 0.0f;
     return ok;
@@ -812,9 +813,9 @@ __device__ __forceinline__ void rhs_mixed(const GridDev &g, const RayPhys<float>
 // holds sum_j a[s+1][j] k_j, the offset (over h) of the next stage; y4 and the
 // error estimate accumulate B4[s] k_s and E[s] k_s.
 struct Tableau {
-    float A[6][5];
-    float B4[6];
-    float E[6];
+    // row s: {A[s][0..3]} and {A[s][4], B4[s], E[s], 0}, two 16-byte loads per stage
+    float4 lo[6];
+    float4 hi[6];
     int ns;
 };
 
@@ -915,10 +916,9 @@ __device__ __forceinline__ RayPhys<float> lane_phys(const GridDev &g, const Lane
 
 // Stage 0 of an attempt: acc/y4/e start from k1.
 __device__ __forceinline__ void accumulate_first(Lane &L, const Tableau &T, const float k1[6]) {
-    float A[5];
-#pragma unroll
-    for (int t = 0; t < 5; ++t) A[t] = T.A[0][t];
-    const float b4 = T.B4[0], e = T.E[0];
+    const float4 lo = T.lo[0], hi = T.hi[0];
+    const float A[5] = {lo.x, lo.y, lo.z, lo.w, hi.x};
+    const float b4 = hi.y, e = hi.z;
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
 #pragma unroll
@@ -930,10 +930,9 @@ __device__ __forceinline__ void accumulate_first(Lane &L, const Tableau &T, cons
 
 // Stage s >= 1: shift the accumulators and add stage s's output ks.
 __device__ __forceinline__ void accumulate_next(Lane &L, const Tableau &T, int s, const float ks[6]) {
-    float A[5];
-#pragma unroll
-    for (int t = 0; t < 5; ++t) A[t] = T.A[s][t];
-    const float b4 = T.B4[s], e = T.E[s];
+    const float4 lo = T.lo[s], hi = T.hi[s];
+    const float A[5] = {lo.x, lo.y, lo.z, lo.w, hi.x};
+    const float b4 = hi.y, e = hi.z;
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
 #pragma unroll
@@ -1600,25 +1599,38 @@ __global__ void eval_rhs_kernel(GridDev g, const double *__restrict__ ys, double
 }
 
 // ================================================================ launchers
-static void fill_tableaus(Tableau tab[2]) {
-    for (int t = 0; t < 2; ++t) {
-        for (int s = 0; s < 6; ++s) {
-            for (int u = 0; u < 5; ++u) tab[t].A[s][u] = 0.0f;
-            tab[t].B4[s] = tab[t].E[s] = 0.0f;
-        }
+// Packs Butcher coefficients A[s][t], B4[s], E[s] (s = 0..5) into the
+// two-float4-per-stage layout of Tableau.
+static void pack_tableau(Tableau &T, const float A[6][5], const float B4[6], const float E[6], int ns) {
+    for (int s = 0; s < 6; ++s) {
+        T.lo[s] = make_float4(A[s][0], A[s][1], A[s][2], A[s][3]);
+        T.hi[s] = make_float4(A[s][4], B4[s], E[s], 0.0f);
     }
+    T.ns = ns;
+}
+
+static void fill_tableaus(Tableau tab[2]) {
+    float A[6][5], B4[6], E[6];
+    auto clear = [&]() {
+        for (int s = 0; s < 6; ++s) {
+            for (int u = 0; u < 5; ++u) A[s][u] = 0.0f;
+            B4[s] = E[s] = 0.0f;
+        }
+    };
     // classic RK4: a21 = a32 = 1/2, a43 = 1; b = (1, 2, 2, 1)/6; A[s][t] = a[s+1+t][s]
+    clear();
     double a4[4][4] = {{0}};
     a4[1][0] = 0.5;
     a4[2][1] = 0.5;
     a4[3][2] = 1.0;
     const double b4[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
-    tab[0].ns = 4;
     for (int s = 0; s < 4; ++s) {
-        for (int u = 0; u < 5; ++u) tab[0].A[s][u] = (s + 1 + u < 4) ? (float)a4[s + 1 + u][s] : 0.0f;
-        tab[0].B4[s] = (float)b4[s];
+        for (int u = 0; u < 5; ++u) A[s][u] = (s + 1 + u < 4) ? (float)a4[s + 1 + u][s] : 0.0f;
+        B4[s] = (float)b4[s];
     }
+    pack_tableau(tab[0], A, B4, E, 4);
     // Fehlberg 4(5)
+    clear();
     double a[6][6] = {{0}};
     a[1][0] = 1.0 / 4.0;
     a[2][0] = 3.0 / 32.0;
@@ -1637,12 +1649,12 @@ static void fill_tableaus(Tableau tab[2]) {
     a[5][4] = -11.0 / 40.0;
     const double b4f[6] = {25.0 / 216.0, 0.0, 1408.0 / 2565.0, 2197.0 / 4104.0, -1.0 / 5.0, 0.0};
     const double b5f[6] = {16.0 / 135.0, 0.0, 6656.0 / 12825.0, 28561.0 / 56430.0, -9.0 / 50.0, 2.0 / 55.0};
-    tab[1].ns = 6;
     for (int s = 0; s < 6; ++s) {
-        for (int u = 0; u < 5; ++u) tab[1].A[s][u] = (s + 1 + u < 6) ? (float)a[s + 1 + u][s] : 0.0f;
-        tab[1].B4[s] = (float)b4f[s];
-        tab[1].E[s] = (float)(b5f[s] - b4f[s]);
+        for (int u = 0; u < 5; ++u) A[s][u] = (s + 1 + u < 6) ? (float)a[s + 1 + u][s] : 0.0f;
+        B4[s] = (float)b4f[s];
+        E[s] = (float)(b5f[s] - b4f[s]);
     }
+    pack_tableau(tab[1], A, B4, E, 6);
 }
 
 cudaError_t upload_tableaus() {
