@@ -530,6 +530,15 @@ def run_ours(args):
         alone_ms, _ = time_one_ray(rt, torch, grid, one_ray_spec(wl, spec, i_long), prec, cfg, 3, 2)
         critical = {"longest_ray_alone_ms": alone_ms, "fan_ms": mean_ms, "fan_over_alone": mean_ms / alone_ms,
                     "ns_per_stage_eval_alone": alone_ms * 1e6 / max(int(res["n_evals"][i_long]), 1)}
+        # the FP64 path's own critical path: its longest ray traced alone (one
+        # thread per ray), beside its whole-fan time
+        fp64_alone = None
+        if prec == rt.RT_MIXED:
+            i64 = int(np.argmax(ref64["n_evals"]))
+            a64, r64 = time_one_ray(rt, torch, grid, one_ray_spec(wl, spec, i64), rt.RT_FP64, None, 1, 1)
+            fp64_alone = {"longest_ray_alone_ms": a64, "stage_evals": int(r64["n_evals"][0]),
+                          "ns_per_stage_eval_alone": a64 * 1e6 / max(int(r64["n_evals"][0]), 1),
+                          "fan_over_alone": fp64_s * 1e3 / a64}
         batch = None
         if world == 1 and not args.no_batch and prec == rt.RT_MIXED:
             try:
@@ -571,7 +580,7 @@ def run_ours(args):
                             "stage_evals_p99": float(np.percentile(res["n_evals"], 99))},
             "accuracy": acc,
             "tighter_rtol": nominal,
-            "fp64_gpu_path": {"rays_per_s": n / fp64_s, "seconds": fp64_s},
+            "fp64_gpu_path": {"rays_per_s": n / fp64_s, "seconds": fp64_s, "critical_path": fp64_alone},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": captured_traffic(args.workload, cfg),
                          "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
