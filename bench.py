@@ -827,7 +827,8 @@ def run_batch(rt, wl, torch, flush, steps=3):
                                                            "5 % of its period",
                                          "own_previous": "the plan's previous execution (same ionosphere)"}}
     ordered_sample = {}
-    for name, c, src in (("plain", cfg, prev), ("persistent", cfg_p, prev), ("plain_own_previous", cfg, own)):
+    for name, c, src in (("plain", cfg, prev), ("persistent", cfg_p, prev), ("plain_own_previous", cfg, own),
+                         ("persistent_own_previous", cfg_p, own)):
         oplan = rt.Plan(grid, fan, cfg=c)
         n_long = oplan.order(src.data_ptr(), spread=2, long_factor=6.0, stream=side.cuda_stream)
         ograph = torch.cuda.CUDAGraph()
