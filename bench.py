@@ -542,6 +542,15 @@ def run_ours(args):
             fp64_alone = {"longest_ray_alone_ms": a64, "stage_evals": int(r64["n_evals"][0]),
                           "ns_per_stage_eval_alone": a64 * 1e6 / max(int(r64["n_evals"][0]), 1),
                           "fan_over_alone": fp64_s * 1e3 / a64}
+        # the same fan as a plan ordered by earlier costs (a repeated scan)
+        fan_ordered = None
+        if prec == rt.RT_MIXED and cfg is not None and args.workload == "c2":
+            try:
+                fan_ordered = run_fan_ordered(rt, wl, torch, grid, fan, spec, cfg, flush, res,
+                                              o_res if world == 1 and len(o_idx) == n else None,
+                                              well_all if world == 1 and len(o_idx) == n else None)
+            except Exception as exc:
+                fan_ordered = {"error": repr(exc)}
         batch = None
         if world == 1 and not args.no_batch and prec == rt.RT_MIXED:
             try:
@@ -577,6 +586,7 @@ def run_ours(args):
             "stage_evals_per_s": evals * world / sec,
             "fan_latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
             "critical_path": critical,
+            "fan_ordered": fan_ordered,
             "longest_ray": {"index": int(np.argmax(res["n_evals"])), "stage_evals": int(res["n_evals"].max()),
                             "status": int(res["status"][int(np.argmax(res["n_evals"]))]),
                             "stage_evals_p50": float(np.median(res["n_evals"])),
@@ -677,6 +687,62 @@ def richardson_table(rt, wl, grid, spec, prec, cfg, stream):
             "observed_order_group_path": order,
             "this_path": err(ours), "fp64_same_rtol": err(same_rtol), "fp64_rtol_1e-11": err(conv),
             "rk4_h_0.25_km": err(runs[2])}
+
+
+def run_fan_ordered(rt, wl, torch, grid, fan, spec, cfg, flush, res, o_res, well, steps=7,
+                    long_factor=2.0):
+    """The fan as a plan whose rays are ordered by the costs of an earlier
+    trace (rt_plan_order): the rays above long_factor x the median cost at
+    four lanes, a warp each, on SMs of their own (RT_PLAN_LONG_EXCLUSIVE |
+    RT_PLAN_LONG_ALONE), the rest in the plan's own order.  Cost sources: the
+    plan's previous execution (a scan repeated on the same ionosphere) and the
+    same scan on a later snapshot (the TID advanced 5 % of its period).
+    Every execution traces every ray; records are compared with the
+    canonical fan's and, where given, with the oracle's."""
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    n = fan.n_rays
+    plan = rt.Plan(grid, fan, cfg)
+    own = torch.empty(n * 64, dtype=torch.uint8, device="cuda")
+    plan.execute(own.data_ptr(), n, stream=sptr)
+    w_snap = wl.config2(tid_phase_shift=0.05)
+    g_snap = rt.Grid(w_snap.grid, w_snap.ne, table=True)
+    snap = torch.empty(n * 64, dtype=torch.uint8, device="cuda")
+    rt.rt_trace_device(g_snap, rt.Fan(spec, rt.RT_MIXED), snap.data_ptr(), n, cfg=cfg, stream=sptr)
+    torch.cuda.synchronize()
+    g_snap.close()
+    out = torch.empty(n * 64, dtype=torch.uint8, device="cuda")
+    ref_bytes = np.ascontiguousarray(res).tobytes()
+    result = {"long_factor": long_factor, "flags": "RT_PLAN_LONG_EXCLUSIVE | RT_PLAN_LONG_ALONE | "
+                                                   "RT_PLAN_REST_IN_PLAN_ORDER",
+              "l2": "flushed before every execution"}
+    for name, src, spread in (("own_previous", own, 0), ("later_snapshot", snap, 1)):
+        n_long = plan.order(src.data_ptr(), spread=spread, long_factor=long_factor, rest_in_plan_order=True,
+                            long_exclusive=True, long_alone=True, stream=sptr)
+        for _ in range(2):
+            plan.execute(out.data_ptr(), n, stream=sptr)
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            plan.execute(out.data_ptr(), n, stream=sptr)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        rec = rt.results_view(out.cpu().numpy(), n).copy()
+        entry = {"ms_per_fan": float(np.mean(ms)), "rays_per_s": n / (float(np.mean(ms)) / 1e3),
+                 "fan_latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
+                 "four_lane_rays": int(n_long), "spread": spread,
+                 "records_identical_to_the_canonical_fan": rec.tobytes() == ref_bytes}
+        if o_res is not None:
+            entry["vs_cpu_oracle"] = gate_errors(rec, o_res, well)
+        result[name] = entry
+    result["cost_sources"] = {"own_previous": "the plan's previous execution (same ionosphere)",
+                              "later_snapshot": "the same scan on the ionosphere with the TID advanced by 5 % "
+                                                "of its period"}
+    plan.close()
+    return result
 
 
 def time_one_ray(rt, torch, grid, one, prec, cfg, steps, warmup):

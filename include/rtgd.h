@@ -326,7 +326,18 @@ rt_err rt_plan_destroy(rt_plan *plan);
  *   flags: by default the other rays are handed out in descending order of
  *     expected cost as well (rays of costs within 2^(1/8) of each other keep
  *     their canonical order); RT_PLAN_REST_IN_PLAN_ORDER keeps the plan's own
- *     claim order for them.
+ *     claim order for them.  RT_PLAN_LONG_EXCLUSIVE makes the four-lane
+ *     launch's blocks one warp wide and gives each an SM of its own (the
+ *     block reserves the SM's whole shared memory, so no other block is
+ *     resident beside it): its rays then run at the latency of a lone warp
+ *     instead of sharing issue slots with the rest of the scan, and the other
+ *     rays have that many SMs fewer.  The share is then cut to at most half
+ *     the SM count in blocks (its most expensive rays), and the other rays'
+ *     launch waits until all of its blocks have begun (a launch-completion
+ *     event; the runtime documents it as best effort).
+ *     RT_PLAN_LONG_ALONE gives each ray of the four-lane launch a warp of its
+ *     own (by default a warp holds eight of them, which then wait for one
+ *     another's branches and gathers at every attempt).
  * rt_plan_execute traces the other rays with the plan's launch
  * configuration.  A ray's record does
  * not depend on the order; rays in the four-lane launch give the records of
@@ -335,7 +346,7 @@ rt_err rt_plan_destroy(rt_plan *plan);
  * Blocking: copies the costs to the host, sorts and uploads the order.  Not
  * concurrent with an execution of the same plan.  Errors: RT_EINVAL,
  * RT_ENOMEM, RT_ECUDA, RT_ETIMEOUT. */
-enum { RT_PLAN_REST_IN_PLAN_ORDER = 1u };
+enum { RT_PLAN_REST_IN_PLAN_ORDER = 1u, RT_PLAN_LONG_EXCLUSIVE = 2u, RT_PLAN_LONG_ALONE = 4u };
 rt_err rt_plan_order(rt_plan *plan, const rt_ray_result *cost_dev, int32_t spread, double long_factor,
                      uint32_t flags, size_t *n_long, void *stream);
 

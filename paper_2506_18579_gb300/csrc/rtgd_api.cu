@@ -739,12 +739,14 @@ struct rt_plan {
     size_t n = 0;
     char *ws = nullptr;  // ray counter (16 B) + fan tables
     // longest-first order (rt_plan_order): claim order over all rays, the
-    // first n_long of which run in a four-lane launch on the side stream
+    // first n_long_claims of which (n_long rays, and holes when each has a
+    // warp of its own) run in a four-lane launch on the side stream
     int *perm = nullptr;
-    size_t n_long = 0;
+    size_t n_long = 0, n_long_claims = 0;
     LaunchPlan lp_long;
     cudaStream_t side = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
+    cudaEvent_t started = nullptr;  // all blocks of the four-lane launch have begun
 };
 
 rt_err rt_plan_create(const rt_grid *grid, const rt_fan_desc *fan, const rt_launch_config *cfg, rt_plan **out) {
@@ -798,14 +800,18 @@ rt_err rt_plan_execute(const rt_plan *plan, rt_ray_result *out_dev, size_t out_l
     FanDev fl = plan->f, fb = plan->f;
     fl.perm = fb.perm = plan->perm;
     fl.perm_off = 0;
-    fl.n_rays = (long long)plan->n_long;
-    fb.perm_off = (long long)plan->n_long;
+    fl.n_rays = (long long)plan->n_long_claims;
+    fb.perm_off = (long long)plan->n_long_claims;
     fb.n_rays = (long long)(plan->n - plan->n_long);
     if (plan->n_long > 0) {
         CUDA_TRY(cudaEventRecord(plan->fork, st));
         CUDA_TRY(cudaStreamWaitEvent(plan->side, plan->fork, 0));
         CUDA_TRY(launch_trace_only(plan->grid->g, fl, out_dev, nullptr, plan->lp_long, plan->side));
         CUDA_TRY(cudaEventRecord(plan->join, plan->side));
+        // SMs of their own for the four-lane blocks: the other rays' blocks
+        // wait until all of those have begun (else they could take every SM
+        // first and the four-lane blocks would wait for whole SMs to drain)
+        if (plan->lp_long.started) CUDA_TRY(cudaStreamWaitEvent(st, plan->lp_long.started, 0));
     }
     CUDA_TRY(launch_trace_only(plan->grid->g, fb, out_dev, (unsigned long long *)plan->ws, plan->lp, st));
     if (plan->n_long > 0) CUDA_TRY(cudaStreamWaitEvent(st, plan->join, 0));
@@ -817,13 +823,14 @@ rt_err rt_plan_order(rt_plan *plan, const rt_ray_result *cost_dev, int32_t sprea
                      uint32_t flags, size_t *n_long, void *stream) {
     if (!plan) return fail(RT_EINVAL, "plan is NULL");
     if (spread < 0 || spread > 64) return fail(RT_EINVAL, "spread must be in 0..64");
-    if (flags & ~(uint32_t)RT_PLAN_REST_IN_PLAN_ORDER) return fail(RT_EINVAL, "unknown flags 0x%x", flags);
+    if (flags & ~(uint32_t)(RT_PLAN_REST_IN_PLAN_ORDER | RT_PLAN_LONG_EXCLUSIVE | RT_PLAN_LONG_ALONE))
+        return fail(RT_EINVAL, "unknown flags 0x%x", flags);
     if (!std::isfinite(long_factor)) return fail(RT_EINVAL, "long_factor must be finite");
     if (n_long) *n_long = 0;
     if (!cost_dev) {  // back to the plan's own order
         if (plan->perm) cudaFree(plan->perm);
         plan->perm = nullptr;
-        plan->n_long = 0;
+        plan->n_long = plan->n_long_claims = 0;
         return RT_OK;
     }
     const size_t n = plan->n;
@@ -876,6 +883,13 @@ rt_err rt_plan_order(rt_plan *plan, const rt_ray_result *cost_dev, int32_t sprea
         const double thr = long_factor * (double)sorted[n / 2];
         while (nl < n / 16 && (double)cost[perm[nl]] >= thr) ++nl;
     }
+    if ((flags & RT_PLAN_LONG_EXCLUSIVE) && nl > 0) {
+        // one-warp blocks on SMs of their own: at most half of the SMs
+        int sms = 0;
+        CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, plan->grid->device));
+        const size_t per_block = (flags & RT_PLAN_LONG_ALONE) ? 1 : 32 / 4;
+        nl = std::min(nl, (size_t)std::max(sms / 2, 1) * per_block);
+    }
     if (flags & RT_PLAN_REST_IN_PLAN_ORDER) {
         // the other rays in the plan's own claim order
         std::vector<char> is_long(n, 0);
@@ -890,8 +904,21 @@ rt_err rt_plan_order(rt_plan *plan, const rt_ray_result *cost_dev, int32_t sprea
             if (!is_long[ray]) perm[k++] = (int)ray;
         }
     }
-    if (!plan->perm) CUDA_TRY(cudaMalloc((void **)&plan->perm, n * sizeof(int)));
-    CUDA_TRY(cudaMemcpy(plan->perm, perm.data(), n * sizeof(int), cudaMemcpyHostToDevice));
+    size_t nc = nl;
+    if ((flags & RT_PLAN_LONG_ALONE) && nl > 0) {
+        // a warp per ray in the four-lane launch: each ray's group of four
+        // lanes is followed by seven holes
+        constexpr size_t kGroups = 32 / 4;
+        std::vector<int> claims(nl * kGroups + (n - nl), -1);
+        for (size_t i = 0; i < nl; ++i) claims[i * kGroups] = perm[i];
+        std::copy(perm.begin() + (long long)nl, perm.end(), claims.begin() + (long long)(nl * kGroups));
+        nc = nl * kGroups;
+        perm.swap(claims);
+    }
+    // capacity for the largest claim list: n rays plus 7 holes for each of at
+    // most n / 16 four-lane rays
+    if (!plan->perm) CUDA_TRY(cudaMalloc((void **)&plan->perm, (n + 7 * (n / 16)) * sizeof(int)));
+    CUDA_TRY(cudaMemcpy(plan->perm, perm.data(), perm.size() * sizeof(int), cudaMemcpyHostToDevice));
     if (!plan->side) {
         int lo = 0, hi = 0;
         CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
@@ -901,11 +928,21 @@ rt_err rt_plan_order(rt_plan *plan, const rt_ray_result *cost_dev, int32_t sprea
         CUDA_TRY(cudaEventCreateWithFlags(&plan->fork, cudaEventDisableTiming));
         CUDA_TRY(cudaEventCreateWithFlags(&plan->join, cudaEventDisableTiming));
     }
+    LaunchPlan ll = plan->lp;
+    ll.kernel = RT_KERNEL_PLAIN;
+    ll.lanes = 4;
+    ll.blocks = 0;
+    ll.smem = 0;
+    if ((flags & RT_PLAN_LONG_EXCLUSIVE) && nl > 0) {
+        // one-warp blocks, each alone on its SM
+        ll.threads = 32;
+        CUDA_TRY(plain_exclusive_smem(ll, plan->grid->g.interp, &ll.smem));
+        if (!plan->started) CUDA_TRY(cudaEventCreateWithFlags(&plan->started, cudaEventDisableTiming));
+        ll.started = plan->started;
+    }
     plan->n_long = nl;
-    plan->lp_long = plan->lp;
-    plan->lp_long.kernel = RT_KERNEL_PLAIN;
-    plan->lp_long.lanes = 4;
-    plan->lp_long.blocks = 0;
+    plan->n_long_claims = nc;
+    plan->lp_long = ll;
     if (n_long) *n_long = nl;
     return RT_OK;
 }
@@ -917,6 +954,7 @@ rt_err rt_plan_destroy(rt_plan *plan) {
     if (plan->side) cudaStreamDestroy(plan->side);
     if (plan->fork) cudaEventDestroy(plan->fork);
     if (plan->join) cudaEventDestroy(plan->join);
+    if (plan->started) cudaEventDestroy(plan->started);
     delete plan;
     if (e != cudaSuccess) return cuda_fail(e, "rt_plan_destroy");
     return RT_OK;

@@ -50,7 +50,9 @@ struct FanDev {
     float rtol_f, atol_f, h0_f, hmin_f, hmax_f;
     int has_max_path;           // max_path > 0
     // Optional claim order (an ordered plan): claim c of this launch traces
-    // canonical ray perm[perm_off + c]; n_rays then counts this launch's rays.
+    // canonical ray perm[perm_off + c]; n_rays then counts this launch's
+    // claims.  A negative entry is a hole (no ray); holes occur only in the
+    // claims of an ordered plan's four-lane launch (plain kernel).
     const int *perm;
     long long perm_off;
 };
@@ -61,6 +63,10 @@ struct LaunchPlan {
     int threads;
     int blocks;   // persistent grid size
     int lanes;    // lanes per ray (1, 2, 4)
+    int smem = 0; // plain kernel: dynamic shared memory per block (bytes); see plain_exclusive_smem
+    // plain kernel: an event (timing disabled) that the launch records once
+    // all of its blocks have begun (a launch-completion event), or null
+    cudaEvent_t started = nullptr;
 };
 
 cudaError_t launch_grid_prep(const void *raw, int dtype, const GridSizes &sz, double *pad64, float *pad32,
@@ -75,6 +81,10 @@ cudaError_t launch_trace_only(const GridDev &g, const FanDev &f, rt_ray_result *
                               const LaunchPlan &lp, cudaStream_t st);
 cudaError_t launch_finish(const GridDev &g, const FanDev &f, rt_ray_result *out, long long n, cudaStream_t st);
 cudaError_t persistent_occupancy(int stencil, int lanes, int threads, int *blocks_per_sm);
+// Dynamic shared memory that makes a block of the plain kernel of lp (with
+// interpolant interp) fill a whole SM's shared memory, so that no other block
+// of any kernel is resident beside it; also raises the kernel's limit to it.
+cudaError_t plain_exclusive_smem(const LaunchPlan &lp, int interp, int *bytes);
 // Mixed path, four lanes per ray: n_fans fans (device array fans) in one
 // launch; first (device, n_fans + 1 entries) holds each fan's first ray in
 // the launch and the total; out receives the records fan after fan.

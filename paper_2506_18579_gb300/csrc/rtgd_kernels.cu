@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <algorithm>
 #include <cmath>
 #include <stdint.h>
 
@@ -1390,9 +1391,11 @@ __global__ void __launch_bounds__(128, G == 1 ? 3 : 2) trace_mixed_plain_kernel(
     if (id >= f.n_rays) return;  // whole groups leave together
     const int lane = threadIdx.x & 31, q = lane % G;
     const unsigned gmask = group_mask<G>(lane);
+    const long long ray = claim_to_ray(f, id);
+    if (ray < 0) return;  // a hole in an ordered plan's claim order: no ray for this group
     Lane L;
     L.active = true;
-    lane_begin_ray(L, g, f, claim_to_ray(f, id), btx);
+    lane_begin_ray(L, g, f, ray, btx);
     bool done = lane_launch<STENCIL, G, IP>(L, g, f, q, gmask);
     // the landing state stays in registers here (a shared-memory slot per
     // thread would take L1 that the sample gathers use; measured 3 % slower on
@@ -1677,9 +1680,65 @@ static cudaError_t launch_mixed_gi(const GridDev &g, const FanDev &f, rt_ray_res
         trace_mixed_persistent_kernel<STENCIL, G, IP><<<lp.blocks, lp.threads, 0, st>>>(g, f, out, counter);
     } else {
         const long long blocks = (f.n_rays * G + lp.threads - 1) / lp.threads;
-        trace_mixed_plain_kernel<STENCIL, G, IP><<<(unsigned)blocks, lp.threads, 0, st>>>(g, f, out);
+        if (lp.started) {
+            cudaLaunchConfig_t lc = {};
+            lc.gridDim = dim3((unsigned)blocks);
+            lc.blockDim = dim3((unsigned)lp.threads);
+            lc.dynamicSmemBytes = (size_t)lp.smem;
+            lc.stream = st;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeLaunchCompletionEvent;
+            at[0].val.launchCompletionEvent.event = lp.started;
+            at[0].val.launchCompletionEvent.flags = 0;
+            lc.attrs = at;
+            lc.numAttrs = 1;
+            return cudaLaunchKernelEx(&lc, trace_mixed_plain_kernel<STENCIL, G, IP>, g, f, out);
+        }
+        trace_mixed_plain_kernel<STENCIL, G, IP><<<(unsigned)blocks, lp.threads, (size_t)lp.smem, st>>>(g, f, out);
     }
     return cudaGetLastError();
+}
+
+template <int STENCIL, int G, int IP>
+static cudaError_t exclusive_smem_gi(int *bytes) {
+    int dev = 0, per_sm = 0, per_block = 0, reserved = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&per_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, trace_mixed_plain_kernel<STENCIL, G, IP>);
+    if (e != cudaSuccess) return e;
+    // the block's static + dynamic shared memory plus the per-block
+    // reservation take the SM's whole capacity
+    const int dyn = std::min(per_block, per_sm - reserved) - (int)fa.sharedSizeBytes;
+    if (dyn <= 0) return cudaErrorInvalidValue;
+    e = cudaFuncSetAttribute(trace_mixed_plain_kernel<STENCIL, G, IP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             dyn);
+    if (e == cudaSuccess) *bytes = dyn;
+    return e;
+}
+
+template <int STENCIL, int G>
+static cudaError_t exclusive_smem_g(int interp, int *bytes) {
+    return interp == 1 ? exclusive_smem_gi<STENCIL, G, 1>(bytes) : exclusive_smem_gi<STENCIL, G, 0>(bytes);
+}
+
+template <int STENCIL>
+static cudaError_t exclusive_smem_s(int lanes, int interp, int *bytes) {
+    switch (lanes) {
+        case 2: return exclusive_smem_g<STENCIL, 2>(interp, bytes);
+        case 4: return exclusive_smem_g<STENCIL, 4>(interp, bytes);
+        default: return exclusive_smem_g<STENCIL, 1>(interp, bytes);
+    }
+}
+
+cudaError_t plain_exclusive_smem(const LaunchPlan &lp, int interp, int *bytes) {
+    switch (lp.stencil) {
+        case RT_STENCIL_GATHER: return exclusive_smem_s<RT_STENCIL_GATHER>(lp.lanes, interp, bytes);
+        case RT_STENCIL_TABLE: return exclusive_smem_s<RT_STENCIL_TABLE>(lp.lanes, interp, bytes);
+        default: return exclusive_smem_s<RT_STENCIL_QUAD>(lp.lanes, interp, bytes);
+    }
 }
 
 template <int STENCIL, int G>

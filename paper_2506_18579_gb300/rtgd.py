@@ -28,6 +28,8 @@ RT_KERNEL_AUTO, RT_KERNEL_PLAIN, RT_KERNEL_PERSISTENT = 0, 1, 2
 RT_STENCIL_AUTO, RT_STENCIL_GATHER, RT_STENCIL_QUAD, RT_STENCIL_TABLE = 0, 1, 2, 3
 RT_ORDER_CANONICAL, RT_ORDER_ELEVATION_FASTEST = 0, 1
 RT_PLAN_REST_IN_PLAN_ORDER = 1
+RT_PLAN_LONG_EXCLUSIVE = 2
+RT_PLAN_LONG_ALONE = 4
 
 EXPORTED = ["rt_grid_create", "rt_grid_destroy", "rt_grid_device_bytes", "rt_fan_size",
             "rt_trace", "rt_trace_device", "rt_trace_fans_device", "rt_tune", "rt_eval_rhs", "rt_last_error",
@@ -328,14 +330,19 @@ class Plan:
     def execute(self, out_ptr, out_len, stream=None):
         _check(load().rt_plan_execute(self.handle, ctypes.c_void_p(out_ptr), out_len, stream))
 
-    def order(self, cost_ptr, spread=2, long_factor=0.0, rest_in_plan_order=False, stream=None):
+    def order(self, cost_ptr, spread=2, long_factor=0.0, rest_in_plan_order=False, long_exclusive=False,
+              long_alone=False, stream=None):
         """rt_plan_order: longest-first order from device records at cost_ptr
         (None: back to the plan's own order); returns the number of rays
-        traced at four lanes each."""
+        traced at four lanes each.  long_exclusive: each block of those rays
+        gets an SM of its own; long_alone: each of those rays a warp of its
+        own."""
         n_long = ctypes.c_size_t()
+        flags = ((RT_PLAN_REST_IN_PLAN_ORDER if rest_in_plan_order else 0) |
+                 (RT_PLAN_LONG_EXCLUSIVE if long_exclusive else 0) |
+                 (RT_PLAN_LONG_ALONE if long_alone else 0))
         _check(load().rt_plan_order(self.handle, None if cost_ptr is None else ctypes.c_void_p(cost_ptr),
-                                    int(spread), float(long_factor), RT_PLAN_REST_IN_PLAN_ORDER if rest_in_plan_order else 0,
-                                    ctypes.byref(n_long), stream))
+                                    int(spread), float(long_factor), flags, ctypes.byref(n_long), stream))
         return n_long.value
 
     def close(self):

@@ -209,15 +209,17 @@ def config1(dtype=np.float64) -> Workload:
     return Workload("chapman-F2 isotropic 21x21x61, 16 rays, RK4 h=1 km", g, ne, fan)
 
 
-def config2(seed=2, dtype=np.float32, elev_step=0.5, az_step=10.0, freqs=(8.0, 12.0, 16.0)) -> Workload:
+def config2(seed=2, dtype=np.float32, elev_step=0.5, az_step=10.0, freqs=(8.0, 12.0, 16.0),
+            tid_phase_shift=0.0) -> Workload:
     """Anisotropic O+X case: dipole (3.1e-5 T, 11 deg tilt); E layer (foE 3 MHz,
     110 km) + F2 with foF2 linear 6-10 MHz across latitude + 5 % / 200 km TID;
     91x181x151 grid (1 deg, 1 deg, 4 km) of FP32 samples; 8/12/16 MHz x
     elevations 3-60 deg step 0.5 x azimuths 0-350 step 10 x O and X
-    (24,840 rays); RKF45, rtol 1e-8."""
+    (24,840 rays); RKF45, rtol 1e-8.  tid_phase_shift (cycles): a later
+    snapshot, the TID advanced along its direction of travel."""
     rng = np.random.default_rng(seed)
     g = centred_grid(TX[0], TX[1], 91, 181, 151, 1.0, 1.0, 4.0, **dipole_field(TX[1]))
-    ne, info = two_layer_ne(g, rng)
+    ne, info = two_layer_ne(g, rng, tid_phase_shift=tid_phase_shift)
     fan = FanSpec(*TX, freq_mhz=np.array(freqs),
                   el_deg=np.arange(3.0, 60.0 + 1e-9, elev_step),
                   az_deg=np.arange(0.0, 360.0 - 1e-9, az_step),

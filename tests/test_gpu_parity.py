@@ -538,8 +538,9 @@ def test_ordered_plan_keeps_every_record(kernel):
     the plan's own order; with a four-lane share, every ray's record is either
     its one-lane record or (the rays of that share, the most expensive among
     them) its record from a four-lane plain trace.  Captured in a graph, the
-    ordered plan replays deterministically; ordering back to NULL restores the
-    plan's own launch."""
+    ordered plan replays deterministically; the four-lane share on SMs of its
+    own or with a warp per ray gives the same records; ordering back to NULL
+    restores the plan's own launch."""
     torch = pytest.importorskip("torch")
     w = wl.config2(elev_step=1.0, az_step=30.0)  # 3 x 2 x 58 x 12 = 4,176 rays
     g = rt.Grid(w.grid, w.ne)
@@ -580,6 +581,30 @@ def test_ordered_plan_keeps_every_record(kernel):
         torch.cuda.synchronize()
         assert rt.results_view(cap.cpu().numpy(), n).tobytes() == got.tobytes()
     del graph
+    # the four-lane share with a warp per ray (holes in the claim list), on SMs
+    # of its own (cut to half the SM count in blocks), and both: four-lane
+    # records for the share, the plan's own for the rest; captured and
+    # replayed as well
+    for excl, alone in ((True, False), (False, True), (True, True)):
+        nl = plan.order(cost.data_ptr(), spread=1, long_factor=3.0, long_exclusive=excl, long_alone=alone,
+                        stream=s.cuda_stream)
+        assert 0 < nl <= n_long
+        if not (excl and alone):
+            assert nl == n_long
+        got_x = run(plan)[1]
+        is1, is4 = _rows(got_x) == _rows(ref), _rows(got_x) == _rows(four)
+        assert np.all(is1 | is4) and (~is1).sum() <= nl and is4[top]
+        if nl == n_long:
+            assert got_x.tobytes() == got.tobytes()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(graph, stream=side):
+                plan.execute(cap.data_ptr(), n, stream=side.cuda_stream)
+        cap.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        assert rt.results_view(cap.cpu().numpy(), n).tobytes() == got_x.tobytes()
+        del graph
     assert plan.order(None) == 0
     assert run(plan)[1].tobytes() == ref.tobytes()
     plan.close()
