@@ -119,6 +119,10 @@ def parse_args():
                         "and print its time per stage evaluation")
     p.add_argument("--profile", action="store_true",
                    help="warm-up launches then one launch, nothing else (for ncu captures)")
+    p.add_argument("--profile-plan", choices=["none", "own-previous"], default="none",
+                   help="with --profile: run the fan as a plan ordered longest-first by the costs of its "
+                        "own previous execution (long factor 6, four-lane share on a second stream) "
+                        "instead of one trace call")
     p.add_argument("--cpu-sample", type=int, default=0,
                    help="rays of the fan the CPU oracle baseline traces (0 = the whole fan)")
     p.add_argument("--serve-fuse", type=int, default=16384,
@@ -405,7 +409,16 @@ def run_ours(args):
         grid.close()
         return
     if args.profile:
-        for _ in range(max(args.warmup, 1) + 1):
+        if args.profile_plan == "own-previous":
+            plan = rt.Plan(grid, fan, cfg)
+            plan.execute(out.data_ptr(), n, stream=sptr)
+            n_long = plan.order(out.data_ptr(), spread=0, long_factor=6.0, stream=sptr)
+            for _ in range(max(args.warmup, 1) + 1):
+                plan.execute(out.data_ptr(), n, stream=sptr)
+            torch.cuda.synchronize()
+            plan.close()
+            print(json.dumps({"profile_plan": "own-previous", "four_lane_rays": n_long}), flush=True)
+        for _ in range(max(args.warmup, 1) + 1 if args.profile_plan == "none" else 0):
             rt.rt_trace_device(grid, fan, out.data_ptr(), n, cfg=cfg, stream=sptr)
         torch.cuda.synchronize()
         res = rt.results_view(out.cpu().numpy(), n)
