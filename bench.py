@@ -52,14 +52,14 @@ KERNEL_SOURCES = ("paper_2506_18579_gb300/csrc/rtgd_kernels.cu", "paper_2506_185
 TRAFFIC = {
     # key = (workload, kernel, stencil, lanes per ray); the anisotropic fan in
     # the autotuner's configurations (plain, 4 lanes, 96-thread blocks)
-    ("c2", 1, 3, 4): {"bytes_per_launch": 26682112 + 17152, "source_sha256": "e3e4be7184bcf3a8"},
-    ("c2", 1, 2, 4): {"bytes_per_launch": 5370880 + 0, "source_sha256": "e3e4be7184bcf3a8"},
+    ("c2", 1, 3, 4): {"bytes_per_launch": 26681088 + 17408, "source_sha256": "f4834e970da2418f"},
+    ("c2", 1, 2, 4): {"bytes_per_launch": 5412352 + 0, "source_sha256": "f4834e970da2418f"},
     # the ionogram batch, one lane per ray (the only lane count the autotuner
     # tries on a fan this large): plain kernel with 32-thread blocks (table
     # and quad stencils), persistent kernel with 128-thread blocks
-    ("c4", 1, 3, 1): {"bytes_per_launch": 20798976 + 1485568, "source_sha256": "e3e4be7184bcf3a8"},
-    ("c4", 1, 2, 1): {"bytes_per_launch": 4582656 + 493056, "source_sha256": "e3e4be7184bcf3a8"},
-    ("c4", 2, 3, 1): {"bytes_per_launch": 20910080 + 533248, "source_sha256": "e3e4be7184bcf3a8"},
+    ("c4", 1, 3, 1): {"bytes_per_launch": 20861440 + 1409280, "source_sha256": "f4834e970da2418f"},
+    ("c4", 1, 2, 1): {"bytes_per_launch": 4627968 + 503296, "source_sha256": "f4834e970da2418f"},
+    ("c4", 2, 3, 1): {"bytes_per_launch": 20888064 + 514560, "source_sha256": "f4834e970da2418f"},
 }
 SMS = 152
 FP32_LANES_PER_SM = 128
