@@ -322,7 +322,9 @@ rt_err rt_plan_destroy(rt_plan *plan);
  *     least long_factor times the median (at most a sixteenth of the rays)
  *     are traced at four lanes per ray by a plain launch of their own, on a
  *     second, high-priority stream forked from and joined back to the
- *     execute call's stream; *n_long (may be NULL) receives their number.
+ *     execute call's stream, in the plan's own claim order (neighbouring
+ *     rays of a trace share a warp); *n_long (may be NULL) receives their
+ *     number.
  *   flags: by default the other rays are handed out in descending order of
  *     expected cost as well (rays of costs within 2^(1/8) of each other keep
  *     their canonical order); RT_PLAN_REST_IN_PLAN_ORDER keeps the plan's own

@@ -890,6 +890,18 @@ rt_err rt_plan_order(rt_plan *plan, const rt_ray_result *cost_dev, int32_t sprea
         const size_t per_block = (flags & RT_PLAN_LONG_ALONE) ? 1 : 32 / 4;
         nl = std::min(nl, (size_t)std::max(sms / 2, 1) * per_block);
     }
+    if (nl > 1) {
+        // the four-lane share in the plan's claim order: neighbouring rays of
+        // one trace share a warp (rays of similar cost from all over the scan
+        // would wait for one another's branches and gathers at every attempt)
+        auto claim_of = [&](long long ray) {
+            if (f.order != RT_ORDER_ELEVATION_FASTEST) return ray;
+            const long long a = ray % n_a, e = (ray / n_a) % n_e, fm = ray / (n_a * n_e);
+            return (fm * n_a + a) * n_e + e;
+        };
+        std::sort(perm.begin(), perm.begin() + (long long)nl,
+                  [&](int x, int y) { return claim_of(x) < claim_of(y); });
+    }
     if (flags & RT_PLAN_REST_IN_PLAN_ORDER) {
         // the other rays in the plan's own claim order
         std::vector<char> is_long(n, 0);
