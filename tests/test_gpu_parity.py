@@ -610,6 +610,44 @@ def test_ordered_plan_keeps_every_record(kernel):
     plan.close()
 
 
+def test_plan_order_arguments_and_the_exclusive_cap():
+    """rt_plan_order refuses unknown flags, a spread outside 0..64 and a
+    non-finite factor (RT_EINVAL); with SMs of their own
+    the four-lane share is cut to half the SM count in one-warp blocks (one
+    ray each with a warp per ray), its most expensive rays first."""
+    import ctypes
+    torch = pytest.importorskip("torch")
+    w = wl.config2(elev_step=1.0, az_step=30.0)  # 4,176 rays
+    g = rt.Grid(w.grid, w.ne)
+    fan = rt.Fan(w.fan, rt.RT_MIXED)
+    n = fan.n_rays
+    s = torch.cuda.current_stream()
+    plan = rt.Plan(g, fan, rt.launch_config(kernel=rt.RT_KERNEL_PLAIN, stencil=rt.RT_STENCIL_QUAD, lanes_per_ray=4))
+    cost = torch.zeros(n * 64, dtype=torch.uint8, device="cuda")
+    plan.execute(cost.data_ptr(), n, stream=s.cuda_stream)
+    s.synchronize()
+    ref = rt.results_view(cost.cpu().numpy(), n).copy()
+    lib = rt.load()
+    nl = ctypes.c_size_t(7)
+    for spread, factor, flags in ((0, 2.0, 8), (65, 2.0, 0), (-1, 2.0, 0), (0, float("nan"), 0)):
+        r = lib.rt_plan_order(plan.handle, ctypes.c_void_p(cost.data_ptr()), spread, ctypes.c_double(factor),
+                              flags, ctypes.byref(nl), ctypes.c_void_p(s.cuda_stream))
+        assert r == rt.RT_EINVAL, (spread, factor, flags)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert plan.order(cost.data_ptr(), spread=0, long_factor=1e-3, stream=s.cuda_stream) == n // 16
+    n_alone = plan.order(cost.data_ptr(), spread=0, long_factor=1e-3, long_exclusive=True, long_alone=True,
+                         stream=s.cuda_stream)
+    assert n_alone == min(n // 16, sms // 2)
+    n_excl = plan.order(cost.data_ptr(), spread=0, long_factor=1e-3, long_exclusive=True, stream=s.cuda_stream)
+    assert n_excl == min(n // 16, 8 * (sms // 2))
+    out = torch.full((n * 64,), 0xAB, dtype=torch.uint8, device="cuda")
+    plan.execute(out.data_ptr(), n, stream=s.cuda_stream)
+    s.synchronize()
+    # every ray traced; with four lanes throughout, the order changes no record
+    assert rt.results_view(out.cpu().numpy(), n).tobytes() == ref.tobytes()
+    plan.close()
+
+
 @pytest.mark.parametrize("prec", [rt.RT_FP64, rt.RT_MIXED])
 def test_ionogram_matches_oracle(orc, prec):
     w = wl.config2()
