@@ -329,14 +329,14 @@ rt_err rt_plan_destroy(rt_plan *plan);
  *     expected cost as well (rays of costs within 2^(1/8) of each other keep
  *     their canonical order); RT_PLAN_REST_IN_PLAN_ORDER keeps the plan's own
  *     claim order for them.  RT_PLAN_LONG_EXCLUSIVE makes the four-lane
- *     launch's blocks one warp wide and gives each an SM of its own (the
+ *     launch's blocks two warps wide and gives each an SM of its own (the
  *     block reserves the SM's whole shared memory, so no other block is
  *     resident beside it): its rays then run at the latency of a lone warp
  *     instead of sharing issue slots with the rest of the scan, and the other
- *     rays have that many SMs fewer.  The share is then cut to at most half
- *     the SM count in blocks (its most expensive rays), and the other rays'
- *     launch waits until all of its blocks have begun (a launch-completion
- *     event; the runtime documents it as best effort).
+ *     rays have that many SMs fewer.  The share is then cut to at most an
+ *     eighth of the SM count in blocks (its most expensive rays), and the
+ *     other rays' launch waits until all of its blocks have begun (a
+ *     launch-completion event; the runtime documents it as best effort).
  *     RT_PLAN_LONG_ALONE gives each ray of the four-lane launch a warp of its
  *     own (by default a warp holds eight of them, which then wait for one
  *     another's branches and gathers at every attempt).

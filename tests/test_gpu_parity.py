@@ -613,8 +613,9 @@ def test_ordered_plan_keeps_every_record(kernel):
 def test_plan_order_arguments_and_the_exclusive_cap():
     """rt_plan_order refuses unknown flags, a spread outside 0..64 and a
     non-finite factor (RT_EINVAL); with SMs of their own
-    the four-lane share is cut to half the SM count in one-warp blocks (one
-    ray each with a warp per ray), its most expensive rays first."""
+    the four-lane share is cut to an eighth of the SM count in two-warp
+    blocks (one ray per warp with a warp per ray), its most expensive rays
+    first."""
     import ctypes
     torch = pytest.importorskip("torch")
     w = wl.config2(elev_step=1.0, az_step=30.0)  # 4,176 rays
@@ -637,9 +638,9 @@ def test_plan_order_arguments_and_the_exclusive_cap():
     assert plan.order(cost.data_ptr(), spread=0, long_factor=1e-3, stream=s.cuda_stream) == n // 16
     n_alone = plan.order(cost.data_ptr(), spread=0, long_factor=1e-3, long_exclusive=True, long_alone=True,
                          stream=s.cuda_stream)
-    assert n_alone == min(n // 16, sms // 2)
+    assert n_alone == min(n // 16, 2 * (sms // 8))
     n_excl = plan.order(cost.data_ptr(), spread=0, long_factor=1e-3, long_exclusive=True, stream=s.cuda_stream)
-    assert n_excl == min(n // 16, 8 * (sms // 2))
+    assert n_excl == min(n // 16, 16 * (sms // 8))
     out = torch.full((n * 64,), 0xAB, dtype=torch.uint8, device="cuda")
     plan.execute(out.data_ptr(), n, stream=s.cuda_stream)
     s.synchronize()
