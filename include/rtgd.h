@@ -345,8 +345,10 @@ rt_err rt_plan_destroy(rt_plan *plan);
  * not depend on the order; rays in the four-lane launch give the records of
  * a four-lane plain trace (their contraction sums in another order).  The
  * execute step stays graph-capturable (the fork and join are stream events).
- * Blocking: copies the costs to the host, sorts and uploads the order.  Not
- * concurrent with an execution of the same plan.  Errors: RT_EINVAL,
+ * Blocking: gathers the costs on the device (into an array the plan then
+ * keeps), copies them to the host, sorts and uploads the order (about 4-5 ms
+ * of host time for 495,122 rays).  Not concurrent with an execution of the
+ * same plan.  Errors: RT_EINVAL,
  * RT_ENOMEM, RT_ECUDA, RT_ETIMEOUT. */
 enum { RT_PLAN_REST_IN_PLAN_ORDER = 1u, RT_PLAN_LONG_EXCLUSIVE = 2u, RT_PLAN_LONG_ALONE = 4u };
 rt_err rt_plan_order(rt_plan *plan, const rt_ray_result *cost_dev, int32_t spread, double long_factor,

@@ -742,6 +742,7 @@ struct rt_plan {
     // first n_long_claims of which (n_long rays, and holes when each has a
     // warp of its own) run in a four-lane launch on the side stream
     int *perm = nullptr;
+    int32_t *evals = nullptr;  // the costs of the last rt_plan_order, gathered on the device
     size_t n_long = 0, n_long_claims = 0;
     LaunchPlan lp_long;
     cudaStream_t side = nullptr;
@@ -840,52 +841,98 @@ rt_err rt_plan_order(rt_plan *plan, const rt_ray_result *cost_dev, int32_t sprea
     }
     const size_t n = plan->n;
     cudaStream_t st = (cudaStream_t)stream;
-    // the n_evals field of every record (a strided copy)
+    // the n_evals field of every record, gathered on the device into the
+    // plan's cost array and copied back in one piece
+    if (!plan->evals) CUDA_TRY(cudaMalloc((void **)&plan->evals, n * sizeof(int32_t)));
+    CUDA_TRY(launch_gather_evals(cost_dev, plan->evals, (long long)n, st));
     std::vector<int32_t> ev(n);
-    CUDA_TRY(cudaMemcpy2DAsync(ev.data(), sizeof(int32_t), (const char *)cost_dev + offsetof(rt_ray_result, n_evals),
-                               sizeof(rt_ray_result), sizeof(int32_t), n, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(ev.data(), plan->evals, n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     rt_err r = sync_with_timeout(st);
     if (r != RT_OK) return r;
     // expected cost: the largest cost within `spread` elevation and frequency
     // steps of the same mode and azimuth (canonical order [freq][mode][el][az])
     const FanDev &f = plan->f;
     const long long n_f = f.n_freq, n_m = f.n_modes, n_e = f.n_el, n_a = f.n_az;
-    std::vector<int32_t> tmp(n), cost(n);
-    auto at = [&](long long q, long long m, long long e, long long a) { return ((q * n_m + m) * n_e + e) * n_a + a; };
-    for (long long q = 0; q < n_f; ++q)
-        for (long long m = 0; m < n_m; ++m)
-            for (long long e = 0; e < n_e; ++e)
-                for (long long a = 0; a < n_a; ++a) {
-                    int32_t v = 0;
-                    for (long long d = std::max(0LL, e - spread); d <= std::min(n_e - 1, e + spread); ++d)
-                        v = std::max(v, ev[at(q, m, d, a)]);
-                    tmp[at(q, m, e, a)] = v;
+    std::vector<int32_t> cost;
+    if (spread == 0) {
+        cost.swap(ev);
+    } else {
+        std::vector<int32_t> tmp(n);
+        cost.resize(n);
+        // elevation, then frequency: the maximum over a window of each line
+        // of the canonical array, whose elements lie `stride` apart (whole
+        // rows at once where the lines are far apart)
+        auto dilate = [&](const std::vector<int32_t> &in, std::vector<int32_t> &out, long long len,
+                          long long stride, long long outer) {
+            for (long long o = 0; o < outer; ++o) {
+                const int32_t *src = in.data() + o * len * stride;
+                int32_t *dst = out.data() + o * len * stride;
+                for (long long x = 0; x < len; ++x) {
+                    const long long lo = std::max(0LL, x - spread), hi = std::min(len - 1, x + (long long)spread);
+                    int32_t *row = dst + x * stride;
+                    if (stride == 1) {
+                        int32_t v = src[lo];
+                        for (long long d = lo + 1; d <= hi; ++d) v = std::max(v, src[d]);
+                        *row = v;
+                        continue;
+                    }
+                    std::copy(src + lo * stride, src + (lo + 1) * stride, row);
+                    for (long long d = lo + 1; d <= hi; ++d) {
+                        const int32_t *sr = src + d * stride;
+                        for (long long k = 0; k < stride; ++k) row[k] = std::max(row[k], sr[k]);
+                    }
                 }
-    for (long long q = 0; q < n_f; ++q)
-        for (long long m = 0; m < n_m; ++m)
-            for (long long e = 0; e < n_e; ++e)
-                for (long long a = 0; a < n_a; ++a) {
-                    int32_t v = 0;
-                    for (long long d = std::max(0LL, q - spread); d <= std::min(n_f - 1, q + spread); ++d)
-                        v = std::max(v, tmp[at(d, m, e, a)]);
-                    cost[at(q, m, e, a)] = v;
-                }
+            }
+        };
+        dilate(ev, tmp, n_e, n_a, n_f * n_m);
+        dilate(tmp, cost, n_f, n_m * n_e * n_a, 1);
+    }
     // descending cost, eight buckets per octave (rays of one bucket keep
-    // their canonical order, so neighbours stay together): a counting sort
-    auto key = [](int32_t c) { return (int)std::floor(8.0 * std::log2((double)std::max(c, 1))); };
+    // their canonical order, so neighbours stay together): a counting sort on
+    // the key floor(8 log2 cost), found with integer comparisons against
+    // ceil(2^(e + j/8)) for the cost's octave e
+    static const std::vector<uint64_t> kThr = [] {
+        std::vector<uint64_t> t(32 * 8);
+        for (int e = 0; e < 32; ++e)
+            for (int j = 0; j < 8; ++j) t[e * 8 + j] = (uint64_t)std::ceil(std::exp2((double)e + j / 8.0));
+        return t;
+    }();
+    auto key = [](int32_t c) {
+        const uint32_t u = (uint32_t)std::max(c, 1);
+        const int e = 31 - __builtin_clz(u);  // floor(log2 u)
+        int k = 8 * e;
+        for (int j = 1; j < 8; ++j) k += (uint64_t)u >= kThr[e * 8 + j];
+        return k;
+    };
     constexpr int kKeys = 8 * 32;
+    std::vector<uint8_t> keys(n);
     std::vector<size_t> start(kKeys + 1, 0);
-    for (size_t i = 0; i < n; ++i) ++start[kKeys - 1 - key(cost[i]) + 1];
+    for (size_t i = 0; i < n; ++i) {
+        keys[i] = (uint8_t)key(cost[i]);
+        ++start[kKeys - 1 - keys[i] + 1];
+    }
     for (int k = 0; k < kKeys; ++k) start[k + 1] += start[k];
     std::vector<int> perm(n);
-    for (size_t i = 0; i < n; ++i) perm[start[kKeys - 1 - key(cost[i])]++] = (int)i;
+    for (size_t i = 0; i < n; ++i) perm[start[kKeys - 1 - keys[i]]++] = (int)i;
     // the four-lane share: rays whose expected cost is at least long_factor
     // times the median (mixed path only), at most a sixteenth of the rays
     size_t nl = 0;
     if (long_factor > 0.0 && f.precision == RT_MIXED) {
-        std::vector<int32_t> sorted(cost);
-        std::nth_element(sorted.begin(), sorted.begin() + (long long)(n / 2), sorted.end());
-        const double thr = long_factor * (double)sorted[n / 2];
+        // the median cost (the element of rank n/2): a radix select over the
+        // upper, then the lower 16 bits of the (non-negative) costs
+        std::vector<size_t> hist(1 << 16);
+        for (size_t i = 0; i < n; ++i) ++hist[(uint32_t)std::max(cost[i], 0) >> 16];
+        size_t rank = n / 2, hi = 0;
+        while (rank >= hist[hi]) rank -= hist[hi++];
+        std::fill(hist.begin(), hist.end(), 0);
+        for (size_t i = 0; i < n; ++i) {
+            const uint32_t u = (uint32_t)std::max(cost[i], 0);
+            if ((u >> 16) == hi) ++hist[u & 0xFFFFu];
+        }
+        size_t lo = 0;
+        while (rank >= hist[lo]) rank -= hist[lo++];
+        const double median = (double)((hi << 16) | lo);
+        const double thr = long_factor * median;
         while (nl < n / 16 && (double)cost[perm[nl]] >= thr) ++nl;
     }
     if ((flags & RT_PLAN_LONG_EXCLUSIVE) && nl > 0) {
@@ -970,6 +1017,7 @@ rt_err rt_plan_destroy(rt_plan *plan) {
     if (!plan) return RT_OK;
     cudaError_t e = cudaFree(plan->ws);
     if (plan->perm) cudaFree(plan->perm);
+    if (plan->evals) cudaFree(plan->evals);
     if (plan->side) cudaStreamDestroy(plan->side);
     if (plan->fork) cudaEventDestroy(plan->fork);
     if (plan->join) cudaEventDestroy(plan->join);

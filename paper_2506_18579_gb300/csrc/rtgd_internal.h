@@ -81,6 +81,8 @@ cudaError_t launch_trace_only(const GridDev &g, const FanDev &f, rt_ray_result *
                               const LaunchPlan &lp, cudaStream_t st);
 cudaError_t launch_finish(const GridDev &g, const FanDev &f, rt_ray_result *out, long long n, cudaStream_t st);
 cudaError_t persistent_occupancy(int stencil, int lanes, int threads, int *blocks_per_sm);
+// ev[i] = rec[i].n_evals for i < n (the cost field of n records, packed).
+cudaError_t launch_gather_evals(const rt_ray_result *rec, int32_t *ev, long long n, cudaStream_t st);
 // Dynamic shared memory that makes a block of the plain kernel of lp (with
 // interpolant interp) fill a whole SM's shared memory, so that no other block
 // of any kernel is resident beside it; also raises the kernel's limit to it.
