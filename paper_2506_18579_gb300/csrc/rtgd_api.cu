@@ -25,6 +25,21 @@
 #include "rtgd.h"
 #include "rtgd_internal.h"
 
+namespace rtgd {
+// The cost field of n records, packed (rt_plan_order reads it back in one piece).
+__global__ void gather_evals_kernel(const rt_ray_result *__restrict__ rec, int32_t *__restrict__ ev, long long n) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) ev[i] = rec[i].n_evals;
+}
+
+cudaError_t launch_gather_evals(const rt_ray_result *rec, int32_t *ev, long long n, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    const int threads = 256;
+    gather_evals_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, st>>>(rec, ev, n);
+    return cudaGetLastError();
+}
+}  // namespace rtgd
+
 using namespace rtgd;
 
 struct rt_grid {

@@ -1774,18 +1774,6 @@ cudaError_t launch_trace_only(const GridDev &g, const FanDev &f, rt_ray_result *
     }
 }
 
-__global__ void gather_evals_kernel(const rt_ray_result *__restrict__ rec, int32_t *__restrict__ ev, long long n) {
-    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i < n) ev[i] = rec[i].n_evals;
-}
-
-cudaError_t launch_gather_evals(const rt_ray_result *rec, int32_t *ev, long long n, cudaStream_t st) {
-    if (n == 0) return cudaSuccess;
-    const int threads = 256;
-    gather_evals_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, st>>>(rec, ev, n);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_finish(const GridDev &g, const FanDev &f, rt_ray_result *out, long long n, cudaStream_t st) {
     if (f.precision == RT_FP64 || n == 0) return cudaSuccess;  // the FP64 kernel writes final records itself
     const int threads = 128;
