@@ -345,6 +345,11 @@ rt_err rt_plan_destroy(rt_plan *plan);
  * not depend on the order; rays in the four-lane launch give the records of
  * a four-lane plain trace (their contraction sums in another order).  The
  * execute step stays graph-capturable (the fork and join are stream events).
+ * A graph captured from rt_plan_execute holds the launch sizes of the order
+ * in effect at capture but reads the claim list from the plan's memory, which
+ * the next rt_plan_order call rewrites: after ordering again (or back to
+ * NULL), discard such graphs and capture anew (an old graph could then trace
+ * some rays twice and skip others).
  * Blocking: gathers the costs on the device (into an array the plan then
  * keeps), copies them to the host, sorts and uploads the order (about 4-5 ms
  * of host time for 495,122 rays).  Not concurrent with an execution of the
