@@ -615,7 +615,8 @@ def test_plan_order_arguments_and_the_exclusive_cap():
     non-finite factor (RT_EINVAL); with SMs of their own
     the four-lane share is cut to an eighth of the SM count in two-warp
     blocks (one ray per warp with a warp per ray), its most expensive rays
-    first."""
+    first; an FP64 plan is ordered without a four-lane share and keeps its
+    records."""
     import ctypes
     torch = pytest.importorskip("torch")
     w = wl.config2(elev_step=1.0, az_step=30.0)  # 4,176 rays
@@ -647,6 +648,20 @@ def test_plan_order_arguments_and_the_exclusive_cap():
     # every ray traced; with four lanes throughout, the order changes no record
     assert rt.results_view(out.cpu().numpy(), n).tobytes() == ref.tobytes()
     plan.close()
+    # an FP64 plan takes the longest-first order (one thread per ray, no
+    # four-lane share whatever the factor and flags) and keeps every record
+    plan64 = rt.Plan(g, rt.Fan(w.fan, rt.RT_FP64))
+    c64 = torch.zeros(n * 64, dtype=torch.uint8, device="cuda")
+    plan64.execute(c64.data_ptr(), n, stream=s.cuda_stream)
+    s.synchronize()
+    ref64 = rt.results_view(c64.cpu().numpy(), n).copy()
+    assert plan64.order(c64.data_ptr(), spread=1, long_factor=3.0, long_exclusive=True, long_alone=True,
+                        stream=s.cuda_stream) == 0
+    out.fill_(0xAB)
+    plan64.execute(out.data_ptr(), n, stream=s.cuda_stream)
+    s.synchronize()
+    assert rt.results_view(out.cpu().numpy(), n).tobytes() == ref64.tobytes()
+    plan64.close()
 
 
 @pytest.mark.parametrize("prec", [rt.RT_FP64, rt.RT_MIXED])
