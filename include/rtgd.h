@@ -359,6 +359,27 @@ enum { RT_PLAN_REST_IN_PLAN_ORDER = 1u, RT_PLAN_LONG_EXCLUSIVE = 2u, RT_PLAN_LON
 rt_err rt_plan_order(rt_plan *plan, const rt_ray_result *cost_dev, int32_t spread, double long_factor,
                      uint32_t flags, size_t *n_long, void *stream);
 
+/* The claim list rt_plan_order builds, from host costs; host arithmetic only
+ * (no GPU call, usable without a device).
+ *   cost: n = n_freq * n_modes * n_el * n_az costs (stage evaluations) of an
+ *     earlier trace, canonical order [freq][mode][el][az], caller-owned.
+ *   claim_order: the plan's claim order (RT_ORDER_CANONICAL or
+ *     RT_ORDER_ELEVATION_FASTEST); spread, long_factor, flags: as in
+ *     rt_plan_order; mixed: nonzero for a mixed-precision plan (only those
+ *     take a four-lane share); sm_count: the device's SM count (used with
+ *     RT_PLAN_LONG_EXCLUSIVE).
+ *   claims (out, caller-owned, claims_cap entries): canonical ray indices in
+ *     claim order, -1 for a hole; the first entries, *n_long rays (each with
+ *     seven holes after it with RT_PLAN_LONG_ALONE), are the four-lane share,
+ *     the rest one entry per other ray.  *n_claims receives the number of
+ *     entries written: n, plus 7 * *n_long with RT_PLAN_LONG_ALONE (at most
+ *     n + 7 * (n / 16)).
+ * Errors: RT_EINVAL (NULL cost or claims, bad dimensions or order, spread,
+ * flags, factor, sm_count, or claims_cap below the entries needed). */
+rt_err rt_order_claims(const int32_t *cost, int32_t n_freq, int32_t n_modes, int32_t n_el, int32_t n_az,
+                       int32_t claim_order, int32_t spread, double long_factor, int32_t mixed, uint32_t flags,
+                       int32_t sm_count, int32_t *claims, size_t claims_cap, size_t *n_long, size_t *n_claims);
+
 /* --------------------------------------------------------------- ionogram */
 /* Oblique-ionogram synthesis (Sec. IV-B-4: joint frequency-elevation scan,
  * group path against frequency at the receiver).  The fan is launched from

@@ -840,34 +840,13 @@ rt_err rt_plan_execute(const rt_plan *plan, rt_ray_result *out_dev, size_t out_l
 // 11.07 ms) and take half the SMs.
 constexpr int kExclusiveWarps = 2;
 
-rt_err rt_plan_order(rt_plan *plan, const rt_ray_result *cost_dev, int32_t spread, double long_factor,
-                     uint32_t flags, size_t *n_long, void *stream) {
-    if (!plan) return fail(RT_EINVAL, "plan is NULL");
-    if (spread < 0 || spread > 64) return fail(RT_EINVAL, "spread must be in 0..64");
-    if (flags & ~(uint32_t)(RT_PLAN_REST_IN_PLAN_ORDER | RT_PLAN_LONG_EXCLUSIVE | RT_PLAN_LONG_ALONE))
-        return fail(RT_EINVAL, "unknown flags 0x%x", flags);
-    if (!std::isfinite(long_factor)) return fail(RT_EINVAL, "long_factor must be finite");
-    if (n_long) *n_long = 0;
-    if (!cost_dev) {  // back to the plan's own order
-        if (plan->perm) cudaFree(plan->perm);
-        plan->perm = nullptr;
-        plan->n_long = plan->n_long_claims = 0;
-        return RT_OK;
-    }
-    const size_t n = plan->n;
-    cudaStream_t st = (cudaStream_t)stream;
-    // the n_evals field of every record, gathered on the device into the
-    // plan's cost array and copied back in one piece
-    if (!plan->evals) CUDA_TRY(cudaMalloc((void **)&plan->evals, n * sizeof(int32_t)));
-    CUDA_TRY(launch_gather_evals(cost_dev, plan->evals, (long long)n, st));
-    std::vector<int32_t> ev(n);
-    CUDA_TRY(cudaMemcpyAsync(ev.data(), plan->evals, n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    rt_err r = sync_with_timeout(st);
-    if (r != RT_OK) return r;
+// The claim list of a longest-first order (rt_order_claims, which
+// rt_plan_order calls): host arithmetic only.
+static void order_claims(std::vector<int32_t> ev, size_t n, long long n_f, long long n_m, long long n_e,
+                         long long n_a, int claim_order, int32_t spread, double long_factor, bool mixed,
+                         uint32_t flags, int sm_count, std::vector<int> &perm, size_t &nl, size_t &nc) {
     // expected cost: the largest cost within `spread` elevation and frequency
     // steps of the same mode and azimuth (canonical order [freq][mode][el][az])
-    const FanDev &f = plan->f;
-    const long long n_f = f.n_freq, n_m = f.n_modes, n_e = f.n_el, n_a = f.n_az;
     std::vector<int32_t> cost;
     if (spread == 0) {
         cost.swap(ev);
@@ -927,12 +906,12 @@ rt_err rt_plan_order(rt_plan *plan, const rt_ray_result *cost_dev, int32_t sprea
         ++start[kKeys - 1 - keys[i] + 1];
     }
     for (int k = 0; k < kKeys; ++k) start[k + 1] += start[k];
-    std::vector<int> perm(n);
+    perm.assign(n, 0);
     for (size_t i = 0; i < n; ++i) perm[start[kKeys - 1 - keys[i]]++] = (int)i;
     // the four-lane share: rays whose expected cost is at least long_factor
     // times the median (mixed path only), at most a sixteenth of the rays
-    size_t nl = 0;
-    if (long_factor > 0.0 && f.precision == RT_MIXED) {
+    nl = 0;
+    if (long_factor > 0.0 && mixed) {
         // the median cost (the element of rank n/2): a radix select over the
         // upper, then the lower 16 bits of the (non-negative) costs
         std::vector<size_t> hist(1 << 16);
@@ -954,17 +933,15 @@ rt_err rt_plan_order(rt_plan *plan, const rt_ray_result *cost_dev, int32_t sprea
         // blocks of kExclusiveWarps warps on SMs of their own: at most an
         // eighth of the SMs, so that a cost estimate that marks too many
         // rays does not take the GPU from the rest of the scan
-        int sms = 0;
-        CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, plan->grid->device));
         const size_t per_block = ((flags & RT_PLAN_LONG_ALONE) ? 1 : 32 / 4) * (size_t)kExclusiveWarps;
-        nl = std::min(nl, (size_t)std::max(sms / 8, 1) * per_block);
+        nl = std::min(nl, (size_t)std::max(sm_count / 8, 1) * per_block);
     }
     if (nl > 1) {
         // the four-lane share in the plan's claim order: neighbouring rays of
         // one trace share a warp (rays of similar cost from all over the scan
         // would wait for one another's branches and gathers at every attempt)
         auto claim_of = [&](long long ray) {
-            if (f.order != RT_ORDER_ELEVATION_FASTEST) return ray;
+            if (claim_order != RT_ORDER_ELEVATION_FASTEST) return ray;
             const long long a = ray % n_a, e = (ray / n_a) % n_e, fm = ray / (n_a * n_e);
             return (fm * n_a + a) * n_e + e;
         };
@@ -975,17 +952,21 @@ rt_err rt_plan_order(rt_plan *plan, const rt_ray_result *cost_dev, int32_t sprea
         // the other rays in the plan's own claim order
         std::vector<char> is_long(n, 0);
         for (size_t i = 0; i < nl; ++i) is_long[perm[i]] = 1;
-        size_t k = nl;
-        for (long long c = 0; c < (long long)n; ++c) {
-            long long ray = c;
-            if (f.order == RT_ORDER_ELEVATION_FASTEST) {  // as the kernels' claim_to_ray
-                const long long e = c % n_e, rest = c / n_e, a = rest % n_a, fm = rest / n_a;
-                ray = (fm * n_e + e) * n_a + a;
-            }
-            if (!is_long[ray]) perm[k++] = (int)ray;
+        const char *in_share = is_long.data();
+        int *out = perm.data() + nl;
+        if (claim_order == RT_ORDER_ELEVATION_FASTEST) {  // as the kernels' claim_to_ray
+            for (long long fm = 0; fm < n_f * n_m; ++fm)
+                for (long long a = 0; a < n_a; ++a)
+                    for (long long e = 0; e < n_e; ++e) {
+                        const long long ray = (fm * n_e + e) * n_a + a;
+                        if (!in_share[ray]) *out++ = (int)ray;
+                    }
+        } else {
+            for (long long ray = 0; ray < (long long)n; ++ray)
+                if (!in_share[ray]) *out++ = (int)ray;
         }
     }
-    size_t nc = nl;
+    nc = nl;
     if ((flags & RT_PLAN_LONG_ALONE) && nl > 0) {
         // a warp per ray in the four-lane launch: each ray's group of four
         // lanes is followed by seven holes
@@ -996,6 +977,41 @@ rt_err rt_plan_order(rt_plan *plan, const rt_ray_result *cost_dev, int32_t sprea
         nc = nl * kGroups;
         perm.swap(claims);
     }
+}
+
+
+rt_err rt_plan_order(rt_plan *plan, const rt_ray_result *cost_dev, int32_t spread, double long_factor,
+                     uint32_t flags, size_t *n_long, void *stream) {
+    if (!plan) return fail(RT_EINVAL, "plan is NULL");
+    if (spread < 0 || spread > 64) return fail(RT_EINVAL, "spread must be in 0..64");
+    if (flags & ~(uint32_t)(RT_PLAN_REST_IN_PLAN_ORDER | RT_PLAN_LONG_EXCLUSIVE | RT_PLAN_LONG_ALONE))
+        return fail(RT_EINVAL, "unknown flags 0x%x", flags);
+    if (!std::isfinite(long_factor)) return fail(RT_EINVAL, "long_factor must be finite");
+    if (n_long) *n_long = 0;
+    if (!cost_dev) {  // back to the plan's own order
+        if (plan->perm) cudaFree(plan->perm);
+        plan->perm = nullptr;
+        plan->n_long = plan->n_long_claims = 0;
+        return RT_OK;
+    }
+    const size_t n = plan->n;
+    cudaStream_t st = (cudaStream_t)stream;
+    // the n_evals field of every record, gathered on the device into the
+    // plan's cost array and copied back in one piece
+    if (!plan->evals) CUDA_TRY(cudaMalloc((void **)&plan->evals, n * sizeof(int32_t)));
+    CUDA_TRY(launch_gather_evals(cost_dev, plan->evals, (long long)n, st));
+    std::vector<int32_t> ev(n);
+    CUDA_TRY(cudaMemcpyAsync(ev.data(), plan->evals, n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    rt_err r = sync_with_timeout(st);
+    if (r != RT_OK) return r;
+    std::vector<int> perm;
+    size_t nl = 0, nc = 0;
+    int sms = 0;
+    if (flags & RT_PLAN_LONG_EXCLUSIVE)
+        CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, plan->grid->device));
+    const FanDev &f = plan->f;
+    order_claims(std::move(ev), n, f.n_freq, f.n_modes, f.n_el, f.n_az, f.order, spread, long_factor,
+                 f.precision == RT_MIXED, flags, sms, perm, nl, nc);
     // capacity for the largest claim list: n rays plus 7 holes for each of at
     // most n / 16 four-lane rays
     if (!plan->perm) CUDA_TRY(cudaMalloc((void **)&plan->perm, (n + 7 * (n / 16)) * sizeof(int)));
@@ -1025,6 +1041,32 @@ rt_err rt_plan_order(rt_plan *plan, const rt_ray_result *cost_dev, int32_t sprea
     plan->n_long_claims = nc;
     plan->lp_long = ll;
     if (n_long) *n_long = nl;
+    return RT_OK;
+}
+
+rt_err rt_order_claims(const int32_t *cost, int32_t n_freq, int32_t n_modes, int32_t n_el, int32_t n_az,
+                       int32_t claim_order, int32_t spread, double long_factor, int32_t mixed, uint32_t flags,
+                       int32_t sm_count, int32_t *claims, size_t claims_cap, size_t *n_long, size_t *n_claims) {
+    if (!cost || !claims) return fail(RT_EINVAL, "NULL argument");
+    if (n_freq < 1 || n_modes < 1 || n_modes > 2 || n_el < 1 || n_az < 1)
+        return fail(RT_EINVAL, "bad fan dimensions %d x %d x %d x %d", n_freq, n_modes, n_el, n_az);
+    const size_t n = (size_t)n_freq * (size_t)n_modes * (size_t)n_el * (size_t)n_az;
+    if (n >= ((size_t)1 << 31)) return fail(RT_EINVAL, "too many rays (at most 2^31 - 1)");
+    if (claim_order != RT_ORDER_CANONICAL && claim_order != RT_ORDER_ELEVATION_FASTEST)
+        return fail(RT_EINVAL, "unknown claim order %d", claim_order);
+    if (spread < 0 || spread > 64) return fail(RT_EINVAL, "spread must be in 0..64");
+    if (flags & ~(uint32_t)(RT_PLAN_REST_IN_PLAN_ORDER | RT_PLAN_LONG_EXCLUSIVE | RT_PLAN_LONG_ALONE))
+        return fail(RT_EINVAL, "unknown flags 0x%x", flags);
+    if (!std::isfinite(long_factor)) return fail(RT_EINVAL, "long_factor must be finite");
+    if ((flags & RT_PLAN_LONG_EXCLUSIVE) && sm_count < 1) return fail(RT_EINVAL, "sm_count must be positive");
+    std::vector<int> perm;
+    size_t nl = 0, nc = 0;
+    order_claims(std::vector<int32_t>(cost, cost + n), n, n_freq, n_modes, n_el, n_az, claim_order, spread,
+                 long_factor, mixed != 0, flags, sm_count, perm, nl, nc);
+    if (claims_cap < perm.size()) return fail(RT_EINVAL, "claims_cap %zu < %zu claims", claims_cap, perm.size());
+    std::copy(perm.begin(), perm.end(), claims);
+    if (n_long) *n_long = nl;
+    if (n_claims) *n_claims = perm.size();
     return RT_OK;
 }
 

@@ -35,7 +35,7 @@ EXPORTED = ["rt_grid_create", "rt_grid_destroy", "rt_grid_device_bytes", "rt_fan
             "rt_trace", "rt_trace_device", "rt_trace_fans_device", "rt_tune", "rt_eval_rhs", "rt_last_error",
             "rt_version", "rt_plan_create", "rt_plan_rays", "rt_plan_execute", "rt_plan_destroy", "rt_plan_order",
             "rt_ionogram", "rt_trace_device_noalloc", "rt_server_create", "rt_server_submit",
-            "rt_server_wait", "rt_server_destroy", "rt_measure_peaks"]
+            "rt_server_wait", "rt_server_destroy", "rt_measure_peaks", "rt_order_claims"]
 
 
 class RtError(RuntimeError):
@@ -170,6 +170,10 @@ def load(path=None):
     L.rt_plan_destroy.restype = ctypes.c_int
     L.rt_plan_order.argtypes = [vp, vp, ctypes.c_int32, ctypes.c_double, ctypes.c_uint32, ctypes.POINTER(sz), vp]
     L.rt_plan_order.restype = ctypes.c_int
+    i32 = ctypes.c_int32
+    L.rt_order_claims.argtypes = [vp, i32, i32, i32, i32, i32, i32, ctypes.c_double, i32, ctypes.c_uint32, i32,
+                                  vp, sz, ctypes.POINTER(sz), ctypes.POINTER(sz)]
+    L.rt_order_claims.restype = ctypes.c_int
     L.rt_ionogram.argtypes = [vp, ctypes.POINTER(rt_ionogram_desc), vp, sz, ctypes.POINTER(sz),
                               ctypes.POINTER(rt_launch_config), vp]
     L.rt_ionogram.restype = ctypes.c_int
@@ -355,6 +359,24 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def rt_order_claims(cost, dims, claim_order=RT_ORDER_ELEVATION_FASTEST, spread=2, long_factor=0.0, mixed=True,
+                    rest_in_plan_order=False, long_exclusive=False, long_alone=False, sm_count=0):
+    """rt_order_claims: the claim list of a longest-first order from host
+    costs (canonical order, dims = (n_freq, n_modes, n_el, n_az)); returns
+    (claims int32 array, -1 for holes; number of four-lane rays)."""
+    cost = np.ascontiguousarray(cost, dtype=np.int32)
+    n_f, n_m, n_e, n_a = (int(x) for x in dims)
+    cap = cost.size + 7 * (cost.size // 16)
+    claims = np.empty(max(cap, 1), dtype=np.int32)
+    n_long, n_claims = ctypes.c_size_t(), ctypes.c_size_t()
+    flags = ((RT_PLAN_REST_IN_PLAN_ORDER if rest_in_plan_order else 0) |
+             (RT_PLAN_LONG_EXCLUSIVE if long_exclusive else 0) | (RT_PLAN_LONG_ALONE if long_alone else 0))
+    _check(load().rt_order_claims(cost.ctypes.data, n_f, n_m, n_e, n_a, int(claim_order), int(spread),
+                                  float(long_factor), int(bool(mixed)), flags, int(sm_count), claims.ctypes.data,
+                                  claims.size, ctypes.byref(n_long), ctypes.byref(n_claims)))
+    return claims[:n_claims.value].copy(), n_long.value
 
 
 def rt_ionogram(grid, tx, rx, freq_mhz, el_deg, modes=RT_MODE_O | RT_MODE_X, integrator=RT_RKF45,
