@@ -281,8 +281,10 @@ rt_err rt_trace_device_noalloc(const rt_grid *grid, const rt_fan_desc *fan, rt_r
  * claim order x lanes per ray x 32, 64, 96 or 128 threads per block) for this grid
  * and fan shape on `stream`, each candidate on a strided sub-fan of at most
  * max_rays rays (0 = 65536; one warm-up and three timed launches each,
- * every timed launch after a 256 MiB fill that evicts L2), and returns the
- * candidate with the lowest median time in *best and that time in *best_ms.  A fan of at least two waves of
+ * every timed launch after a 256 MiB fill that evicts L2), then the four
+ * with the lowest median again in seven interleaved rounds, and returns the
+ * one with the lowest median of those seven in *best and that time in
+ * *best_ms.  A fan of at least two waves of
  * resident lanes at one lane per ray is issue-bound: it tries one lane per
  * ray only, on a sub-fan of at least four such waves (a smaller sub-fan would
  * reward the latency of its slowest rays instead).  Blocking.  Uses
