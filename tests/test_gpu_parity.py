@@ -213,6 +213,46 @@ def test_mixed_config2_whole_fan_against_the_oracle(c2_oracle):
         _mixed_vs_oracle(res, ref, well, key)
 
 
+def test_config2_fan_ordered_on_sms_of_its_own_keeps_every_record():
+    """The benchmark's fan as a four-lane plan ordered by its own previous
+    costs, its longest rays a warp each on SMs of their own (the bench's
+    `fan_ordered`): the same records, byte for byte, as the plan's canonical
+    execution -- eager and replayed from a captured graph."""
+    torch = pytest.importorskip("torch")
+    w = wl.config2()
+    g = rt.Grid(w.grid, w.ne, table=True)
+    fan = rt.Fan(w.fan, rt.RT_MIXED)
+    n = fan.n_rays
+    s = torch.cuda.current_stream()
+    plan = rt.Plan(g, fan, rt.launch_config(kernel=rt.RT_KERNEL_PLAIN, stencil=rt.RT_STENCIL_TABLE,
+                                            lanes_per_ray=4, block_threads=96,
+                                            order=rt.RT_ORDER_ELEVATION_FASTEST))
+    ref = torch.empty(n * 64, dtype=torch.uint8, device="cuda")
+    plan.execute(ref.data_ptr(), n, stream=s.cuda_stream)
+    s.synchronize()
+    want = ref.cpu().numpy().tobytes()
+    n_long = plan.order(ref.data_ptr(), spread=0, long_factor=2.0, rest_in_plan_order=True, long_exclusive=True,
+                        long_alone=True, stream=s.cuda_stream)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert 0 < n_long <= 2 * (sms // 8)
+    out = torch.full((n * 64,), 0xAB, dtype=torch.uint8, device="cuda")
+    plan.execute(out.data_ptr(), n, stream=s.cuda_stream)
+    s.synchronize()
+    assert out.cpu().numpy().tobytes() == want
+    side = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(graph, stream=side):
+            plan.execute(out.data_ptr(), n, stream=side.cuda_stream)
+    for _ in range(2):
+        out.fill_(0xAB)
+        graph.replay()
+        torch.cuda.synchronize()
+        assert out.cpu().numpy().tobytes() == want
+    del graph
+    plan.close()
+
+
 def test_mixed_config2_tighter_rtol_meets_the_bar_on_every_ray(orc):
     """At rtol 1e-9 the truncation error of a diverged step sequence is well
     inside 0.05 km: every well-conditioned ray of the fan (every second
