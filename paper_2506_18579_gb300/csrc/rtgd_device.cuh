@@ -135,11 +135,24 @@ __device__ __forceinline__ void interp_weights(R t, R w[4], R d[4], int interp) 
     gd_weights<R>(t, w, d);
 }
 
-// Eq. 13 contraction of one row of 4 altitude samples.
-template <typename R>
+// Eq. 13 contraction of one row of 4 altitude samples.  PACK (float only):
+// packed FMAs on the sample pairs (u0, u1) and (u2, u3) against the weight
+// pairs, then one addition per sum -- four instructions fewer per two sums
+// and a shorter chain; the sum is formed in another order (pairs first).
+template <typename R, bool PACK = false>
 __device__ __forceinline__ void row4(R u0, R u1, R u2, R u3, const R wc[4], const R dc[4], R &v, R &dv) {
     v = u0 * wc[0] + u1 * wc[1] + u2 * wc[2] + u3 * wc[3];
     dv = u0 * dc[0] + u1 * dc[1] + u2 * dc[2] + u3 * dc[3];
+}
+
+template <>
+__device__ __forceinline__ void row4<float, true>(float u0, float u1, float u2, float u3, const float wc[4],
+                                                  const float dc[4], float &v, float &dv) {
+    const float2 a = make_float2(u0, u1), b = make_float2(u2, u3);
+    const float2 p = __ffma2_rn(b, make_float2(wc[2], wc[3]), __fmul2_rn(a, make_float2(wc[0], wc[1])));
+    const float2 q = __ffma2_rn(b, make_float2(dc[2], dc[3]), __fmul2_rn(a, make_float2(dc[0], dc[1])));
+    v = p.x + p.y;
+    dv = q.x + q.y;
 }
 
 // Accumulates the (a, b) row into the lon/lat partial sums.
@@ -156,8 +169,9 @@ __device__ __forceinline__ void acc_row(R v, R dv, R wb, R db, R &s, R &sb, R &s
 // (a, b).  The samples are contracted relative to REF (Ne = REF + sum (u -
 // REF) w, the weights summing to 1 and their derivatives to 0), so that in
 // float the sums do not cancel against the magnitude of Ne; the caller adds
-// REF back (after combining partial sums, when the rows are split).
-#define RTGD_CONTRACT(R, ROW, REF, A0, NA, wa, da, wb, db, wc, dc, out)           \
+// REF back (after combining partial sums, when the rows are split).  PACK
+// selects the packed altitude rows (row4).
+#define RTGD_CONTRACT(R, PACK, ROW, REF, A0, NA, wa, da, wb, db, wc, dc, out)     \
     do {                                                                          \
         R n_ = R(0), na_ = R(0), nb_ = R(0), nc_ = R(0);                          \
         _Pragma("unroll") for (int a_ = 0; a_ < (NA); ++a_) {                     \
@@ -169,7 +183,7 @@ __device__ __forceinline__ void acc_row(R v, R dv, R wb, R db, R &s, R &sb, R &s
                 u1_ -= (REF);                                                     \
                 u2_ -= (REF);                                                     \
                 u3_ -= (REF);                                                     \
-                row4<R>(u0_, u1_, u2_, u3_, wc, dc, v_, dv_);                     \
+                row4<R, (PACK)>(u0_, u1_, u2_, u3_, wc, dc, v_, dv_);             \
                 acc_row<R>(v_, dv_, wb[b_], db[b_], s_, sb_, sc_);                \
             }                                                                     \
             n_ += s_ * wa[a_];                                                    \

@@ -291,7 +291,7 @@ __device__ void rhs64(const GridDev &g, const RayPhys<double> &rp, const double 
         u2 = __ldg(p_ + 2);                           \
         u3 = __ldg(p_ + 3);                           \
     }
-        RTGD_CONTRACT(double, RTGD_ROW64, 0.0, 0, 4, wa, da, wb, db, wc, dc, out);
+        RTGD_CONTRACT(double, false, RTGD_ROW64, 0.0, 0, 4, wa, da, wb, db, wc, dc, out);
 #undef RTGD_ROW64
         s.X = rp.xfac * out[0];
         s.dX[0] = rp.xfac * out[3] * g.inv_dalt;
@@ -761,7 +761,7 @@ __device__ __forceinline__ void rhs_mixed(const GridDev &g, const RayPhys<float>
         u2 = v_.z;                                        \
         u3 = v_.w;                                        \
     }
-        RTGD_CONTRACT(float, RTGD_ROWQ, ref, a0, NA, wa, da, wb, db, wc, dc, out);
+        RTGD_CONTRACT(float, (G > 1), RTGD_ROWQ, ref, a0, NA, wa, da, wb, db, wc, dc, out);
 #undef RTGD_ROWQ
     } else if (STENCIL == RT_STENCIL_TABLE) {
         const long long cell = ((long long)ia * (g.n_lon - 1) + ib) * (g.n_alt - 1) + ic;
@@ -775,7 +775,7 @@ __device__ __forceinline__ void rhs_mixed(const GridDev &g, const RayPhys<float>
         u2 = v_.z;                                  \
         u3 = v_.w;                                  \
     }
-        RTGD_CONTRACT(float, RTGD_ROWT, 0.0f, a0, NA, wa, da, wb, db, wc, dc, out);
+        RTGD_CONTRACT(float, (G > 1), RTGD_ROWT, 0.0f, a0, NA, wa, da, wb, db, wc, dc, out);
 #undef RTGD_ROWT
     } else {
         const long long sj = g.p_alt, si = (long long)g.p_lon * g.p_alt;
@@ -789,7 +789,7 @@ __device__ __forceinline__ void rhs_mixed(const GridDev &g, const RayPhys<float>
         u2 = __ldg(p_ + 2);                        \
         u3 = __ldg(p_ + 3);                        \
     }
-        RTGD_CONTRACT(float, RTGD_ROWG, ref, a0, NA, wa, da, wb, db, wc, dc, out);
+        RTGD_CONTRACT(float, (G > 1), RTGD_ROWG, ref, a0, NA, wa, da, wb, db, wc, dc, out);
 #undef RTGD_ROWG
     }
     if (G > 1) {
