@@ -52,14 +52,14 @@ KERNEL_SOURCES = ("paper_2506_18579_gb300/csrc/rtgd_kernels.cu", "paper_2506_185
 TRAFFIC = {
     # key = (workload, kernel, stencil, lanes per ray); the anisotropic fan in
     # the autotuner's configurations (plain, 4 lanes, 96-thread blocks)
-    ("c2", 1, 3, 4): {"bytes_per_launch": 26681088 + 17408, "source_sha256": "f4834e970da2418f"},
-    ("c2", 1, 2, 4): {"bytes_per_launch": 5412352 + 0, "source_sha256": "f4834e970da2418f"},
+    ("c2", 1, 3, 4): {"bytes_per_launch": 26680320 + 22272, "source_sha256": "b1b72ac8efe6498c"},
+    ("c2", 1, 2, 4): {"bytes_per_launch": 5698304 + 0, "source_sha256": "b1b72ac8efe6498c"},
     # the ionogram batch, one lane per ray (the only lane count the autotuner
     # tries on a fan this large): plain kernel with 32-thread blocks (table
     # and quad stencils), persistent kernel with 128-thread blocks
-    ("c4", 1, 3, 1): {"bytes_per_launch": 20861440 + 1409280, "source_sha256": "f4834e970da2418f"},
-    ("c4", 1, 2, 1): {"bytes_per_launch": 4627968 + 503296, "source_sha256": "f4834e970da2418f"},
-    ("c4", 2, 3, 1): {"bytes_per_launch": 20888064 + 514560, "source_sha256": "f4834e970da2418f"},
+    ("c4", 1, 3, 1): {"bytes_per_launch": 21006848 + 1536768, "source_sha256": "b1b72ac8efe6498c"},
+    ("c4", 1, 2, 1): {"bytes_per_launch": 4695040 + 478208, "source_sha256": "b1b72ac8efe6498c"},
+    ("c4", 2, 3, 1): {"bytes_per_launch": 21222656 + 523776, "source_sha256": "b1b72ac8efe6498c"},
 }
 SMS = 152
 FP32_LANES_PER_SM = 128
