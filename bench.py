@@ -52,14 +52,14 @@ KERNEL_SOURCES = ("paper_2506_18579_gb300/csrc/rtgd_kernels.cu", "paper_2506_185
 TRAFFIC = {
     # key = (workload, kernel, stencil, lanes per ray); the anisotropic fan in
     # the autotuner's configurations (plain, 4 lanes, 96-thread blocks)
-    ("c2", 1, 3, 4): {"bytes_per_launch": 26680320 + 22272, "source_sha256": "b1b72ac8efe6498c"},
-    ("c2", 1, 2, 4): {"bytes_per_launch": 5698304 + 0, "source_sha256": "b1b72ac8efe6498c"},
+    ("c2", 1, 3, 4): {"bytes_per_launch": 26831616 + 22528, "source_sha256": "2602d2aac951aea9"},
+    ("c2", 1, 2, 4): {"bytes_per_launch": 5379072 + 256, "source_sha256": "2602d2aac951aea9"},
     # the ionogram batch, one lane per ray (the only lane count the autotuner
     # tries on a fan this large): plain kernel with 32-thread blocks (table
     # and quad stencils), persistent kernel with 128-thread blocks
-    ("c4", 1, 3, 1): {"bytes_per_launch": 21006848 + 1536768, "source_sha256": "b1b72ac8efe6498c"},
-    ("c4", 1, 2, 1): {"bytes_per_launch": 4695040 + 478208, "source_sha256": "b1b72ac8efe6498c"},
-    ("c4", 2, 3, 1): {"bytes_per_launch": 21222656 + 523776, "source_sha256": "b1b72ac8efe6498c"},
+    ("c4", 1, 3, 1): {"bytes_per_launch": 21227520 + 1478144, "source_sha256": "2602d2aac951aea9"},
+    ("c4", 1, 2, 1): {"bytes_per_launch": 4333312 + 483584, "source_sha256": "2602d2aac951aea9"},
+    ("c4", 2, 3, 1): {"bytes_per_launch": 20590080 + 385792, "source_sha256": "2602d2aac951aea9"},
 }
 SMS = 152
 FP32_LANES_PER_SM = 128

@@ -1456,17 +1456,25 @@ __global__ void __launch_bounds__(128, G == 1 ? 3 : 2) trace_mixed_persistent_ke
             }
         }
         if (!__any_sync(FULL, L.active)) break;
-        if (++iters > max_iter) {  // defensive bound; never reached for valid inputs
-            if (L.active) {
-                L.status = RT_RAY_MAX_STEPS;
-                lane_finish(L, g, f, out, q == 0);
+        // the warp's rays to their end; the refill above stays out of this
+        // hot loop (with it inside, the loop ran 1-2 % slower on the batch)
+        bool over = false;
+        do {
+            if (++iters > max_iter) {  // defensive bound; never reached for valid inputs
+                if (L.active) {
+                    L.status = RT_RAY_MAX_STEPS;
+                    lane_finish(L, g, f, out, q == 0);
+                    L.active = false;
+                }
+                over = true;
+                break;
             }
-            break;
-        }
-        if (L.active) {
-            lane_attempt<STENCIL, G, IP>(L, g, f, T, q, gmask);
-            if (lane_end_attempt(L, g, f, land[threadIdx.x])) lane_finish(L, g, f, out, q == 0);
-        }
+            if (L.active) {
+                lane_attempt<STENCIL, G, IP>(L, g, f, T, q, gmask);
+                if (lane_end_attempt(L, g, f, land[threadIdx.x])) lane_finish(L, g, f, out, q == 0);
+            }
+        } while (__any_sync(FULL, L.active));
+        if (over) break;
     }
 }
 
