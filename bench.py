@@ -905,6 +905,7 @@ def run_batch(rt, wl, torch, flush, steps=3):
     torch.cuda.synchronize()
     g5.close()
     out_d["ordered"] = {"spread": {"later_snapshot": 1, "own_previous": 0}, "long_factor": 6.0,
+                        "flags": "RT_PLAN_LONG_EXCLUSIVE (the four-lane share on SMs of its own)",
                         "cost_sources": {"later_snapshot": "the same scan on the ionosphere with the TID advanced by "
                                                            "5 % of its period",
                                          "own_previous": "the plan's previous execution (same ionosphere)"}}
@@ -914,7 +915,8 @@ def run_batch(rt, wl, torch, flush, steps=3):
     for name, c, src, spread in (("plain", cfg, prev, 1), ("persistent", cfg_p, prev, 1),
                                  ("plain_own_previous", cfg, own, 0), ("persistent_own_previous", cfg_p, own, 0)):
         oplan = rt.Plan(grid, fan, cfg=c)
-        n_long = oplan.order(src.data_ptr(), spread=spread, long_factor=6.0, stream=side.cuda_stream)
+        n_long = oplan.order(src.data_ptr(), spread=spread, long_factor=6.0, long_exclusive=True,
+                             stream=side.cuda_stream)
         ograph = torch.cuda.CUDAGraph()
         torch.cuda.synchronize()
         with torch.cuda.stream(side):

@@ -819,5 +819,15 @@ def test_config4_batched_fan_in_captured_graph(c4_sample):
     ordered = rt.results_view(outp.cpu().numpy(), n).copy()
     assert np.all(ordered["status"] != rt.RT_RAY_NOT_RUN)
     _mixed_vs_oracle(ordered[idx], ref, well, "ordered persistent")
+    # the four-lane share on SMs of its own (cut to an eighth of the SMs)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    n_excl = pplan.order(prev.data_ptr(), spread=2, long_factor=6.0, long_exclusive=True, stream=side.cuda_stream)
+    assert 0 < n_excl <= min(n_long, 16 * (sms // 8))
+    outp.zero_()
+    pplan.execute(outp.data_ptr(), n, stream=side.cuda_stream)
+    torch.cuda.synchronize()
+    excl = rt.results_view(outp.cpu().numpy(), n).copy()
+    assert np.all(excl["status"] != rt.RT_RAY_NOT_RUN)
+    _mixed_vs_oracle(excl[idx], ref, well, "ordered persistent, exclusive share")
     pplan.close()
     g5.close()
